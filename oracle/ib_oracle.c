@@ -1,0 +1,236 @@
+/*
+ * ib_oracle.c -- FP64 reference for spreading and interpolation (arXiv 2012.06646).
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py, never by the CUDA library.
+ * Compile with -ffp-contract=off so that X*(N/L) - xi is two rounded FP64 ops.
+ */
+#include "ib_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static int g_mutation = 0;
+void or_set_mutation(int m) { g_mutation = m; }
+
+/* Kernels of Peskin (2002), cited by the paper in Section 2.
+ * Standard 4-point: (3 - 2|r| + sqrt(1 + 4|r| - 4r^2))/8 on |r| <= 1,
+ *                   (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2))/8 on 1 <= |r| <= 2, else 0.
+ * Cosine 4-point:   (1 + cos(pi r / 2))/4 on |r| <= 2, else 0. */
+double or_phi(int kernel, double r) {
+  double a = fabs(r);
+  if (a >= 2.0) return 0.0;
+  if (kernel == 1) return 0.25 * (1.0 + cos(M_PI * r / 2.0));
+  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+  return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+}
+
+/* d phi / d r of the same formulas (both kernels are C^1 on the real line). */
+double or_dphi(int kernel, double r) {
+  double a = fabs(r);
+  double sgn = (r < 0.0) ? -1.0 : 1.0;
+  if (a >= 2.0) return 0.0;
+  if (kernel == 1) return -(M_PI / 8.0) * sin(M_PI * r / 2.0);
+  if (a <= 1.0) {
+    double q = sqrt(1.0 + 4.0 * a - 4.0 * a * a);
+    return sgn * (-2.0 + (2.0 - 4.0 * a) / q) / 8.0;
+  }
+  double q = sqrt(-7.0 + 12.0 * a - 4.0 * a * a);
+  if (q == 0.0) return 0.0; /* |r| = 2 exactly is excluded above; guard the endpoint anyway */
+  return sgn * (-2.0 - (6.0 - 4.0 * a) / q) / 8.0;
+}
+
+void or_cell(double X, double scale, double xi, long long* i, double* r) {
+  volatile double u = X * scale; /* one rounded multiply */
+  u = u - xi;                    /* one rounded subtract */
+  double fl = floor(u);
+  *i = (long long)fl;
+  *r = u - fl;
+}
+
+double or_stagger(const or_grid* g, int comp, int b) {
+  if (g->grid == 1) return (comp == b) ? 0.0 : 0.5;
+  return 0.5;
+}
+
+static long long wrap(long long i, long long n) {
+  long long m = i % n;
+  return m < 0 ? m + n : m;
+}
+
+static long long ncell_of(const or_grid* g) {
+  long long c = (long long)g->n[0] * g->n[1];
+  if (g->dim == 3) c *= g->n[2];
+  return c;
+}
+
+static int check_grid(const or_grid* g) {
+  if (g->dim != 2 && g->dim != 3) return 1;
+  for (int b = 0; b < g->dim; ++b)
+    if (g->n[b] < 1 || !(g->L[b] > 0.0)) return 1;
+  if (g->ncomp < 1) return 1;
+  if (g->grid == 1 && g->ncomp != g->dim) return 1;
+  return 0;
+}
+
+int or_cell_keys(const or_grid* g, long long n, const double* X, unsigned long long* key) {
+  if (check_grid(g)) return 1;
+  for (long long j = 0; j < n; ++j) {
+    unsigned long long k = 0, stride = 1;
+    for (int b = 0; b < g->dim; ++b) {
+      long long i;
+      double r;
+      or_cell(X[j * g->dim + b], (double)g->n[b] / g->L[b], 0.0, &i, &r);
+      k += (unsigned long long)wrap(i, g->n[b]) * stride;
+      stride *= (unsigned long long)g->n[b];
+    }
+    key[j] = k;
+  }
+  return 0;
+}
+
+long long or_bin_stable(long long n, const unsigned long long* key, unsigned long long nkeys,
+                        long long* perm, long long* start) {
+  long long* count = (long long*)calloc(nkeys + 1, sizeof(long long));
+  long long q = 0;
+  for (long long j = 0; j < n; ++j) count[key[j]] += 1;
+  long long run = 0;
+  for (unsigned long long k = 0; k < nkeys; ++k) {
+    long long c = count[k];
+    if (c > 0) ++q;
+    start[k] = run;
+    count[k] = run; /* next free slot of key k */
+    run += c;
+  }
+  start[nkeys] = run;
+  for (long long j = 0; j < n; ++j) perm[count[key[j]]++] = j; /* index order within a key: stable */
+  free(count);
+  return q;
+}
+
+/* Per point: cell index and offset for one component in every dimension. */
+typedef struct {
+  long long i[3];
+  double r[3];
+} cellrec;
+
+static void point_cell(const or_grid* g, const double* Xj, int comp, cellrec* c) {
+  for (int b = 0; b < g->dim; ++b) {
+    or_cell(Xj[b], (double)g->n[b] / g->L[b], or_stagger(g, comp, b), &c->i[b], &c->r[b]);
+  }
+  if (g_mutation == 3 && g->dim >= 2) {
+    double t = c->r[0];
+    c->r[0] = c->r[1];
+    c->r[1] = t;
+  }
+}
+
+/* Shift number s (0-based) in colexicographic order, x fastest (Algorithm 1 with
+ * the digits of s read base 4), mapped to t in {-1, 0, 1, 2}. */
+static void shift_of(int s, int dim, int* t) {
+  for (int b = 0; b < dim; ++b) {
+    t[b] = (s % 4) - 1;
+    s /= 4;
+  }
+}
+
+/* Argument of phi for shift t and offset r: the displacement t - r of Eq. delta-defs. */
+static double karg(int t, double r) { return (g_mutation == 2) ? (double)t + r : (double)t - r; }
+
+static long long node_index(const or_grid* g, const cellrec* c, const int* t) {
+  long long k = 0, stride = 1;
+  for (int b = 0; b < g->dim; ++b) {
+    k += wrap(c->i[b] + t[b], g->n[b]) * stride;
+    stride *= g->n[b];
+  }
+  return k;
+}
+
+static double inv_cell_volume(const or_grid* g) {
+  double v = 1.0;
+  for (int b = 0; b < g->dim; ++b) v *= (double)g->n[b] / g->L[b];
+  return v;
+}
+
+int or_spread(const or_grid* g, long long n, const double* X, const double* G, double* f, double* fabs_out) {
+  if (check_grid(g)) return 1;
+  long long ncell = ncell_of(g);
+  int nshift = (g->dim == 3) ? 64 : 16;
+  double hmd = (g_mutation == 1) ? 1.0 : inv_cell_volume(g);
+  memset(f, 0, sizeof(double) * (size_t)(ncell * g->ncomp));
+  if (fabs_out) memset(fabs_out, 0, sizeof(double) * (size_t)(ncell * g->ncomp));
+  for (long long j = 0; j < n; ++j) {          /* loop over IB points (Algorithm 2) */
+    for (int a = 0; a < g->ncomp; ++a) {
+      cellrec c;
+      point_cell(g, X + j * g->dim, a, &c);
+      for (int s = 0; s < nshift; ++s) {       /* loop over shifts */
+        int t[3];
+        shift_of(s, g->dim, t);
+        double w = 1.0;
+        for (int b = 0; b < g->dim; ++b) w *= or_phi(g->kernel, karg(t[b], c.r[b]));
+        long long k = node_index(g, &c, t);
+        double contrib = hmd * w * G[j * g->ncomp + a];
+        f[a * ncell + k] += contrib;
+        if (fabs_out) fabs_out[a * ncell + k] += fabs(contrib);
+      }
+    }
+  }
+  return 0;
+}
+
+int or_interp(const or_grid* g, long long n, const double* X, const double* u, double* U, double* Uabs) {
+  if (check_grid(g)) return 1;
+  long long ncell = ncell_of(g);
+  int nshift = (g->dim == 3) ? 64 : 16;
+  for (long long j = 0; j < n; ++j) {          /* one independent row of S* per point (Algorithm 3) */
+    for (int a = 0; a < g->ncomp; ++a) {
+      cellrec c;
+      point_cell(g, X + j * g->dim, a, &c);
+      double acc = 0.0, aabs = 0.0;
+      for (int s = 0; s < nshift; ++s) {
+        int t[3];
+        shift_of(s, g->dim, t);
+        double w = 1.0;
+        for (int b = 0; b < g->dim; ++b) w *= or_phi(g->kernel, karg(t[b], c.r[b]));
+        double term = w * u[a * ncell + node_index(g, &c, t)];
+        acc += term;
+        aabs += fabs(term);
+      }
+      U[j * g->ncomp + a] = acc;
+      if (Uabs) Uabs[j * g->ncomp + a] = aabs;
+    }
+  }
+  return 0;
+}
+
+int or_pos_grad(const or_grid* g, long long n, const double* X, const double* field, const double* v,
+                double* D, double* Dabs) {
+  if (check_grid(g)) return 1;
+  long long ncell = ncell_of(g);
+  int nshift = (g->dim == 3) ? 64 : 16;
+  for (long long j = 0; j < n; ++j) {
+    for (int b = 0; b < g->dim; ++b) {
+      double acc = 0.0, aabs = 0.0;
+      /* d r_b / d X_b = N_b / L_b, and the weight depends on r_b through phi(t_b - r_b). */
+      double drdx = (double)g->n[b] / g->L[b];
+      double chain = (g_mutation == 4) ? drdx : -drdx;
+      for (int a = 0; a < g->ncomp; ++a) {
+        cellrec c;
+        point_cell(g, X + j * g->dim, a, &c);
+        for (int s = 0; s < nshift; ++s) {
+          int t[3];
+          shift_of(s, g->dim, t);
+          double w = chain * or_dphi(g->kernel, karg(t[b], c.r[b]));
+          for (int e = 0; e < g->dim; ++e)
+            if (e != b) w *= or_phi(g->kernel, karg(t[e], c.r[e]));
+          double term = v[j * g->ncomp + a] * w * field[a * ncell + node_index(g, &c, t)];
+          acc += term;
+          aabs += fabs(term);
+        }
+      }
+      D[j * g->dim + b] = acc;
+      if (Dabs) Dabs[j * g->dim + b] = aabs;
+    }
+  }
+  return 0;
+}

@@ -1,0 +1,46 @@
+"""Dense brute-force spreading matrix, a code path independent of the oracle.
+
+S[k, j] = h^-d prod_b phi((x_k - X_j)_b / h_b), summed over every periodic
+image of X_j: the regularised delta of Section 2 on a periodic box, written
+with no cell map, no shifts and no floor.  Used only to pin the oracle on
+tiny grids.  phi is typed here a second time from the kernel formulas of
+Peskin (2002); the closed-form pins in test_oracle_pins.py pin both copies.
+"""
+import itertools
+
+import numpy as np
+
+
+def phi_std(r):
+    a = np.abs(r)
+    inner = (3 - 2 * a + np.sqrt(np.clip(1 + 4 * a - 4 * a * a, 0, None))) / 8
+    outer = (5 - 2 * a - np.sqrt(np.clip(-7 + 12 * a - 4 * a * a, 0, None))) / 8
+    return np.where(a <= 1, inner, np.where(a < 2, outer, 0.0))
+
+
+def phi_cos(r):
+    return np.where(np.abs(r) < 2, 0.25 * (1 + np.cos(np.pi * r / 2)), 0.0)
+
+
+def node_positions(n, L, xi):
+    """Positions h (i + xi) of every node, x fastest, shape (ncell, d)."""
+    d = len(n)
+    axes = [L[b] / n[b] * (np.arange(n[b]) + xi[b]) for b in range(d)]
+    mesh = np.meshgrid(*reversed(axes), indexing="ij")       # z, y, x order
+    return np.stack([m.ravel() for m in reversed(mesh)], axis=1)
+
+
+def dense_S(n, L, xi, kernel, X):
+    d = len(n)
+    h = np.array([L[b] / n[b] for b in range(d)])
+    phi = phi_std if kernel == 0 else phi_cos
+    xk = node_positions(n, L, xi)
+    S = np.zeros((len(xk), len(X)))
+    lo = int(np.floor(np.min(X / np.array(L[:d])))) - 3 if len(X) else -3
+    hi = int(np.ceil(np.max(X / np.array(L[:d])))) + 3 if len(X) else 3
+    span = [range(-hi, -lo + 1)] * d
+    for img in itertools.product(*span):
+        shift = np.array(img) * np.array(L[:d])
+        diff = (xk[:, None, :] - (X[None, :, :] + shift)) / h
+        S += np.prod(phi(diff), axis=2)
+    return S / np.prod(h)

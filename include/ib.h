@@ -1,0 +1,211 @@
+/*
+ * ib.h -- C ABI of the GB300 (sm_103a) immersed-boundary coupling library.
+ *
+ * The library evaluates the Eulerian-Lagrangian coupling steps of the
+ * immersed boundary method of arXiv 2012.06646 ("A fine-grained
+ * parallelization of the immersed boundary method"):
+ *
+ *   spreading      f_a[k]  = sum_j delta_h(x_k - X_j) G_{j,a}          (Eq. disc-spread, Eq. matrix-spread)
+ *   interpolation  U_{j,a} = sum_k delta_h(x_k - X_j) u_a[k] h^d       (Eq. disc-interp, Eq. matrix-interp)
+ *
+ * with delta_h(x) = prod_b h_b^-1 phi(x_b / h_b) (Section 2) on a periodic
+ * box, G = F dtheta premultiplied by the caller.  The operator statements
+ * par-spread(Gamma_h, Omega_h, L) and par-interpolate(Gamma_h, Omega_h, e)
+ * of Algorithms 3 and 4 map onto ib_spread and ib_interpolate: a point set,
+ * a grid description (the plan) and one field per component.
+ *
+ * Conventions, shared with the paper's Section 3.1:
+ *   - Grid point of index i and staggering xi sits at h (i + xi).  MAC grid
+ *     (IB_GRID_MAC, Section 2): component a has xi_a = 0, xi_b = 1/2 (b != a).
+ *     Cell-centred grid: xi = (1/2, ..., 1/2) for every component.
+ *   - Cell of a point: i_b = floor(X_b * (N_b/L_b) - xi_b), evaluated so that
+ *     the integer agrees exactly with the FP64 evaluation of that formula;
+ *     support nodes i + t, t in {-1, 0, 1, 2}, weight prod_b phi(t_b - r_b)
+ *     with r = X (N/L) - xi - i (Eq. delta-defs, Fig. 1a).
+ *   - Node indices wrap modulo N_b (triply periodic box, Section 4).
+ *   - Points may lie outside [0, L); they are wrapped.  A position with
+ *     |X_b N_b / L_b| >= 2^30, or a non-finite one, is reported through
+ *     ib_plan_check (IB_ERR_RANGE / IB_ERR_NONFINITE); such a point spreads
+ *     nothing and interpolates to NaN.
+ *   - Layouts: X is row-major (npts, dim); G and U are row-major
+ *     (npts, ncomp); grid fields are component-major [ncomp][n2][n1][n0]
+ *     (x fastest), n2 absent in 2-D.  All arrays are contiguous.
+ *   - Every data pointer passed to a compute call is a DEVICE pointer owned
+ *     by the caller; the library never frees or retains it past the call.
+ *     The plan owns only its scratch.  Calls are asynchronous on `stream`
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - Argument errors are detected on the host before any launch and return
+ *     an error status with nothing enqueued.  Errors found on the device
+ *     (non-finite or out-of-range positions) are latched in the plan and
+ *     returned by ib_plan_check.
+ *   - A plan is not thread-safe: use it from one host thread and one stream
+ *     at a time.
+ *   - Results are run-to-run bit-reproducible: every node sum is formed in
+ *     a fixed order that does not depend on scheduling.
+ */
+#ifndef IB_H
+#define IB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IB_OK = 0,
+  IB_ERR_INVALID_ARG = 1,     /* bad descriptor, null pointer, unsupported combination */
+  IB_ERR_OOM = 2,             /* device or pinned host allocation failed */
+  IB_ERR_CUDA = 3,            /* a CUDA runtime call failed (launch or copy) */
+  IB_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up */
+  IB_ERR_CAPACITY = 5,        /* npts (or a batch wave) exceeds the capacity given at creation */
+  IB_ERR_NOT_IMPLEMENTED = 6,
+  IB_ERR_NONFINITE = 7,       /* a position was NaN or infinite (reported by ib_plan_check) */
+  IB_ERR_RANGE = 8,           /* a position was 2^30 or more cells away from the box */
+  IB_ERR_NO_BINS = 9          /* IB_REUSE_BINS without a matching ib_bin call */
+} ib_status;
+
+enum { IB_KERNEL_PESKIN4 = 0, IB_KERNEL_COSINE4 = 1 };   /* standard 4-point / cosine 4-point phi (Section 2) */
+enum { IB_GRID_CELL_CENTERED = 0, IB_GRID_MAC = 1 };
+enum { IB_F32 = 0, IB_F64 = 1 };
+
+/* Per-call flags. */
+#define IB_ACCUMULATE   0x1u   /* spread: f += S G (the paper's l_k <- l_k + w L_i), instead of f = S G */
+#define IB_COMPENSATED  0x2u   /* spread: node sums carried as TwoSum (value, error) pairs */
+#define IB_REUSE_BINS   0x4u   /* skip binning: reuse the bins of the last ib_bin call (same X, same npts) */
+
+typedef struct ib_plan_s* ib_plan;
+
+typedef struct {
+  int dim;                /* 2 or 3 */
+  int n[3];               /* grid points per dimension, each >= 1 (n[2] ignored in 2-D) */
+  double L[3];            /* box side per dimension, > 0 */
+  int grid;               /* IB_GRID_MAC (requires ncomp == dim) or IB_GRID_CELL_CENTERED */
+  int kernel;             /* IB_KERNEL_PESKIN4 or IB_KERNEL_COSINE4 */
+  int dtype;              /* IB_F32 or IB_F64: element type of X, G, f, u, U */
+  int ncomp;              /* components per field, 1..4 */
+  long long max_points;   /* largest npts any call on this plan will pass, >= 0 */
+  unsigned flags;         /* reserved, must be 0 */
+} ib_plan_desc;
+
+/* Device scratch bytes ib_plan_create would allocate for `desc`.  Host-only:
+ * no CUDA call.  Returns IB_ERR_INVALID_ARG for an invalid descriptor. */
+ib_status ib_plan_footprint(const ib_plan_desc* desc, size_t* bytes);
+
+/* Validate `desc`, allocate the plan's device scratch (one cudaMalloc arena)
+ * on the current device, and return the plan in *out.  Errors:
+ * IB_ERR_INVALID_ARG (descriptor), IB_ERR_OOM (allocation). */
+ib_status ib_plan_create(const ib_plan_desc* desc, ib_plan* out);
+
+/* Synchronise the device, free the plan's scratch and the plan.  NULL is a no-op. */
+ib_status ib_plan_destroy(ib_plan plan);
+
+/* Bin the npts points X by Eulerian cell: the key computation, stable key
+ * sort and unique-key offsets of Algorithm 4 (Fig. 2), keyed by the cell of
+ * xi = 0, key = c_x + n0 (c_y + n1 c_z).  The bins stay in the plan and are
+ * reused by later calls that pass IB_REUSE_BINS with the same X. */
+ib_status ib_bin(ib_plan plan, long long npts, const void* X, void* stream);
+
+/* Spreading (Eq. disc-spread): f = S G, or f += S G with IB_ACCUMULATE.
+ * X (npts, dim), G (npts, ncomp) read; f [ncomp][grid] written.  Bins X
+ * first unless IB_REUSE_BINS.  IB_COMPENSATED carries every node sum as a
+ * TwoSum pair (FP32 plans; accepted and ignored for FP64 plans).  npts = 0
+ * writes zeros (or leaves f unchanged with IB_ACCUMULATE). */
+ib_status ib_spread(ib_plan plan, long long npts, const void* X, const void* G, void* f,
+                    unsigned flags, void* stream);
+
+/* Interpolation (Eq. disc-interp, Algorithm 3): U = S* u.
+ * X (npts, dim), u [ncomp][grid] read; U (npts, ncomp) written.  Bins X first
+ * unless IB_REUSE_BINS (binning orders the per-point work by cell). */
+ib_status ib_interpolate(ib_plan plan, long long npts, const void* X, const void* u, void* U,
+                         unsigned flags, void* stream);
+
+/* Position derivative of the interpolation weights, contracted with a field
+ * and a per-point vector (derived from Eqs. disc-interp and disc-spread):
+ *   D_{j,b} = scale * sum_a v_{j,a} sum_t field_a[i+t] d/dX_b[prod_c phi(t_c - r_c)].
+ * With field = u, v = dLoss/dU and scale = 1 this is dLoss/dX of
+ * interpolation; with field = dLoss/df, v = G and scale = h^-d it is dLoss/dX
+ * of spreading.  X (npts, dim), field [ncomp][grid], v (npts, ncomp) read;
+ * D (npts, dim) written.  Bins X first unless IB_REUSE_BINS. */
+ib_status ib_pos_grad(ib_plan plan, long long npts, const void* X, const void* field, const void* v,
+                      double scale, void* D, unsigned flags, void* stream);
+
+/* Lagrangian position update of the timestep (steps b and g of Section 2):
+ * Xout = X + dt U, wrapped into [0, L) per dimension.  X, U (npts, dim);
+ * Xout may alias X.  Requires ncomp == dim. */
+ib_status ib_advect(ib_plan plan, long long npts, const void* X, const void* U, double dt, void* Xout,
+                    void* stream);
+
+/* Synchronise `stream`, then read and clear the plan's device error word:
+ * IB_OK, IB_ERR_NONFINITE or IB_ERR_RANGE (or IB_ERR_CUDA if the stream
+ * reports an error). */
+ib_status ib_plan_check(ib_plan plan, void* stream);
+
+/* Device pointers to the bins of the last ib_bin on this plan (for
+ * inspection and tests): perm[p] = index of the p-th point in cell order
+ * (uint32, npts entries), cell_start[c] = first sorted position of cell c
+ * (uint32, ncell + 2 entries; entry ncell starts the invalid points). */
+ib_status ib_plan_bins(ib_plan plan, const void** perm, const void** cell_start, long long* ncell,
+                       long long* npts);
+
+/* ---------------------------------------------------------------------------
+ * Batched, served form: one wave of independent spread + interpolate jobs of
+ * uneven grid and point counts runs as a fixed number of launches, whatever
+ * the number of jobs.  Jobs in a wave share dim, grid kind, kernel, dtype and
+ * ncomp (the batch descriptor); each has its own grid size, box, points and
+ * fields.  Paper counterpart: none (the paper runs one problem at a time);
+ * each job's result equals what ib_spread / ib_interpolate give for it alone.
+ * ------------------------------------------------------------------------- */
+
+typedef struct ib_batch_s* ib_batch;
+
+typedef struct {
+  int dim, grid, kernel, dtype, ncomp;   /* as in ib_plan_desc, shared by every job */
+  int max_jobs;                          /* jobs per wave */
+  long long max_points;                  /* total points per wave */
+  long long max_cells;                   /* total grid cells per wave (sum of n0 n1 n2), < 2^31 */
+  unsigned flags;                        /* reserved, must be 0 */
+} ib_batch_desc;
+
+typedef struct {
+  int n[3];              /* grid points per dimension */
+  double L[3];           /* box side per dimension */
+  long long npts;        /* points of this job, >= 0 */
+  const void* X;         /* (npts, dim), device */
+  const void* G;         /* (npts, ncomp), device; spread input (NULL: skip spreading) */
+  void* f;               /* [ncomp][grid], device; spread output */
+  const void* u;         /* [ncomp][grid], device; interpolation input (may equal f; NULL: skip) */
+  void* U;               /* (npts, ncomp), device; interpolation output */
+} ib_job;
+
+/* Device scratch bytes ib_batch_create would allocate.  Host-only. */
+ib_status ib_batch_footprint(const ib_batch_desc* desc, size_t* bytes);
+
+/* Scratch bytes one job occupies inside a wave (points, cells and spreading
+ * boxes), for admission by HBM footprint.  Host-only. */
+ib_status ib_batch_job_footprint(const ib_batch_desc* desc, const ib_job* job, size_t* bytes);
+
+ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out);
+ib_status ib_batch_destroy(ib_batch batch);
+
+/* Run one wave of njobs jobs on `stream`: bin every job's points, spread
+ * G -> f for every job with G != NULL, then interpolate u -> U for every job
+ * with u != NULL.  The job array is copied before the call returns.  Waits
+ * (host side) for the previous wave's job-table upload on this batch object
+ * before reusing its staging buffer.  IB_ERR_CAPACITY if the wave exceeds
+ * the batch capacity. */
+ib_status ib_batch_run(ib_batch batch, int njobs, const ib_job* jobs, unsigned flags, void* stream);
+
+/* As ib_plan_check, for the batch object's device error word. */
+ib_status ib_batch_check(ib_batch batch, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* ib_status_string(ib_status status);
+
+/* Library version string (static storage). */
+const char* ib_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IB_H */

@@ -16,13 +16,23 @@ void or_set_mutation(int m) { g_mutation = m; }
 /* Kernels of Peskin (2002), cited by the paper in Section 2.
  * Standard 4-point: (3 - 2|r| + sqrt(1 + 4|r| - 4r^2))/8 on |r| <= 1,
  *                   (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2))/8 on 1 <= |r| <= 2, else 0.
- * Cosine 4-point:   (1 + cos(pi r / 2))/4 on |r| <= 2, else 0. */
+ * Cosine 4-point:   (1 + cos(pi r / 2))/4 on |r| <= 2, else 0.
+ * Near |r| = 2 both definitions subtract nearly equal numbers.  They are
+ * evaluated here in identical closed forms without that cancellation, so the
+ * tail weights keep full relative accuracy:
+ *   outer branch: multiply and divide by (5 - 2|r| + sqrt(...)); the
+ *     numerator (5 - 2|r|)^2 - (-7 + 12|r| - 4r^2) equals 8 (2 - |r|)^2;
+ *   cosine: 1 + cos(2 y) = 2 cos(y)^2 with y = pi r / 4. */
 double or_phi(int kernel, double r) {
   double a = fabs(r);
   if (a >= 2.0) return 0.0;
-  if (kernel == 1) return 0.25 * (1.0 + cos(M_PI * r / 2.0));
+  if (kernel == 1) {
+    /* cos(pi a / 4) = sin(pi (2 - a) / 4); 2 - a is exact for 1 <= a <= 2 */
+    double c = (a < 1.0) ? cos(M_PI * a / 4.0) : sin(M_PI * (2.0 - a) / 4.0);
+    return 0.5 * c * c;
+  }
   if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
-  return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+  return (2.0 - a) * (2.0 - a) / (5.0 - 2.0 * a + sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
 }
 
 /* d phi / d r of the same formulas (both kernels are C^1 on the real line). */

@@ -306,3 +306,15 @@ def test_mutations_are_caught(orc, mutation):
     finally:
         orc.set_mutation(0)
     assert _pins_pass(orc)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_kernel_tail_keeps_relative_accuracy(orc, kernel):
+    """Near |r| = 2 the weights vanish like (2 - |r|)^2; the tail must stay accurate relative to itself.
+    Leading terms: standard (2-a)^2 / (5 - 2a + sqrt(..)) -> (2-a)^2 / 2; cosine (pi (2-a) / 4)^2 / 2."""
+    for eps in (1e-3, 1e-6, 1e-9):
+        a = 2.0 - eps
+        e = 2.0 - a                                # exact (Sterbenz): the distance actually represented
+        lead = e * e / 2.0 if kernel == 0 else (math.pi * e / 4.0) ** 2 / 2.0
+        v = orc.phi(kernel, a)[0]
+        assert abs(v / lead - 1.0) < 10 * eps + 1e-12, (eps, v, lead)

@@ -1,0 +1,381 @@
+"""Benchmark: spread + interpolate throughput on the 128^3 MAC grid with 10^6 points.
+
+One step (the unstructured-point protocol of the paper's Section 4.1, reduced
+to one spread and one interpolation): bin X, spread the step's forces G from X
+onto the grid, interpolate the shear velocity u back to X, and move X by
+dt U (dt chosen so the largest displacement is h/2).  `value` counts
+Lagrangian points processed per second by that spread + interpolate pair.
+
+Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
+the launching stream; L2 is flushed (256 MB write) between timed steps,
+outside the events.  Per-call events give the per-kernel durations used for
+the roofline.  `e2e` repeats the step through the same C ABI with host
+buffers: X and G copied in from pinned memory and U, f and the new X copied
+back, inside the timed region.
+
+--impl reference runs the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).  Under torchrun each rank runs its own independent
+replica of the workload (weak scaling, no data-path collective); rank 0
+prints the max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spread+interp Lagrangian pts/s @128^3 vs HBM roofline; batched p50/p99 latency"
+N_GRID = 128
+N_POINTS = 1_000_000
+GAMMA = 1.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--points", type=int, default=N_POINTS)
+    ap.add_argument("--grid", type=int, default=N_GRID)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=100_000)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2012_06646_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    captured on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src, val = None, None
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 2 and parts[0] == "csrc_sha256_16:":
+                src = parts[1]
+            if len(parts) >= 2 and parts[0] == f"{kernel}_dram_bytes_per_launch:":
+                val = float(parts[1])
+    return val if (src == csrc_hash() and val is not None) else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(seed, npts, N):
+    import ib_inputs
+    X = ib_inputs.uniform_points(seed, npts, (1.0, 1.0, 1.0), 3)
+    u = ib_inputs.shear_field_mac(N, 1.0, GAMMA)
+    return X, u
+
+
+def forces(seed, step, npts):
+    import ib_inputs
+    return ib_inputs.normal_array(seed * 1000 + step, (npts, 3), purpose="G")
+
+
+def cpu_oracle_rate(sample: int, N: int, seed: int):
+    """The FP64 oracle (single thread) on `sample` points of the workload:
+    one spread + one interpolation; returns (pts/s, seconds)."""
+    import oracle
+    X, u = workload(seed, sample, N)
+    G = forces(seed, 0, sample)
+    g = oracle.Grid(dim=3, n=(N, N, N), L=(1.0, 1.0, 1.0), mac=True)
+    t0 = time.perf_counter()
+    oracle.spread(g, X, G)
+    oracle.interp(g, X, u)
+    dt = time.perf_counter() - t0
+    return sample / dt, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sample = max(1000, min(args.points, 30_000))
+    N = args.grid
+    X, u = workload(args.seed, sample, N)
+    g = oracle.Grid(dim=3, n=(N, N, N), L=(1.0, 1.0, 1.0), mac=True)
+    h = 1.0 / N
+    dt = h / (GAMMA * 1.0)
+    times = []
+    for step in range(args.warmup + args.steps):
+        G = forces(args.seed, step, sample)
+        t0 = time.perf_counter()
+        oracle.spread(g, X, G)
+        U, _ = oracle.interp(g, X, u)
+        X = (X.astype(np.float64) + dt * U)
+        X = (X - np.floor(X)).astype(np.float32)
+        t = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(t)
+    tot = sum(times)
+    value = sample * len(times) / tot
+    cores = 1
+    line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{N}^3 MAC grid, uniform points, one spread + one interpolation + advection "
+                                   f"per step (bounded sample of {sample} of the {args.points} points)",
+                       "grid": N, "n_points": args.points, "sample_points": sample},
+            "cpu_baseline": {"value": value, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} points per step, FP64 direct sums, single thread"},
+            "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2012_06646_gb300 import build
+    build()
+    from paper_2012_06646_gb300.plan import Plan
+
+    N, npts = args.grid, args.points
+    seed = args.seed + 7919 * rank
+    X0, u = workload(seed, npts, N)
+    h = 1.0 / N
+    dt = h / (GAMMA * 1.0)            # max |u| = gamma L / 2  ->  max displacement h / 2
+    plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", max_points=npts, device=device)
+    stream = torch.cuda.Stream(device)
+    nsteps = args.warmup + args.steps
+    Gs = [torch.from_numpy(forces(seed, s, npts)).to(device) for s in range(nsteps)]
+    ud = torch.from_numpy(u).to(device)
+    X = torch.from_numpy(X0).to(device)
+    f = torch.empty(plan.grid_shape(), dtype=torch.float32, device=device)
+    U = torch.empty((npts, 3), dtype=torch.float32, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    torch.cuda.synchronize()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    names = ("bin", "spread", "interp", "advect")
+    per_call = {k: [] for k in names}
+    step_ms = []
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    with torch.cuda.stream(stream):
+        for s in range(nsteps):
+            timed = s >= args.warmup
+            if timed and s == args.warmup:
+                if world > 1:
+                    torch.distributed.barrier()
+                torch.cuda.synchronize()
+                sampler.start()
+            flush.fill_(s & 0xFF)                    # L2 flush, outside the timed events
+            e = [ev() for _ in range(5)]
+            e[0].record(stream)
+            plan.bin(X, stream=stream)
+            e[1].record(stream)
+            plan.spread(X, Gs[s], f=f, reuse_bins=True, stream=stream)
+            e[2].record(stream)
+            plan.interpolate(X, ud, U=U, reuse_bins=True, stream=stream)
+            e[3].record(stream)
+            plan.advect(X, U, dt, out=X, stream=stream)
+            e[4].record(stream)
+            if timed:
+                e[4].synchronize()
+                step_ms.append(e[0].elapsed_time(e[4]))
+                for i, k in enumerate(names):
+                    per_call[k].append(e[i].elapsed_time(e[i + 1]))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    plan.check(stream)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    value = npts * world * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X0).pin_memory()
+        Gh = [g.cpu().pin_memory() for g in Gs[: min(len(Gs), 4)]]
+        Uh = torch.empty((npts, 3), dtype=torch.float32).pin_memory()
+        fh = torch.empty(plan.grid_shape(), dtype=torch.float32).pin_memory()
+        Xd = torch.empty_like(X)
+        Gd = torch.empty_like(Gs[0])
+        e2e_ms = []
+        with torch.cuda.stream(stream):
+            for s in range(nsteps):
+                flush.fill_(s & 0xFF)
+                a, b = ev(), ev()
+                a.record(stream)
+                Xd.copy_(Xh, non_blocking=True)
+                Gd.copy_(Gh[s % len(Gh)], non_blocking=True)
+                plan.bin(Xd, stream=stream)
+                plan.spread(Xd, Gd, f=f, reuse_bins=True, stream=stream)
+                plan.interpolate(Xd, ud, U=U, reuse_bins=True, stream=stream)
+                plan.advect(Xd, U, dt, out=Xd, stream=stream)
+                Uh.copy_(U, non_blocking=True)
+                fh.copy_(f, non_blocking=True)
+                Xh.copy_(Xd, non_blocking=True)
+                b.record(stream)
+                b.synchronize()
+                if s >= args.warmup:
+                    e2e_ms.append(a.elapsed_time(b))
+        tot = sum(e2e_ms)
+        if world > 1:
+            t = torch.tensor([tot], device=device)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e = {"value": npts * world * args.steps / (tot / 1e3), "unit": "pts/s",
+               "h2d_bytes_per_step": int(Xd.numel() * 4 + Gd.numel() * 4),
+               "d2h_bytes_per_step": int(Uh.numel() * 4 + fh.numel() * 4 + Xh.numel() * 4)}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant call ----
+    peak, peak_kind = load_peaks()
+    nc = 3
+    alg = {"spread": npts * 3 * 4 + npts * nc * 4 + nc * N ** 3 * 4,
+           "interp": npts * 3 * 4 + nc * N ** 3 * 4 + npts * nc * 4}
+    mean_ms = {k: statistics.mean(v) for k, v in per_call.items()}
+    dom = max(("spread", "interp"), key=lambda k: mean_ms[k])
+    achieved = alg[dom] / (mean_ms[dom] / 1e3) / 1e9
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "algorithmic_bytes_per_launch": alg[dom]}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            rate, secs = cpu_oracle_rate(min(args.cpu_sample, npts), N, args.seed)
+            cpu = {"value": rate, "unit": "pts/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{min(args.cpu_sample, npts)} of the {npts} points, one FP64 spread + one "
+                             f"interpolation on the {N}^3 MAC grid, single thread ({secs:.1f} s)"}
+        except Exception as exc:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": "pts/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    launches_per_step = 6 + 2 + 1 + 1     # bin: count, 3 scan, scatter, stable; spread: box, combine; interp; advect
+    line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{N}^3 MAC grid, {npts} uniform points per GPU, FP32, standard 4-point "
+                                   "kernel; per step: bin, spread, interpolate, advect",
+                       "grid": N, "n_points": npts, "steps": args.steps,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "calls_ms": mean_ms}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,6 +69,9 @@ enum { IB_KERNEL_PESKIN4 = 0, IB_KERNEL_COSINE4 = 1 };   /* standard 4-point / c
 enum { IB_GRID_CELL_CENTERED = 0, IB_GRID_MAC = 1 };
 enum { IB_F32 = 0, IB_F64 = 1 };
 
+/* Plan creation flags (ib_plan_desc.flags). */
+#define IB_PLAN_COMPENSATED 0x1u   /* size the scratch for IB_COMPENSATED spreading (twice the box scratch) */
+
 /* Per-call flags. */
 #define IB_ACCUMULATE   0x1u   /* spread: f += S G (the paper's l_k <- l_k + w L_i), instead of f = S G */
 #define IB_COMPENSATED  0x2u   /* spread: node sums carried as TwoSum (value, error) pairs */
@@ -84,8 +87,8 @@ typedef struct {
   int kernel;             /* IB_KERNEL_PESKIN4 or IB_KERNEL_COSINE4 */
   int dtype;              /* IB_F32 or IB_F64: element type of X, G, f, u, U */
   int ncomp;              /* components per field, 1..4 */
-  long long max_points;   /* largest npts any call on this plan will pass, >= 0 */
-  unsigned flags;         /* reserved, must be 0 */
+  long long max_points;   /* largest npts any call on this plan will pass, 0 <= max_points < 2^31 */
+  unsigned flags;         /* 0 or IB_PLAN_COMPENSATED */
 } ib_plan_desc;
 
 /* Device scratch bytes ib_plan_create would allocate for `desc`.  Host-only:
@@ -109,7 +112,8 @@ ib_status ib_bin(ib_plan plan, long long npts, const void* X, void* stream);
 /* Spreading (Eq. disc-spread): f = S G, or f += S G with IB_ACCUMULATE.
  * X (npts, dim), G (npts, ncomp) read; f [ncomp][grid] written.  Bins X
  * first unless IB_REUSE_BINS.  IB_COMPENSATED carries every node sum as a
- * TwoSum pair (FP32 plans; accepted and ignored for FP64 plans).  npts = 0
+ * TwoSum (value, error) pair and rounds once at the end; it needs a plan
+ * created with IB_PLAN_COMPENSATED (else IB_ERR_INVALID_ARG).  npts = 0
  * writes zeros (or leaves f unchanged with IB_ACCUMULATE). */
 ib_status ib_spread(ib_plan plan, long long npts, const void* X, const void* G, void* f,
                     unsigned flags, void* stream);
@@ -164,6 +168,7 @@ typedef struct {
   int max_jobs;                          /* jobs per wave */
   long long max_points;                  /* total points per wave */
   long long max_cells;                   /* total grid cells per wave (sum of n0 n1 n2), < 2^31 */
+  long long max_tiles;                   /* total spreading tiles per wave (see ib_batch_job_footprint) */
   unsigned flags;                        /* reserved, must be 0 */
 } ib_batch_desc;
 
@@ -181,9 +186,11 @@ typedef struct {
 /* Device scratch bytes ib_batch_create would allocate.  Host-only. */
 ib_status ib_batch_footprint(const ib_batch_desc* desc, size_t* bytes);
 
-/* Scratch bytes one job occupies inside a wave (points, cells and spreading
- * boxes), for admission by HBM footprint.  Host-only. */
-ib_status ib_batch_job_footprint(const ib_batch_desc* desc, const ib_job* job, size_t* bytes);
+/* Scratch one job occupies inside a wave, for admission by HBM footprint:
+ * bytes of points, cells and spreading boxes, and its number of spreading
+ * tiles (counted against max_tiles).  Host-only; either output may be NULL. */
+ib_status ib_batch_job_footprint(const ib_batch_desc* desc, const ib_job* job, size_t* bytes,
+                                 long long* tiles);
 
 ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out);
 ib_status ib_batch_destroy(ib_batch batch);

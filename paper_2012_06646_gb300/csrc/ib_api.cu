@@ -1,0 +1,551 @@
+// ib_api.cu -- the C ABI (include/ib.h): plan and batch objects, the device
+// scratch arena, argument checks and the launch sequence of every entry point.
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/ib.h"
+#include "ib_internal.h"
+
+using namespace ibgb;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr long long kMaxCellsTotal = (1ll << 31) - 16;
+constexpr long long kMaxPointsTotal = (1ll << 31) - 16;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// scale = S 2^E with 0 < S < 2^24 when possible (X * scale is then exact in
+// FP64 for every FP32 X); S = 0 otherwise.
+void short_scale(double s, int* S, int* E) {
+  int ex = 0;
+  const double m = frexp(s, &ex);
+  uint64_t M = (uint64_t)ldexp(m, 53);
+  int e = ex - 53;
+  while (M != 0 && (M & 1u) == 0) {
+    M >>= 1;
+    ++e;
+  }
+  if (M > 0 && M < (1ull << 24)) {
+    *S = (int)M;
+    *E = e;
+  } else {
+    *S = 0;
+    *E = 0;
+  }
+}
+
+int entry_bytes(int dtype, bool comp) { return (dtype == IB_F64 ? 8 : 4) * (comp ? 2 : 1); }
+
+// Fill the geometry part of a job for a grid of n points and sides L.
+bool fill_job(Job& jb, int dim, const int n[3], const double L[3], int tile) {
+  memset(&jb, 0, sizeof(jb));
+  long long ncell = 1;
+  double hmd = 1.0;
+  for (int b = 0; b < 3; ++b) {
+    const bool live = b < dim;
+    const int nb = live ? n[b] : 1;
+    const double Lb = live ? L[b] : 1.0;
+    if (nb < 1 || !(Lb > 0.0) || !isfinite(Lb)) return false;
+    jb.n[b] = nb;
+    jb.ntile[b] = live ? (nb + tile - 1) / tile : 1;
+    jb.scale[b] = (double)nb / Lb;
+    if (!isfinite(jb.scale[b]) || !(jb.scale[b] > 0.0)) return false;
+    short_scale(jb.scale[b], &jb.sS[b], &jb.sE[b]);
+    jb.Lf[b] = (float)Lb;
+    jb.Ld[b] = Lb;
+    if (live) {
+      ncell *= nb;
+      hmd *= jb.scale[b];
+    }
+    if (ncell > kMaxCellsTotal) return false;
+  }
+  jb.ncell = ncell;
+  jb.hmd = hmd;
+  jb.ntiles = (long long)jb.ntile[0] * jb.ntile[1] * jb.ntile[2];
+  return true;
+}
+
+void set_tiles(Job& jb, int dim, int tile) {
+  for (int b = 0; b < 3; ++b) jb.ntile[b] = (b < dim) ? (jb.n[b] + tile - 1) / tile : 1;
+  jb.ntiles = (long long)jb.ntile[0] * jb.ntile[1] * jb.ntile[2];
+}
+
+bool valid_shape(int dim, int grid, int kernel, int dtype, int ncomp) {
+  if (dim != 2 && dim != 3) return false;
+  if (grid != IB_GRID_MAC && grid != IB_GRID_CELL_CENTERED) return false;
+  if (kernel != IB_KERNEL_PESKIN4 && kernel != IB_KERNEL_COSINE4) return false;
+  if (dtype != IB_F32 && dtype != IB_F64) return false;
+  if (ncomp < 1 || ncomp > 4) return false;
+  if (grid == IB_GRID_MAC && ncomp != dim) return false;
+  return true;
+}
+
+// Arena layout shared by plans and batches.
+struct Layout {
+  size_t count, key, rank, perm_tmp, perm, block_sums, err, boxes, table, total;
+};
+
+Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t table_bytes) {
+  Layout L;
+  size_t off = 0;
+  L.count = off;      off += align_up(sizeof(uint32_t) * (size_t)(ncell + 2));
+  L.key = off;        off += align_up(sizeof(uint32_t) * (size_t)npts);
+  L.rank = off;       off += align_up(sizeof(uint32_t) * (size_t)npts);
+  L.perm_tmp = off;   off += align_up(sizeof(uint32_t) * (size_t)npts);
+  L.perm = off;       off += align_up(sizeof(uint32_t) * (size_t)npts);
+  L.block_sums = off; off += align_up(sizeof(uint32_t) * (size_t)(scan_blocks(ncell + 1) + 1));
+  L.err = off;        off += align_up(sizeof(uint32_t));
+  L.boxes = off;      off += align_up(boxes_bytes);
+  L.table = off;      off += align_up(table_bytes);
+  L.total = off;
+  return L;
+}
+
+Bins carve(char* base, const Layout& L) {
+  Bins B;
+  B.count = (uint32_t*)(base + L.count);
+  B.key = (uint32_t*)(base + L.key);
+  B.rank = (uint32_t*)(base + L.rank);
+  B.perm_tmp = (uint32_t*)(base + L.perm_tmp);
+  B.perm = (uint32_t*)(base + L.perm);
+  B.block_sums = (uint32_t*)(base + L.block_sums);
+  B.err = (uint32_t*)(base + L.err);
+  B.ncell_total = 0;
+  B.npts_total = 0;
+  return B;
+}
+
+ib_status check_error_word(uint32_t* err_dev, cudaStream_t s) {
+  if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
+  uint32_t e = 0;
+  if (cudaMemcpy(&e, err_dev, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return IB_ERR_CUDA;
+  if (e != 0 && cudaMemset(err_dev, 0, sizeof(uint32_t)) != cudaSuccess) return IB_ERR_CUDA;
+  if (e & ERR_NONFINITE) return IB_ERR_NONFINITE;
+  if (e & ERR_RANGE) return IB_ERR_RANGE;
+  return IB_OK;
+}
+
+}  // namespace
+
+struct ib_plan_s {
+  ib_plan_desc desc;
+  Shape sh;
+  Job job;             // geometry; per-call fields are filled on a copy
+  int tile_plain, tile_comp;
+  long long ntiles_plain, ntiles_comp;
+  Layout layout;
+  void* arena;
+  Bins bins;
+  void* boxes;
+  // bins state
+  bool binned;
+  const void* binned_X;
+  long long binned_n;
+};
+
+struct ib_batch_s {
+  ib_batch_desc desc;
+  Shape sh;
+  int tile;
+  Layout layout;
+  void* arena;
+  Bins bins;
+  void* boxes;
+  Job* d_table;
+  Job* h_stage;        // pinned staging buffer of the job table
+  cudaEvent_t uploaded;
+  bool pending;
+};
+
+namespace {
+
+bool plan_sizes(const ib_plan_desc* d, Job* jb, int* tp, int* tc, long long* ntp, long long* ntc, Layout* L) {
+  if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
+  if (d->max_points < 0 || d->max_points > kMaxPointsTotal) return false;
+  if (d->flags & ~IB_PLAN_COMPENSATED) return false;
+  const int tile_plain = spread_tile_side(d->dim, entry_bytes(d->dtype, false), d->ncomp);
+  const int tile_comp = spread_tile_side(d->dim, entry_bytes(d->dtype, true), d->ncomp);
+  Job j;
+  if (!fill_job(j, d->dim, d->n, d->L, tile_plain)) return false;
+  if (j.ncell > kMaxCellsTotal) return false;
+  const long long ntp_ = j.ntiles;
+  set_tiles(j, d->dim, tile_comp);
+  const long long ntc_ = j.ntiles;
+  set_tiles(j, d->dim, tile_plain);
+  size_t boxes = (size_t)ntp_ * box_bytes(d->dim, tile_plain, entry_bytes(d->dtype, false), d->ncomp);
+  if (d->flags & IB_PLAN_COMPENSATED) {
+    const size_t bc = (size_t)ntc_ * box_bytes(d->dim, tile_comp, entry_bytes(d->dtype, true), d->ncomp);
+    if (bc > boxes) boxes = bc;
+  }
+  if (jb) *jb = j;
+  if (tp) *tp = tile_plain;
+  if (tc) *tc = tile_comp;
+  if (ntp) *ntp = ntp_;
+  if (ntc) *ntc = ntc_;
+  if (L) *L = make_layout(j.ncell, d->max_points, boxes, 0);
+  return true;
+}
+
+ib_status run_bin(ib_plan p, long long npts, const void* X, cudaStream_t s) {
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.njobs = 1;
+  Bins B = p->bins;
+  B.npts_total = npts;
+  B.ncell_total = p->job.ncell;
+  if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(B.ncell_total + 2), s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  if (launch_bin(J, p->sh, B, p->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  p->binned = true;
+  p->binned_X = X;
+  p->binned_n = npts;
+  return IB_OK;
+}
+
+ib_status prepare(ib_plan p, long long npts, const void* X, unsigned flags, cudaStream_t s) {
+  if (flags & IB_REUSE_BINS) {
+    if (!p->binned || p->binned_X != X || p->binned_n != npts) return IB_ERR_NO_BINS;
+    return IB_OK;
+  }
+  return run_bin(p, npts, X, s);
+}
+
+ib_status check_call(ib_plan p, long long npts, const void* X) {
+  if (!p) return IB_ERR_INVALID_ARG;
+  if (npts < 0) return IB_ERR_INVALID_ARG;
+  if (npts > p->desc.max_points) return IB_ERR_CAPACITY;
+  if (npts > 0 && !X) return IB_ERR_INVALID_ARG;
+  return IB_OK;
+}
+
+Bins call_bins(ib_plan p, long long npts) {
+  Bins B = p->bins;
+  B.npts_total = npts;
+  B.ncell_total = p->job.ncell;
+  return B;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ib_status_string(ib_status st) {
+  switch (st) {
+    case IB_OK: return "IB_OK";
+    case IB_ERR_INVALID_ARG: return "IB_ERR_INVALID_ARG";
+    case IB_ERR_OOM: return "IB_ERR_OOM";
+    case IB_ERR_CUDA: return "IB_ERR_CUDA";
+    case IB_ERR_TIMEOUT: return "IB_ERR_TIMEOUT";
+    case IB_ERR_CAPACITY: return "IB_ERR_CAPACITY";
+    case IB_ERR_NOT_IMPLEMENTED: return "IB_ERR_NOT_IMPLEMENTED";
+    case IB_ERR_NONFINITE: return "IB_ERR_NONFINITE";
+    case IB_ERR_RANGE: return "IB_ERR_RANGE";
+    case IB_ERR_NO_BINS: return "IB_ERR_NO_BINS";
+  }
+  return "IB_ERR_UNKNOWN";
+}
+
+const char* ib_version(void) { return "ibgb 0.1 (sm_103a)"; }
+
+ib_status ib_plan_footprint(const ib_plan_desc* desc, size_t* bytes) {
+  Layout L;
+  if (!bytes || !plan_sizes(desc, nullptr, nullptr, nullptr, nullptr, nullptr, &L)) return IB_ERR_INVALID_ARG;
+  *bytes = L.total;
+  return IB_OK;
+}
+
+ib_status ib_plan_create(const ib_plan_desc* desc, ib_plan* out) {
+  if (!out) return IB_ERR_INVALID_ARG;
+  *out = nullptr;
+  ib_plan p = new (std::nothrow) ib_plan_s;
+  if (!p) return IB_ERR_OOM;
+  memset(p, 0, sizeof(*p));
+  if (!plan_sizes(desc, &p->job, &p->tile_plain, &p->tile_comp, &p->ntiles_plain, &p->ntiles_comp, &p->layout)) {
+    delete p;
+    return IB_ERR_INVALID_ARG;
+  }
+  p->desc = *desc;
+  p->sh.dim = desc->dim;
+  p->sh.ncomp = desc->ncomp;
+  p->sh.mac = desc->grid == IB_GRID_MAC ? 1 : 0;
+  p->sh.kernel = desc->kernel;
+  if (cudaMalloc(&p->arena, p->layout.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return IB_ERR_OOM;
+  }
+  p->bins = carve((char*)p->arena, p->layout);
+  p->boxes = (char*)p->arena + p->layout.boxes;
+  if (cudaMemset(p->bins.err, 0, sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(p->arena);
+    delete p;
+    return IB_ERR_CUDA;
+  }
+  *out = p;
+  return IB_OK;
+}
+
+ib_status ib_plan_destroy(ib_plan p) {
+  if (!p) return IB_OK;
+  cudaDeviceSynchronize();
+  cudaFree(p->arena);
+  delete p;
+  return IB_OK;
+}
+
+ib_status ib_bin(ib_plan p, long long npts, const void* X, void* stream) {
+  ib_status st = check_call(p, npts, X);
+  if (st != IB_OK) return st;
+  return run_bin(p, npts, X, (cudaStream_t)stream);
+}
+
+ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, void* f, unsigned flags,
+                    void* stream) {
+  ib_status st = check_call(p, npts, X);
+  if (st != IB_OK) return st;
+  if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
+  if (flags & ~(IB_ACCUMULATE | IB_COMPENSATED | IB_REUSE_BINS)) return IB_ERR_INVALID_ARG;
+  const bool comp = (flags & IB_COMPENSATED) != 0;
+  if (comp && !(p->desc.flags & IB_PLAN_COMPENSATED)) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = prepare(p, npts, X, flags, s);
+  if (st != IB_OK) return st;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  const int tile = comp ? p->tile_comp : p->tile_plain;
+  set_tiles(J.one, p->desc.dim, tile);
+  J.one.npts = npts;
+  J.one.X = X;
+  J.one.G = G ? G : f;  // npts == 0: any non-null marker; no point is read
+  J.one.f = f;
+  J.njobs = 1;
+  if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp,
+                    (flags & IB_ACCUMULATE) != 0, s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  return IB_OK;
+}
+
+ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u, void* U, unsigned flags,
+                         void* stream) {
+  ib_status st = check_call(p, npts, X);
+  if (st != IB_OK) return st;
+  if (npts > 0 && (!u || !U)) return IB_ERR_INVALID_ARG;
+  if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = prepare(p, npts, X, flags, s);
+  if (st != IB_OK) return st;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.one.u = u;
+  J.one.U = U;
+  J.njobs = 1;
+  if (launch_interp(J, p->sh, call_bins(p, npts), p->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  return IB_OK;
+}
+
+ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* field, const void* v, double scale,
+                      void* D, unsigned flags, void* stream) {
+  ib_status st = check_call(p, npts, X);
+  if (st != IB_OK) return st;
+  if (npts > 0 && (!field || !v || !D)) return IB_ERR_INVALID_ARG;
+  if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
+  if (!isfinite(scale)) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = prepare(p, npts, X, flags, s);
+  if (st != IB_OK) return st;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.njobs = 1;
+  if (launch_pos_grad(J, p->sh, call_bins(p, npts), p->desc.dtype, field, v, scale, D, s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  return IB_OK;
+}
+
+ib_status ib_advect(ib_plan p, long long npts, const void* X, const void* U, double dt, void* Xout,
+                    void* stream) {
+  ib_status st = check_call(p, npts, X);
+  if (st != IB_OK) return st;
+  if (p->desc.ncomp != p->desc.dim) return IB_ERR_INVALID_ARG;
+  if (npts > 0 && (!U || !Xout)) return IB_ERR_INVALID_ARG;
+  if (!isfinite(dt)) return IB_ERR_INVALID_ARG;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.njobs = 1;
+  if (launch_advect(J, p->sh, p->desc.dtype, U, dt, Xout, (cudaStream_t)stream) != cudaSuccess) return IB_ERR_CUDA;
+  if (Xout == X) p->binned = false;  // positions changed in place: the bins no longer describe X
+  return IB_OK;
+}
+
+ib_status ib_plan_check(ib_plan p, void* stream) {
+  if (!p) return IB_ERR_INVALID_ARG;
+  return check_error_word(p->bins.err, (cudaStream_t)stream);
+}
+
+ib_status ib_plan_bins(ib_plan p, const void** perm, const void** cell_start, long long* ncell, long long* npts) {
+  if (!p) return IB_ERR_INVALID_ARG;
+  if (perm) *perm = p->bins.perm;
+  if (cell_start) *cell_start = p->bins.count;
+  if (ncell) *ncell = p->job.ncell;
+  if (npts) *npts = p->binned ? p->binned_n : -1;
+  return IB_OK;
+}
+
+// ----------------------------------------------------------------- batches --
+
+static bool batch_sizes(const ib_batch_desc* d, int* tile, Layout* L) {
+  if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
+  if (d->flags != 0 || d->max_jobs < 1 || d->max_points < 0 || d->max_points > kMaxPointsTotal) return false;
+  if (d->max_cells < 1 || d->max_cells > kMaxCellsTotal || d->max_tiles < 0) return false;
+  const int t = spread_tile_side(d->dim, entry_bytes(d->dtype, false), d->ncomp);
+  const size_t boxes = (size_t)d->max_tiles * box_bytes(d->dim, t, entry_bytes(d->dtype, false), d->ncomp);
+  if (tile) *tile = t;
+  if (L) *L = make_layout(d->max_cells, d->max_points, boxes, sizeof(Job) * (size_t)d->max_jobs);
+  return true;
+}
+
+ib_status ib_batch_footprint(const ib_batch_desc* desc, size_t* bytes) {
+  Layout L;
+  if (!bytes || !batch_sizes(desc, nullptr, &L)) return IB_ERR_INVALID_ARG;
+  *bytes = L.total;
+  return IB_OK;
+}
+
+ib_status ib_batch_job_footprint(const ib_batch_desc* desc, const ib_job* job, size_t* bytes, long long* tiles) {
+  int tile = 0;
+  if (!job || !batch_sizes(desc, &tile, nullptr)) return IB_ERR_INVALID_ARG;
+  Job jb;
+  if (job->npts < 0 || !fill_job(jb, desc->dim, job->n, job->L, tile)) return IB_ERR_INVALID_ARG;
+  const size_t b = sizeof(uint32_t) * (size_t)(jb.ncell + 4 * job->npts) +
+                   (size_t)jb.ntiles * box_bytes(desc->dim, tile, entry_bytes(desc->dtype, false), desc->ncomp);
+  if (bytes) *bytes = b;
+  if (tiles) *tiles = jb.ntiles;
+  return IB_OK;
+}
+
+ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out) {
+  if (!out) return IB_ERR_INVALID_ARG;
+  *out = nullptr;
+  ib_batch b = new (std::nothrow) ib_batch_s;
+  if (!b) return IB_ERR_OOM;
+  memset(b, 0, sizeof(*b));
+  if (!batch_sizes(desc, &b->tile, &b->layout)) {
+    delete b;
+    return IB_ERR_INVALID_ARG;
+  }
+  b->desc = *desc;
+  b->sh.dim = desc->dim;
+  b->sh.ncomp = desc->ncomp;
+  b->sh.mac = desc->grid == IB_GRID_MAC ? 1 : 0;
+  b->sh.kernel = desc->kernel;
+  if (cudaMalloc(&b->arena, b->layout.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return IB_ERR_OOM;
+  }
+  if (cudaMallocHost((void**)&b->h_stage, sizeof(Job) * (size_t)desc->max_jobs) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->arena);
+    delete b;
+    return IB_ERR_OOM;
+  }
+  if (cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFreeHost(b->h_stage);
+    cudaFree(b->arena);
+    delete b;
+    return IB_ERR_CUDA;
+  }
+  b->bins = carve((char*)b->arena, b->layout);
+  b->boxes = (char*)b->arena + b->layout.boxes;
+  b->d_table = (Job*)((char*)b->arena + b->layout.table);
+  cudaMemset(b->bins.err, 0, sizeof(uint32_t));
+  *out = b;
+  return IB_OK;
+}
+
+ib_status ib_batch_destroy(ib_batch b) {
+  if (!b) return IB_OK;
+  cudaDeviceSynchronize();
+  cudaEventDestroy(b->uploaded);
+  cudaFreeHost(b->h_stage);
+  cudaFree(b->arena);
+  delete b;
+  return IB_OK;
+}
+
+ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags, void* stream) {
+  if (!b || njobs < 0 || (njobs > 0 && !jobs)) return IB_ERR_INVALID_ARG;
+  if (njobs > b->desc.max_jobs) return IB_ERR_CAPACITY;
+  if (flags != 0) return IB_ERR_INVALID_ARG;
+  if (njobs == 0) return IB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  // The staging buffer still feeds the previous upload until that copy ran.
+  if (b->pending) {
+    if (cudaEventSynchronize(b->uploaded) != cudaSuccess) return IB_ERR_CUDA;
+    b->pending = false;
+  }
+  long long cells = 0, pts = 0, tiles = 0;
+  for (int i = 0; i < njobs; ++i) {
+    const ib_job& in = jobs[i];
+    Job& jb = b->h_stage[i];
+    if (in.npts < 0 || !fill_job(jb, b->desc.dim, in.n, in.L, b->tile)) return IB_ERR_INVALID_ARG;
+    if (in.npts > 0 && !in.X) return IB_ERR_INVALID_ARG;
+    if (in.G && (!in.f || (in.npts > 0 && !in.G))) return IB_ERR_INVALID_ARG;
+    if (in.u && (in.npts > 0 && !in.U)) return IB_ERR_INVALID_ARG;
+    jb.cell_base = cells;
+    jb.pt_base = pts;
+    jb.tile_base = tiles;
+    jb.npts = in.npts;
+    jb.X = in.X;
+    jb.G = in.G;
+    jb.f = in.f;
+    jb.u = in.u;
+    jb.U = in.U;
+    cells += jb.ncell;
+    pts += in.npts;
+    tiles += jb.ntiles;
+    if (cells > b->desc.max_cells || pts > b->desc.max_points || tiles > b->desc.max_tiles) return IB_ERR_CAPACITY;
+  }
+  if (cudaMemcpyAsync(b->d_table, b->h_stage, sizeof(Job) * (size_t)njobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  if (cudaEventRecord(b->uploaded, s) != cudaSuccess) return IB_ERR_CUDA;
+  b->pending = true;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.table = b->d_table;
+  J.njobs = njobs;
+  Bins B = b->bins;
+  B.ncell_total = cells;
+  B.npts_total = pts;
+  if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(cells + 2), s) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_bin(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  if (launch_interp(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  return IB_OK;
+}
+
+ib_status ib_batch_check(ib_batch b, void* stream) {
+  if (!b) return IB_ERR_INVALID_ARG;
+  return check_error_word(b->bins.err, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// ib_bin.cu -- binning of Lagrangian points by Eulerian cell: the key
+// computation, key-value sort and unique-key offsets of Algorithm 4 (Section
+// 3.4, Fig. 2), as a stable counting sort over cells.
+//
+//   1. k_bin_count   per point: exact cell of xi = 0, key = c_x + n0 (c_y + n1 c_z)
+//                    (plus the job's cell base), atomic per-cell count; the
+//                    value returned by the atomic is the point's arrival rank.
+//   2. scan          exclusive prefix of the counts -> cell_start.
+//   3. k_bin_scatter perm_tmp[cell_start[key] + rank] = point (any order in a cell).
+//   4. k_bin_stable  perm[cell_start[key] + #(same-cell points with a smaller
+//                    index)] = point: ties keep index order, as in Fig. 2
+//                    where X3 precedes X5 in cell 5.
+// Invalid points (non-finite or out of range) get the sentinel cell
+// ncell_total and end up after every valid point.
+#include "ib_internal.h"
+
+namespace ibgb {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B) {
+  const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (g >= B.npts_total) return;
+  const Job& jb = job_at(J, job_of_point(J, g));
+  const T* X = (const T*)jb.X + (g - jb.pt_base) * D;
+  uint32_t err = 0;
+  long long key = 0, stride = 1;
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    Cell1<T> c;
+    err |= point_cell<T>(X[b], jb, b, c);
+    const int n = jb.n[b];
+    const int cb = ((unsigned)c.i0 < (unsigned)n) ? c.i0 : modn(c.i0, n);
+    key += (long long)cb * stride;
+    stride *= n;
+  }
+  uint32_t k;
+  if (err) {
+    atomicOr(B.err, err);
+    k = (uint32_t)B.ncell_total;
+  } else {
+    k = (uint32_t)(jb.cell_base + key);
+  }
+  B.key[g] = k;
+  B.rank[g] = atomicAdd(&B.count[k], 1u);
+}
+
+// Block-level exclusive scan of per-thread totals; returns this thread's
+// exclusive offset and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = (lane < kScanThreads / 32) ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;  // inclusive over warps
+  }
+  __syncthreads();
+  const uint32_t before = (warp > 0) ? warp_tot[warp - 1] : 0u;
+  *total = warp_tot[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ a, long long m,
+                                                               uint32_t* __restrict__ sums) {
+  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < m) s += a[base + i];
+  uint32_t tot;
+  block_exclusive(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// One block: exclusive scan of the block sums in place; sums[nb] = grand total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t* __restrict__ sums, long long nb) {
+  uint32_t carry = 0;
+  for (long long base = 0; base < nb; base += kScanChunk) {
+    const long long i0 = base + (long long)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      v[i] = (i0 + i < nb) ? sums[i0 + i] : 0u;
+      s += v[i];
+    }
+    uint32_t tot;
+    uint32_t off = carry + block_exclusive(s, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      if (i0 + i < nb) sums[i0 + i] = off;
+      off += v[i];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restrict__ a, long long m,
+                                                              const uint32_t* __restrict__ sums, long long nb) {
+  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < m) ? a[base + i] : 0u;
+    s += v[i];
+  }
+  uint32_t tot;
+  uint32_t off = sums[blockIdx.x] + block_exclusive(s, &tot);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < m) a[base + i] = off;
+    off += v[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a[m] = sums[nb];
+}
+
+__global__ void __launch_bounds__(kThreads) k_bin_scatter(const Bins B) {
+  const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (g >= B.npts_total) return;
+  const uint32_t k = B.key[g];
+  B.perm_tmp[B.count[k] + B.rank[g]] = (uint32_t)g;
+}
+
+// Stable order inside a cell: the rank of point g among the points of its
+// cell is the number of them with a smaller index.  O(cell size) per point;
+// cells hold a handful of points in every workload of interest, and the
+// cost stays bounded (quadratic in the largest cell) for adversarial input.
+__global__ void __launch_bounds__(kThreads) k_bin_stable(const Bins B) {
+  const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (g >= B.npts_total) return;
+  const uint32_t k = B.key[g];
+  const uint32_t s = B.count[k];
+  const uint32_t e = B.count[k + 1];
+  uint32_t r = 0;
+  if (e - s > 1) {
+    const uint32_t me = (uint32_t)g;
+    for (uint32_t q = s; q < e; ++q) r += (B.perm_tmp[q] < me) ? 1u : 0u;
+  }
+  B.perm[s + r] = (uint32_t)g;
+}
+
+inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+long long scan_blocks(long long m) { return (m + kScanChunk - 1) / kScanChunk; }
+
+cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s) {
+  const long long n = B.npts_total;
+  if (n > 0) {
+    if (dtype == 0) {
+      if (sh.dim == 3) k_bin_count<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
+      else k_bin_count<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
+    } else {
+      if (sh.dim == 3) k_bin_count<double, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
+      else k_bin_count<double, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
+    }
+  }
+  const long long m = B.ncell_total + 1;  // cells plus the sentinel; count[m] receives the total
+  const long long nb = scan_blocks(m);
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.block_sums);
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(B.block_sums, nb);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.block_sums, nb);
+  if (n > 0) {
+    k_bin_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);
+    k_bin_stable<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ibgb

@@ -1,0 +1,303 @@
+// ib_common.cuh -- device-side types and helpers shared by the kernels of the
+// GB300 immersed-boundary coupling library (arXiv 2012.06646).
+//
+// A "job" is one independent problem: a periodic grid, a point set and its
+// fields.  A single-job call passes its job by value in the kernel parameter
+// block; a batched wave passes a device table of jobs.  Every global array of
+// the scratch arena is indexed by a global point index (job.pt_base + local),
+// a global cell id (job.cell_base + local key) or a global tile id
+// (job.tile_base + local tile), so one launch covers every job of a wave.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ibgb {
+
+constexpr uint32_t ERR_NONFINITE = 1u;
+constexpr uint32_t ERR_RANGE = 2u;
+
+// Positions are accepted while |X_b N_b / L_b| < 2^30 (cell indices fit in int).
+constexpr double kMaxCells = 1073741824.0;
+
+struct Job {
+  int n[3];              // grid points per dimension (n[2] = 1 in 2-D)
+  int ntile[3];          // spreading tiles per dimension (ntile[2] = 1 in 2-D)
+  int sS[3], sE[3];      // scale_b = sS_b * 2^sE_b exactly when sS_b > 0 ("short" scale)
+  double scale[3];       // N_b / L_b, computed on the host as (double)N_b / L_b
+  double hmd;            // h^-d = prod_b scale_b
+  float Lf[3];           // box side per dimension (FP32, for the position update)
+  double Ld[3];          // box side per dimension (FP64)
+  long long cell_base;   // first global cell id of this job
+  long long ncell;       // n0 n1 n2
+  long long pt_base;     // first global point index of this job
+  long long npts;
+  long long tile_base;   // first global tile id of this job
+  long long ntiles;
+  const void* X;         // (npts, dim)
+  const void* G;         // (npts, ncomp) spread input
+  void* f;               // [ncomp][grid] spread output
+  const void* u;         // [ncomp][grid] interpolation input
+  void* U;               // (npts, ncomp) interpolation output
+};
+
+struct Jobs {
+  const Job* table;      // device table of njobs jobs, or nullptr for a single job
+  Job one;               // the job when table == nullptr
+  int njobs;
+};
+
+// Static description shared by all jobs of a launch.
+struct Shape {
+  int dim;               // 2 or 3
+  int ncomp;             // components per field
+  int mac;               // 1: MAC staggering, 0: cell-centred
+  int kernel;            // 0: standard 4-point, 1: cosine 4-point
+};
+
+// Scratch arena views (global arrays over all jobs of a wave).
+struct Bins {
+  uint32_t* count;       // [ncell_total + 2]: per-cell counts, then exclusive prefix (cell_start)
+  uint32_t* key;         // [npts_total]: global cell id of each point (ncell_total = invalid point)
+  uint32_t* rank;        // [npts_total]: arrival rank of the point inside its cell
+  uint32_t* perm_tmp;    // [npts_total]: points in cell order, arbitrary order inside a cell
+  uint32_t* perm;        // [npts_total]: points in cell order, index order inside a cell (stable)
+  uint32_t* block_sums;  // scan scratch
+  uint32_t* err;         // device error word
+  long long ncell_total;
+  long long npts_total;
+};
+
+__device__ __forceinline__ const Job& job_at(const Jobs& J, int j) {
+  return J.table ? J.table[j] : J.one;
+}
+
+// Largest job index j with field(j) <= v, for a field that is non-decreasing in j.
+#define IBGB_JOB_SEARCH(NAME, FIELD)                                        \
+  __device__ __forceinline__ int NAME(const Jobs& J, long long v) {         \
+    if (!J.table) return 0;                                                 \
+    int lo = 0, hi = J.njobs - 1;                                           \
+    while (lo < hi) {                                                       \
+      int mid = (lo + hi + 1) >> 1;                                         \
+      if (J.table[mid].FIELD <= v) lo = mid; else hi = mid - 1;             \
+    }                                                                       \
+    return lo;                                                              \
+  }
+IBGB_JOB_SEARCH(job_of_point, pt_base)
+IBGB_JOB_SEARCH(job_of_cell, cell_base)
+IBGB_JOB_SEARCH(job_of_tile, tile_base)
+#undef IBGB_JOB_SEARCH
+
+// ---------------------------------------------------------------------------
+// Cell map (Section 3.1, Fig. 1a): for staggering xi, i = floor(X (N/L) - xi)
+// and r = X (N/L) - xi - i.  The integer i must equal the FP64 evaluation of
+// that formula (two rounded operations, no fused multiply-add).  Only the
+// staggerings xi = 0 and xi = 1/2 occur (MAC and cell-centred grids).
+// ---------------------------------------------------------------------------
+
+template <typename R>
+struct Cell1 {
+  int i0, i1;   // cells for xi = 0 and xi = 1/2 (unwrapped)
+  R r0, r1;     // offsets in [0, 1] (1 only through rounding of r -> 1-)
+};
+
+// FP32 position with a short scale (scale = S 2^E, 0 < S < 2^24).  X (N/L) is
+// then exact in FP64, so floor(X (N/L)) and floor(X (N/L) - 1/2) are plain
+// integer questions; this evaluates them exactly with 64-bit integers, giving
+// the FP64 result without the GPU's FP64 pipe.  |u| = P 2^e with P < 2^48.
+__device__ __forceinline__ float pow2_neg(int k) {  // 2^-k, 1 <= k <= 126
+  return __int_as_float((127 - k) << 23);
+}
+
+__device__ __forceinline__ uint32_t cell_short(float X, int S, int E, Cell1<float>& c) {
+  const uint32_t bits = __float_as_uint(X);
+  const uint32_t ex = (bits >> 23) & 0xffu;
+  if (ex == 0xffu) return ERR_NONFINITE;
+  uint64_t M = bits & 0x7fffffu;
+  int e;
+  if (ex == 0u) {
+    e = -149 + E;
+  } else {
+    M |= 0x800000u;
+    e = (int)ex - 150 + E;
+  }
+  const uint64_t P = M * (uint64_t)S;
+  const bool neg = (bits >> 31) != 0u;
+  if (P == 0) {  // X = +-0
+    c.i0 = 0; c.r0 = 0.f; c.i1 = -1; c.r1 = 0.5f;
+    return 0;
+  }
+  if (e >= 0) {  // u is an integer
+    if (e >= 30 || (P >> (30 - e)) != 0) return ERR_RANGE;
+    const int ip = (int)(P << e);
+    c.i0 = neg ? -ip : ip; c.r0 = 0.f; c.i1 = c.i0 - 1; c.r1 = 0.5f;
+    return 0;
+  }
+  const int k = -e;
+  if (k >= 64) {  // |u| < 2^-16
+    const float t = ldexpf(__ull2float_rn(P), -k);
+    if (!neg) { c.i0 = 0; c.r0 = t; c.i1 = -1; c.r1 = 0.5f + t; }
+    else      { c.i0 = -1; c.r0 = 1.f - t; c.i1 = -1; c.r1 = 0.5f - t; }
+    return 0;
+  }
+  const uint64_t ip = P >> k;
+  if (ip >= (1ull << 30)) return ERR_RANGE;
+  uint64_t F = P & ((1ull << k) - 1ull);   // fractional part numerator over 2^k
+  long long i0;
+  if (!neg) {
+    i0 = (long long)ip;
+  } else if (F == 0) {
+    i0 = -(long long)ip;
+  } else {
+    i0 = -(long long)ip - 1;
+    F = (1ull << k) - F;
+  }
+  const uint64_t half = 1ull << (k - 1);
+  long long i1;
+  uint64_t F1;
+  if (F >= half) { i1 = i0; F1 = F - half; } else { i1 = i0 - 1; F1 = F + half; }
+  c.i0 = (int)i0;
+  c.i1 = (int)i1;
+  c.r0 = __ull2float_rn(F) * pow2_neg(k);
+  c.r1 = __ull2float_rn(F1) * pow2_neg(k);
+  return 0;
+}
+
+// FP64 evaluation, the oracle's formula literally (u = X * scale; u - xi).
+template <typename R>
+__device__ __forceinline__ uint32_t cell_fp64(double X, double scale, Cell1<R>& c) {
+  if (!isfinite(X)) return ERR_NONFINITE;
+  const double u = __dmul_rn(X, scale);
+  if (!(fabs(u) < kMaxCells)) return ERR_RANGE;
+  const double f0 = floor(u);
+  const double v = __dsub_rn(u, 0.5);
+  const double f1 = floor(v);
+  c.i0 = (int)f0;
+  c.i1 = (int)f1;
+  c.r0 = (R)__dsub_rn(u, f0);
+  c.r1 = (R)__dsub_rn(v, f1);
+  return 0;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t point_cell(T X, const Job& jb, int b, Cell1<T>& c);
+
+template <>
+__device__ __forceinline__ uint32_t point_cell<float>(float X, const Job& jb, int b, Cell1<float>& c) {
+  if (jb.sS[b] > 0) return cell_short(X, jb.sS[b], jb.sE[b], c);
+  return cell_fp64<float>((double)X, jb.scale[b], c);
+}
+
+template <>
+__device__ __forceinline__ uint32_t point_cell<double>(double X, const Job& jb, int b, Cell1<double>& c) {
+  return cell_fp64<double>(X, jb.scale[b], c);
+}
+
+// Periodic wrap of v into [0, n) for v in [-2n, 3n).
+__device__ __forceinline__ int wrapn(int v, int n) {
+  if (v < 0) v += n;
+  if (v < 0) v += n;
+  if (v >= n) v -= n;
+  if (v >= n) v -= n;
+  return v;
+}
+
+// Positive modulo for arbitrary v (|v| < 2^30).
+__device__ __forceinline__ int modn(int v, int n) {
+  int m = v % n;
+  return m < 0 ? m + n : m;
+}
+
+// ---------------------------------------------------------------------------
+// Weights w[t+1] = phi(t - r), t in {-1, 0, 1, 2}, r in [0, 1] (Eq. delta-defs).
+// Standard 4-point kernel: with q = sqrt(1 + 4 r (1 - r)),
+//   phi(-1-r) = (3-2r-q)/8, phi(-r) = (3-2r+q)/8, phi(1-r) = (1+2r+q)/8,
+//   phi(2-r) = (1+2r-q)/8,
+// and the two small ones rewritten without cancellation:
+//   (3-2r-q)/8 = (1-r)^2/(3-2r+q),  (1+2r-q)/8 = r^2/(1+2r+q).
+// Cosine kernel phi(x) = cos(pi x/4)^2 / 2: with (s1,c1) = sincospi(r/4) and
+// (s2,c2) = sincospi((1-r)/4) the four weights are s2^2/2, c1^2/2, c2^2/2, s1^2/2.
+// dw[t+1] = d phi(t - r) / d r, used by the position gradients.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void weights(int kernel, float r, float w[4]) {
+  if (kernel == 0) {
+    const float q = sqrtf(fmaf(4.f * r, 1.f - r, 1.f));
+    const float a = 3.f - 2.f * r + q;
+    const float b = 1.f + 2.f * r + q;
+    const float om = 1.f - r;
+    w[0] = om * om / a;
+    w[1] = 0.125f * a;
+    w[2] = 0.125f * b;
+    w[3] = r * r / b;
+  } else {
+    float s1, c1, s2, c2;
+    sincospif(0.25f * r, &s1, &c1);
+    sincospif(0.25f * (1.f - r), &s2, &c2);
+    w[0] = 0.5f * s2 * s2;
+    w[1] = 0.5f * c1 * c1;
+    w[2] = 0.5f * c2 * c2;
+    w[3] = 0.5f * s1 * s1;
+  }
+}
+
+__device__ __forceinline__ void weights(int kernel, double r, double w[4]) {
+  if (kernel == 0) {
+    const double q = sqrt(fma(4.0 * r, 1.0 - r, 1.0));
+    const double a = 3.0 - 2.0 * r + q;
+    const double b = 1.0 + 2.0 * r + q;
+    const double om = 1.0 - r;
+    w[0] = om * om / a;
+    w[1] = 0.125 * a;
+    w[2] = 0.125 * b;
+    w[3] = r * r / b;
+  } else {
+    double s1, c1, s2, c2;
+    sincospi(0.25 * r, &s1, &c1);
+    sincospi(0.25 * (1.0 - r), &s2, &c2);
+    w[0] = 0.5 * s2 * s2;
+    w[1] = 0.5 * c1 * c1;
+    w[2] = 0.5 * c2 * c2;
+    w[3] = 0.5 * s1 * s1;
+  }
+}
+
+__device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float mfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ void msincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void msincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+
+template <typename R>
+__device__ __forceinline__ void weights_and_derivs(int kernel, R r, R w[4], R dw[4]) {
+  weights(kernel, r, w);
+  if (kernel == 0) {
+    const R q = msqrt(mfma((R)4 * r, (R)1 - r, (R)1));
+    const R qp = ((R)2 - (R)4 * r) / q;
+    dw[0] = (R)0.125 * (-(R)2 - qp);
+    dw[1] = (R)0.125 * (-(R)2 + qp);
+    dw[2] = (R)0.125 * ((R)2 + qp);
+    dw[3] = (R)0.125 * ((R)2 - qp);
+  } else {
+    R s1, c1, s2, c2;
+    msincospi((R)0.25 * r, &s1, &c1);
+    msincospi((R)0.25 * ((R)1 - r), &s2, &c2);
+    const R k = (R)0.78539816339744830962;  // pi / 4
+    dw[0] = -k * s2 * c2;
+    dw[1] = -k * s1 * c1;
+    dw[2] = k * s2 * c2;
+    dw[3] = k * s1 * c1;
+  }
+}
+
+// Staggering of component a in dimension b: 1 means xi = 1/2, 0 means xi = 0.
+__device__ __forceinline__ int half_stag(const Shape& s, int a, int b) {
+  return s.mac ? (a != b) : 1;
+}
+
+template <typename T> struct Acc;            // accumulation type for node sums
+template <> struct Acc<float> { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+}  // namespace ibgb

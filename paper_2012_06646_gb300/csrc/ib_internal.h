@@ -1,0 +1,38 @@
+// ib_internal.h -- host-side launch interface between the C ABI (ib_api.cu)
+// and the kernel translation units (ib_bin.cu, ib_ops.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ib_common.cuh"
+
+namespace ibgb {
+
+// Tile side of the spreading boxes for a plan: 16 in 3-D when the box
+// (side + 4)^3 of every component fits in shared memory, else 8; 32 in 2-D.
+int spread_tile_side(int dim, int entry_bytes, int ncomp);
+
+// Bytes of one spreading box (all components) for a tile side.
+size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp);
+
+// Number of blocks of the cell-count scan for m entries.
+long long scan_blocks(long long m);
+
+// Binning (Algorithm 4 keys, sort and unique-key offsets): count, scan,
+// scatter and stable fix-up.  B.count must be zeroed by the caller.
+cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s);
+
+// Spreading in two launches: per-tile boxes in shared memory written to
+// `boxes`, then the fixed-order combination of overlapping boxes into f.
+cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles_total,
+                          int tile, int dtype, bool compensated, bool accumulate, cudaStream_t s);
+
+cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s);
+
+cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,
+                            const void* v, double scale, void* D, cudaStream_t s);
+
+cudaError_t launch_advect(const Jobs& J, const Shape& sh, int dtype, const void* U, double dt, void* Xout,
+                          cudaStream_t s);
+
+}  // namespace ibgb

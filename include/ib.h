@@ -76,6 +76,10 @@ enum { IB_F32 = 0, IB_F64 = 1 };
 #define IB_ACCUMULATE   0x1u   /* spread: f += S G (the paper's l_k <- l_k + w L_i), instead of f = S G */
 #define IB_COMPENSATED  0x2u   /* spread: node sums carried as TwoSum (value, error) pairs */
 #define IB_REUSE_BINS   0x4u   /* skip binning: reuse the bins of the last ib_bin call (same X, same npts) */
+#define IB_ADJOINT      0x8u   /* the transpose of the other operator in the plain (unweighted) inner product:
+                                  ib_spread computes sum_j W_kj G_j (no h^-d), the adjoint of interpolation;
+                                  ib_interpolate computes h^-d sum_k W_kj u_k, the adjoint of spreading
+                                  (W_kj = prod_b phi(t_b - r_b); Eqs. matrix-interp, matrix-spread: S* = S^T) */
 
 typedef struct ib_plan_s* ib_plan;
 

@@ -35,6 +35,7 @@ IB_PLAN_COMPENSATED = 0x1
 IB_ACCUMULATE = 0x1
 IB_COMPENSATED = 0x2
 IB_REUSE_BINS = 0x4
+IB_ADJOINT = 0x8
 
 
 class ib_plan_desc(ctypes.Structure):

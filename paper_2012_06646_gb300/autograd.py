@@ -1,0 +1,77 @@
+"""Differentiable spreading and interpolation (torch.autograd.Function).
+
+With W_jk = prod_b phi(t_b - r_b) the weight of point j at node k,
+spreading is f = h^-d W^T G and interpolation is U = W u (Eqs. disc-spread,
+disc-interp; S* = S^T, Eqs. matrix-interp and matrix-spread).  Hence
+
+  spread:       dL/dG = h^-d W (dL/df)      -> ib_interpolate with IB_ADJOINT
+                dL/dX = h^-d D(dL/df, G)    -> ib_pos_grad, scale = h^-d
+  interpolate:  dL/du = W^T (dL/dU)         -> ib_spread with IB_ADJOINT
+                dL/dX = D(u, dL/dU)         -> ib_pos_grad, scale = 1
+
+where D(field, v)_{j,b} = sum_a v_{j,a} sum_k field_a[k] dW_jk/dX_{j,b}, the
+position derivative of the weights.  Every backward step runs in the CUDA
+kernels of libibgb.so.
+"""
+
+from __future__ import annotations
+
+import torch
+
+from .plan import Plan
+
+
+class SpreadFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, G, plan: Plan, compensated: bool = False):
+        f = plan.spread(X.detach().contiguous(), G.detach().contiguous(), compensated=compensated)
+        ctx.plan = plan
+        ctx.save_for_backward(X, G)
+        return f
+
+    @staticmethod
+    def backward(ctx, gf):
+        X, G = ctx.saved_tensors
+        plan = ctx.plan
+        gf = gf.contiguous()
+        Xc = X.detach().contiguous()
+        gX = gG = None
+        plan.bin(Xc)
+        if ctx.needs_input_grad[1]:
+            gG = plan.interpolate(Xc, gf, reuse_bins=True, adjoint=True)
+        if ctx.needs_input_grad[0]:
+            gX = plan.pos_grad(Xc, gf, G.detach().contiguous(), scale=plan.hmd, reuse_bins=True)
+        return gX, gG, None, None
+
+
+class InterpolateFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, u, plan: Plan):
+        U = plan.interpolate(X.detach().contiguous(), u.detach().contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(X, u)
+        return U
+
+    @staticmethod
+    def backward(ctx, gU):
+        X, u = ctx.saved_tensors
+        plan = ctx.plan
+        gU = gU.contiguous()
+        Xc = X.detach().contiguous()
+        gX = gu = None
+        plan.bin(Xc)
+        if ctx.needs_input_grad[1]:
+            gu = plan.spread(Xc, gU, reuse_bins=True, adjoint=True)
+        if ctx.needs_input_grad[0]:
+            gX = plan.pos_grad(Xc, u.detach().contiguous(), gU, scale=1.0, reuse_bins=True)
+        return gX, gu, None
+
+
+def spread(X, G, plan: Plan, compensated: bool = False):
+    """Differentiable f = S G on the plan's grid."""
+    return SpreadFunction.apply(X, G, plan, compensated)
+
+
+def interpolate(X, u, plan: Plan):
+    """Differentiable U = S* u at the points X."""
+    return InterpolateFunction.apply(X, u, plan)

@@ -313,7 +313,7 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
-  if (flags & ~(IB_ACCUMULATE | IB_COMPENSATED | IB_REUSE_BINS)) return IB_ERR_INVALID_ARG;
+  if (flags & ~(IB_ACCUMULATE | IB_COMPENSATED | IB_REUSE_BINS | IB_ADJOINT)) return IB_ERR_INVALID_ARG;
   const bool comp = (flags & IB_COMPENSATED) != 0;
   if (comp && !(p->desc.flags & IB_PLAN_COMPENSATED)) return IB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -328,6 +328,7 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   J.one.X = X;
   J.one.G = G ? G : f;  // npts == 0: any non-null marker; no point is read
   J.one.f = f;
+  if (flags & IB_ADJOINT) J.one.hmd = 1.0;
   J.njobs = 1;
   if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp,
                     (flags & IB_ACCUMULATE) != 0, s) != cudaSuccess)
@@ -340,7 +341,7 @@ ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (npts > 0 && (!u || !U)) return IB_ERR_INVALID_ARG;
-  if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
+  if (flags & ~(IB_REUSE_BINS | IB_ADJOINT)) return IB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare(p, npts, X, flags, s);
   if (st != IB_OK) return st;
@@ -352,7 +353,8 @@ ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u
   J.one.u = u;
   J.one.U = U;
   J.njobs = 1;
-  if (launch_interp(J, p->sh, call_bins(p, npts), p->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  const double scale = (flags & IB_ADJOINT) ? p->job.hmd : 1.0;
+  if (launch_interp(J, p->sh, call_bins(p, npts), p->desc.dtype, scale, s) != cudaSuccess) return IB_ERR_CUDA;
   return IB_OK;
 }
 
@@ -539,7 +541,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
   if (launch_bin(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, s) != cudaSuccess)
     return IB_ERR_CUDA;
-  if (launch_interp(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_interp(J, b->sh, B, b->desc.dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
   return IB_OK;
 }
 

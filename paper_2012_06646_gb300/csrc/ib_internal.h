@@ -27,7 +27,8 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles_total,
                           int tile, int dtype, bool compensated, bool accumulate, cudaStream_t s);
 
-cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s);
+// Interpolation; every value is multiplied by `scale` (1 for plain interpolation).
+cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, int dtype, double scale, cudaStream_t s);
 
 cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,
                             const void* v, double scale, void* D, cudaStream_t s);

@@ -422,7 +422,8 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kThreads) k_interp(const __grid_constant__ Jobs J, const Shape sh, const Bins B) {
+__global__ void __launch_bounds__(kThreads) k_interp(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
+                                                     const T scale) {
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= B.npts_total) return;
   const uint32_t g = B.perm[p];
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(kThreads) k_interp(const __grid_constant__ Job
       }
       acc += wz[tz] * accy;
     }
-    U[a] = acc;
+    U[a] = acc * scale;
   }
 }
 
@@ -647,15 +648,15 @@ cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* b
   return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, s);
 }
 
-cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s) {
+cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, int dtype, double scale, cudaStream_t s) {
   const long long n = B.npts_total;
   if (n == 0) return cudaSuccess;
   if (dtype == 0) {
-    if (sh.dim == 3) k_interp<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B);
-    else k_interp<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B);
+    if (sh.dim == 3) k_interp<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, (float)scale);
+    else k_interp<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, (float)scale);
   } else {
-    if (sh.dim == 3) k_interp<double, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B);
-    else k_interp<double, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B);
+    if (sh.dim == 3) k_interp<double, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, scale);
+    else k_interp<double, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, scale);
   }
   return cudaGetLastError();
 }

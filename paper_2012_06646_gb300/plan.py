@@ -32,7 +32,7 @@ class _DeviceArray:
     """Zero-copy view of library-owned device memory through __cuda_array_interface__."""
 
     def __init__(self, ptr: int, n: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True), "version": 3}
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
 
 
 class Plan:
@@ -101,24 +101,25 @@ class Plan:
         n = self._points(X)
         check(self.lib.ib_bin(self.handle, n, _ptr(X), _stream_ptr(stream)), "ib_bin")
 
-    def spread(self, X, G, f=None, accumulate=False, compensated=False, reuse_bins=False, stream=None):
+    def spread(self, X, G, f=None, accumulate=False, compensated=False, reuse_bins=False, adjoint=False,
+               stream=None):
         n = self._points(X)
         self._check(G, (n, self.ncomp), "G")
         if f is None:
             f = self._new(self.grid_shape())
         self._check(f, self.grid_shape(), "f")
         flags = ((_abi.IB_ACCUMULATE if accumulate else 0) | (_abi.IB_COMPENSATED if compensated else 0)
-                 | (_abi.IB_REUSE_BINS if reuse_bins else 0))
+                 | (_abi.IB_REUSE_BINS if reuse_bins else 0) | (_abi.IB_ADJOINT if adjoint else 0))
         check(self.lib.ib_spread(self.handle, n, _ptr(X), _ptr(G), _ptr(f), flags, _stream_ptr(stream)), "ib_spread")
         return f
 
-    def interpolate(self, X, u, U=None, reuse_bins=False, stream=None):
+    def interpolate(self, X, u, U=None, reuse_bins=False, adjoint=False, stream=None):
         n = self._points(X)
         self._check(u, self.grid_shape(), "u")
         if U is None:
             U = self._new((n, self.ncomp))
         self._check(U, (n, self.ncomp), "U")
-        flags = _abi.IB_REUSE_BINS if reuse_bins else 0
+        flags = (_abi.IB_REUSE_BINS if reuse_bins else 0) | (_abi.IB_ADJOINT if adjoint else 0)
         check(self.lib.ib_interpolate(self.handle, n, _ptr(X), _ptr(u), _ptr(U), flags, _stream_ptr(stream)),
               "ib_interpolate")
         return U

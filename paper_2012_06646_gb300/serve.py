@@ -1,0 +1,247 @@
+"""Served form: a persistent request loop with continuous batching.
+
+Each request is one independent job: a periodic 3-D MAC grid of its own size
+and a point set of its own size; the job spreads its forces onto its grid
+and interpolates that grid back to its points (f = S G, U = S* f; the grid
+never leaves the device).  The loop
+
+  * admits waiting requests into a wave whenever one of `nstreams` wave
+    slots is free, as long as the wave fits the slot's batch capacity and
+    the in-flight HBM footprint (I/O buffers + scratch share) fits the
+    budget -- requests that arrive while other waves run on the GPU join
+    the next free slot, so their work overlaps on the device;
+  * runs a wave as one ib_batch_run (a fixed number of launches for any
+    number of jobs), with the job's inputs copied in and U copied out on
+    the slot's stream;
+  * retires a wave when its completion event fires and records each
+    request's latency (completion minus arrival).
+
+`single_job_loop` is the comparison: one ib_spread + ib_interpolate per job.
+A job's result is the same whether it runs alone or in a mix: the batched
+kernels give each job its own bins, tiles and summation order.
+"""
+
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .plan import Batch, Plan
+
+
+@dataclass
+class Request:
+    rid: int
+    N: int
+    X: torch.Tensor                  # (n, 3) float32, pinned host
+    G: torch.Tensor                  # (n, 3) float32, pinned host
+    arrival: float = 0.0             # seconds from the start of serving
+    L: float = 1.0
+    U: torch.Tensor | None = None    # result, pinned host
+    t_admit: float = -1.0
+    t_done: float = -1.0
+
+    @property
+    def npts(self) -> int:
+        return int(self.X.shape[0])
+
+    def io_bytes(self) -> int:
+        return int(self.npts * 3 * 4 * 3 + 3 * self.N ** 3 * 4)
+
+
+@dataclass
+class _Wave:
+    reqs: list
+    bufs: list
+    event: torch.cuda.Event
+    footprint: int
+
+
+@dataclass
+class ServeStats:
+    latencies_ms: list = field(default_factory=list)
+    wall_s: float = 0.0
+    points: int = 0
+    jobs: int = 0
+    waves: int = 0
+    max_inflight_bytes: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        return {"jobs": self.jobs, "waves": self.waves, "wall_s": self.wall_s,
+                "pts_per_s": self.points / self.wall_s if self.wall_s > 0 else None,
+                "jobs_per_s": self.jobs / self.wall_s if self.wall_s > 0 else None,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "max_inflight_bytes": self.max_inflight_bytes}
+
+
+class Server:
+    def __init__(self, nstreams: int = 3, max_jobs: int = 256, max_points: int = 1 << 23,
+                 max_cells: int = 1 << 26, budget_bytes: int | None = None, device=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.nstreams = nstreams
+        self.batches = [Batch(dim=3, grid="mac", max_jobs=max_jobs, max_points=max_points, max_cells=max_cells,
+                              max_tiles=max_cells // 4096 + 8 * max_jobs, device=self.device)
+                        for _ in range(nstreams)]
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(nstreams)]
+        self.cap = (max_jobs, max_points, max_cells)
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            budget_bytes = int(0.5 * free)
+        self.budget = int(budget_bytes)
+
+    def footprint(self, r: Request) -> tuple:
+        job = self.batches[0].job_struct((r.N, r.N, r.N), (r.L, r.L, r.L), r.X)
+        scratch, tiles = self.batches[0].job_footprint(job)
+        return r.io_bytes() + scratch, tiles
+
+    def _launch(self, slot: int, reqs: list, footprint: int) -> _Wave:
+        s = self.streams[slot]
+        bufs, jobs = [], []
+        with torch.cuda.stream(s):
+            for r in reqs:
+                X = torch.empty((r.npts, 3), dtype=torch.float32, device=self.device)
+                G = torch.empty_like(X)
+                U = torch.empty_like(X)
+                f = torch.empty((3, r.N, r.N, r.N), dtype=torch.float32, device=self.device)
+                X.copy_(r.X, non_blocking=True)
+                G.copy_(r.G, non_blocking=True)
+                bufs.append((X, G, U, f))
+                jobs.append(self.batches[slot].job_struct((r.N, r.N, r.N), (r.L, r.L, r.L), X, G=G, f=f, u=f, U=U))
+            self.batches[slot].run(jobs, stream=s)
+            for r, (X, G, U, f) in zip(reqs, bufs):
+                if r.U is None:
+                    r.U = torch.empty((r.npts, 3), dtype=torch.float32).pin_memory()
+                r.U.copy_(U, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return _Wave(reqs=reqs, bufs=bufs, event=ev, footprint=footprint)
+
+    def serve(self, requests: list, realtime: bool = True) -> ServeStats:
+        """Serve `requests` (sorted by arrival).  realtime=False admits everything at t = 0."""
+        stats = StatsAccumulator()
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting: collections.deque = collections.deque()
+        slots: list = [None] * self.nstreams
+        inflight = 0
+        t0 = time.perf_counter()
+        sizes = {}
+        while pending or waiting or any(w is not None for w in slots):
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.popleft())
+            for i, w in enumerate(slots):
+                if w is not None and w.event.query():
+                    tdone = time.perf_counter() - t0
+                    for r in w.reqs:
+                        r.t_done = tdone
+                        stats.add(r)
+                    inflight -= w.footprint
+                    slots[i] = None
+            for i in range(self.nstreams):
+                if slots[i] is not None or not waiting:
+                    continue
+                wave, fp, pts, cells, tiles = [], 0, 0, 0, 0
+                while waiting and len(wave) < self.cap[0]:
+                    r = waiting[0]
+                    if r.rid not in sizes:
+                        sizes[r.rid] = self.footprint(r)
+                    rf, rt = sizes[r.rid]
+                    if (pts + r.npts > self.cap[1] or cells + r.N ** 3 > self.cap[2]
+                            or tiles + rt > self.batches[i].desc.max_tiles
+                            or (inflight + fp + rf > self.budget and (wave or inflight > 0))):
+                        break
+                    waiting.popleft()
+                    r.t_admit = time.perf_counter() - t0
+                    wave.append(r)
+                    fp += rf
+                    pts += r.npts
+                    cells += r.N ** 3
+                    tiles += rt
+                if wave:
+                    slots[i] = self._launch(i, wave, fp)
+                    inflight += fp
+                    stats.waves += 1
+                    stats.max_inflight = max(stats.max_inflight, inflight)
+            if realtime and not waiting and pending and all(w is None for w in slots):
+                delay = pending[0].arrival - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(min(delay, 0.001))
+        torch.cuda.synchronize(self.device)
+        for b in self.batches:
+            b.check()
+        return stats.finish(time.perf_counter() - t0)
+
+    def close(self):
+        for b in self.batches:
+            b.close()
+
+
+class StatsAccumulator:
+    def __init__(self):
+        self.lat = []
+        self.points = 0
+        self.jobs = 0
+        self.waves = 0
+        self.max_inflight = 0
+
+    def add(self, r: Request):
+        self.lat.append(1e3 * (r.t_done - r.arrival))
+        self.points += r.npts
+        self.jobs += 1
+
+    def finish(self, wall: float) -> ServeStats:
+        return ServeStats(latencies_ms=self.lat, wall_s=wall, points=self.points, jobs=self.jobs, waves=self.waves,
+                          max_inflight_bytes=self.max_inflight)
+
+
+def single_job_loop(requests: list, realtime: bool = True, device=None) -> ServeStats:
+    """One job per launch sequence: for each request in arrival order, copy in, ib_spread +
+    ib_interpolate on a plan for its grid size, copy U out, wait."""
+    device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    plans = {}
+    maxn = collections.defaultdict(int)
+    for r in requests:
+        maxn[r.N] = max(maxn[r.N], r.npts)
+    for N, m in maxn.items():
+        plans[N] = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", max_points=m, device=device)
+    stats = StatsAccumulator()
+    s = torch.cuda.Stream(device)
+    order = sorted(requests, key=lambda r: r.arrival)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for r in order:
+            if realtime:
+                while time.perf_counter() - t0 < r.arrival:
+                    pass
+            p = plans[r.N]
+            X = r.X.to(device, non_blocking=True)
+            G = r.G.to(device, non_blocking=True)
+            f = p.spread(X, G, stream=s)
+            U = p.interpolate(X, f, reuse_bins=True, stream=s)
+            if r.U is None:
+                r.U = torch.empty((r.npts, 3), dtype=torch.float32).pin_memory()
+            r.U.copy_(U, non_blocking=True)
+            s.synchronize()
+            r.t_done = time.perf_counter() - t0
+            stats.add(r)
+    for p in plans.values():
+        p.check(s)
+        p.close()
+    return stats.finish(time.perf_counter() - t0)
+
+
+def make_requests(specs, L: float = 1.0, arrivals=None) -> list:
+    """Requests from ib_inputs job specs (positions and N(0,1) forces), pinned host buffers."""
+    import ib_inputs
+    out = []
+    for i, sp in enumerate(specs):
+        X = ib_inputs.job_points(sp, L)
+        G = ib_inputs.normal_array(sp.seed, (sp.npts, 3), purpose="job-G")
+        out.append(Request(rid=i, N=sp.N, X=torch.from_numpy(X).pin_memory(), G=torch.from_numpy(G).pin_memory(),
+                           arrival=float(arrivals[i]) if arrivals is not None else 0.0, L=L))
+    return out

@@ -1,0 +1,83 @@
+"""Served batch: each job's result is the same alone and in a mix; waves of uneven
+jobs match the oracle; the continuous-batching loop completes every request."""
+import numpy as np
+import pytest
+import torch
+
+import ib_inputs
+from _gpu import assert_interp_close, assert_spread_close, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_2012_06646_gb300 import build
+    build()
+    from paper_2012_06646_gb300 import serve
+    from paper_2012_06646_gb300.plan import Batch, Plan
+    return Plan, Batch, serve
+
+
+def _jobs(seed, count, grids=(8, 17, 32, 48), n_lo=50, n_hi=3000):
+    return ib_inputs.job_mix(seed, count, grids=grids, n_lo=n_lo, n_hi=n_hi)
+
+
+def test_batched_wave_equals_single_jobs_and_oracle(mods, orc):
+    Plan, Batch, serve = mods
+    specs = _jobs(5, 12)
+    batch = Batch(dim=3, max_jobs=16, max_points=1 << 16, max_cells=1 << 20)
+    jobs, bufs = [], []
+    for sp in specs:
+        X = ib_inputs.job_points(sp)
+        G = ib_inputs.normal_array(sp.seed, (sp.npts, 3), purpose="job-G")
+        Xd, Gd = dev(X), dev(G)
+        f = torch.empty((3, sp.N, sp.N, sp.N), device="cuda")
+        U = torch.empty_like(Xd)
+        bufs.append((X, G, Xd, Gd, f, U))
+        jobs.append(batch.job_struct((sp.N,) * 3, (1.0,) * 3, Xd, G=Gd, f=f, u=f, U=U))
+    batch.run(jobs)
+    batch.check()
+    for sp, (X, G, Xd, Gd, f, U) in zip(specs, bufs):
+        plan = Plan(3, (sp.N,) * 3, (1.0,) * 3, max_points=sp.npts)
+        f1 = plan.spread(Xd, Gd)
+        U1 = plan.interpolate(Xd, f1, reuse_bins=True)
+        # identical alone and in the mix (same bins, tiles and summation order per job)
+        assert torch.equal(f, f1) and torch.equal(U, U1)
+        g = orc.Grid(dim=3, n=(sp.N,) * 3, L=(1.0,) * 3)
+        f_ref, fabs = orc.spread(g, X, G)
+        assert_spread_close(host(f), f_ref, fabs)
+        U_ref, Uabs = orc.interp(g, X, host(f).astype(np.float64))
+        assert_interp_close(host(U), U_ref, Uabs)
+        plan.close()
+
+
+def test_server_continuous_batching_matches_single_loop(mods):
+    Plan, Batch, serve = mods
+    specs = _jobs(9, 60)
+    arrivals = ib_inputs.poisson_arrivals(9, len(specs), rate_per_s=4000.0)
+    reqs = serve.make_requests(specs, arrivals=arrivals)
+    srv = serve.Server(nstreams=3, max_jobs=16, max_points=1 << 16, max_cells=1 << 19)
+    st = srv.serve(reqs)
+    assert st.jobs == len(reqs) and all(r.t_done >= r.arrival for r in reqs)
+    assert st.waves >= 2
+    mixed = [r.U.clone() for r in reqs]
+    reqs2 = serve.make_requests(specs, arrivals=arrivals)
+    st2 = serve.single_job_loop(reqs2)
+    assert st2.jobs == len(reqs2)
+    for a, r in zip(mixed, reqs2):
+        assert torch.equal(a, r.U)
+    srv.close()
+
+
+def test_server_admission_respects_budget(mods):
+    Plan, Batch, serve = mods
+    specs = _jobs(11, 20, grids=(32,), n_lo=1000, n_hi=1001)
+    reqs = serve.make_requests(specs)
+    srv = serve.Server(nstreams=2, max_jobs=8, max_points=1 << 16, max_cells=1 << 18)
+    one = srv.footprint(reqs[0])[0]
+    srv.budget = int(2.5 * one)                  # at most two jobs in flight
+    st = srv.serve(reqs, realtime=False)
+    assert st.jobs == 20
+    assert st.max_inflight_bytes <= srv.budget
+    srv.close()

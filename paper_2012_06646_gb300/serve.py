@@ -79,6 +79,37 @@ class ServeStats:
                 "mean_ms": float(lat.mean()), "max_inflight_bytes": self.max_inflight_bytes}
 
 
+@dataclass
+class WaveCaps:
+    jobs: int
+    points: int
+    cells: int
+    tiles: int
+
+
+def admit_wave(queue, caps: WaveCaps, inflight: int, budget: int):
+    """FIFO admission of waiting jobs into one wave.
+
+    queue: (npts, cells, footprint_bytes, tiles) per waiting job, in arrival order.
+    A job joins while the wave stays within the slot's capacity and the
+    in-flight footprint stays within the HBM budget; a job larger than the
+    whole budget still runs when nothing else is in flight (else it would
+    wait forever).  Returns (number of jobs admitted, wave footprint).
+    """
+    n, fp, pts, cells, tiles = 0, 0, 0, 0, 0
+    for npts, ncell, rf, rt in queue:
+        if n >= caps.jobs or pts + npts > caps.points or cells + ncell > caps.cells or tiles + rt > caps.tiles:
+            break
+        if inflight + fp + rf > budget and (n > 0 or inflight > 0):
+            break
+        n += 1
+        fp += rf
+        pts += npts
+        cells += ncell
+        tiles += rt
+    return n, fp
+
+
 class Server:
     def __init__(self, nstreams: int = 3, max_jobs: int = 256, max_points: int = 1 << 23,
                  max_cells: int = 1 << 26, budget_bytes: int | None = None, device=None):
@@ -145,23 +176,15 @@ class Server:
             for i in range(self.nstreams):
                 if slots[i] is not None or not waiting:
                     continue
-                wave, fp, pts, cells, tiles = [], 0, 0, 0, 0
-                while waiting and len(wave) < self.cap[0]:
-                    r = waiting[0]
+                for r in waiting:
                     if r.rid not in sizes:
                         sizes[r.rid] = self.footprint(r)
-                    rf, rt = sizes[r.rid]
-                    if (pts + r.npts > self.cap[1] or cells + r.N ** 3 > self.cap[2]
-                            or tiles + rt > self.batches[i].desc.max_tiles
-                            or (inflight + fp + rf > self.budget and (wave or inflight > 0))):
-                        break
-                    waiting.popleft()
+                caps = WaveCaps(self.cap[0], self.cap[1], self.cap[2], self.batches[i].desc.max_tiles)
+                take, fp = admit_wave([(r.npts, r.N ** 3) + sizes[r.rid] for r in waiting], caps, inflight,
+                                      self.budget)
+                wave = [waiting.popleft() for _ in range(take)]
+                for r in wave:
                     r.t_admit = time.perf_counter() - t0
-                    wave.append(r)
-                    fp += rf
-                    pts += r.npts
-                    cells += r.N ** 3
-                    tiles += rt
                 if wave:
                     slots[i] = self._launch(i, wave, fp)
                     inflight += fp

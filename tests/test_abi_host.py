@@ -1,0 +1,118 @@
+"""CPU-side checks of the boundary: the library loads without a GPU, exports every
+entry point include/ib.h declares, and validates arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2012_06646_gb300.build import build
+    build()
+    from paper_2012_06646_gb300 import _abi
+    return _abi
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "ib.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ib_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(abi):
+    names = header_functions()
+    assert len(names) >= 18
+    lib = ctypes.CDLL(abi.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ib.h but not exported"
+    assert sorted(abi.SIGNATURES) == names
+
+
+def _desc(abi, **kw):
+    d = abi.ib_plan_desc()
+    d.dim = kw.get("dim", 3)
+    for b, v in enumerate(kw.get("n", (128, 128, 128))):
+        d.n[b] = v
+    for b, v in enumerate(kw.get("L", (1.0, 1.0, 1.0))):
+        d.L[b] = v
+    d.grid = kw.get("grid", abi.IB_GRID_MAC)
+    d.kernel = kw.get("kernel", abi.IB_KERNEL_PESKIN4)
+    d.dtype = kw.get("dtype", abi.IB_F32)
+    d.ncomp = kw.get("ncomp", 3)
+    d.max_points = kw.get("max_points", 10 ** 6)
+    d.flags = kw.get("flags", 0)
+    return d
+
+
+def test_footprint_and_validation_on_host(abi):
+    lib = abi.load()
+    size = ctypes.c_size_t()
+    assert lib.ib_plan_footprint(ctypes.byref(_desc(abi)), ctypes.byref(size)) == abi.IB_OK
+    # 128^3 MAC, 10^6 points: cells 8.4 MB, 4 point arrays 16 MB, boxes 512 x 3 x 20^3 x 4 B
+    assert 60e6 < size.value < 80e6
+    comp = ctypes.c_size_t()
+    assert lib.ib_plan_footprint(ctypes.byref(_desc(abi, flags=abi.IB_PLAN_COMPENSATED)), ctypes.byref(comp)) == 0
+    assert comp.value > size.value
+    bad = [dict(dim=4), dict(ncomp=2), dict(ncomp=5, grid=abi.IB_GRID_CELL_CENTERED), dict(n=(0, 4, 4)),
+           dict(L=(1.0, -1.0, 1.0)), dict(max_points=-1), dict(flags=0x80), dict(kernel=7), dict(dtype=3),
+           dict(n=(2048, 2048, 1024))]
+    h = ctypes.c_void_p()
+    for kw in bad:
+        assert lib.ib_plan_footprint(ctypes.byref(_desc(abi, **kw)), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG, kw
+        assert lib.ib_plan_create(ctypes.byref(_desc(abi, **kw)), ctypes.byref(h)) == abi.IB_ERR_INVALID_ARG, kw
+    assert lib.ib_spread(None, 0, None, None, None, 0, None) == abi.IB_ERR_INVALID_ARG
+    assert lib.ib_batch_run(None, 0, None, 0, None) == abi.IB_ERR_INVALID_ARG
+    assert lib.ib_plan_destroy(None) == abi.IB_OK
+    assert lib.ib_status_string(abi.IB_ERR_NO_BINS) == b"IB_ERR_NO_BINS"
+    assert b"sm_103a" in lib.ib_version()
+
+
+def test_batch_footprints_on_host(abi):
+    lib = abi.load()
+    d = abi.ib_batch_desc(dim=3, grid=abi.IB_GRID_MAC, kernel=0, dtype=0, ncomp=3, max_jobs=64,
+                          max_points=1 << 20, max_cells=1 << 24, max_tiles=8192, flags=0)
+    size = ctypes.c_size_t()
+    assert lib.ib_batch_footprint(ctypes.byref(d), ctypes.byref(size)) == abi.IB_OK
+    job = abi.ib_job()
+    for b, v in enumerate((96, 96, 96)):
+        job.n[b] = v
+        job.L[b] = 1.0
+    job.npts = 5000
+    jb = ctypes.c_size_t()
+    tiles = ctypes.c_longlong()
+    assert lib.ib_batch_job_footprint(ctypes.byref(d), ctypes.byref(job), ctypes.byref(jb), ctypes.byref(tiles)) == 0
+    assert tiles.value == 6 ** 3                  # 96 / 16 tiles per dimension
+    assert jb.value == 4 * (96 ** 3 + 4 * 5000) + 216 * 3 * 20 ** 3 * 4
+    d.max_cells = 0
+    assert lib.ib_batch_footprint(ctypes.byref(d), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG
+
+
+def test_wave_admission_is_fifo_and_respects_caps_and_budget():
+    from paper_2012_06646_gb300.serve import WaveCaps, admit_wave
+    caps = WaveCaps(jobs=3, points=1000, cells=10 ** 6, tiles=100)
+    q = [(100, 1000, 10, 1)] * 5
+    assert admit_wave(q, caps, inflight=0, budget=10 ** 9) == (3, 30)          # job cap
+    assert admit_wave(q, caps, inflight=0, budget=25) == (2, 20)               # budget
+    assert admit_wave(q, caps, inflight=20, budget=25) == (0, 0)               # budget already used
+    assert admit_wave([(2000, 1, 10, 1)], caps, inflight=0, budget=10 ** 9) == (0, 0)   # over the point cap
+    assert admit_wave([(10, 1, 10 ** 10, 1)], caps, inflight=0, budget=5) == (1, 10 ** 10)  # alone: runs anyway
+    big_first = [(900, 1, 1, 1), (200, 1, 1, 1), (50, 1, 1, 1)]
+    assert admit_wave(big_first, caps, 0, 10 ** 9) == (1, 1)                   # FIFO: no overtaking
+
+
+def test_inputs_are_deterministic_and_stream_separated():
+    import numpy as np
+    import ib_inputs
+    a = ib_inputs.uniform_points(3, 100, (1.0, 2.0, 3.0), 3)
+    b = ib_inputs.uniform_points(3, 100, (1.0, 2.0, 3.0), 3)
+    c = ib_inputs.uniform_points(4, 100, (1.0, 2.0, 3.0), 3)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert a.dtype == np.float32 and np.all(a >= 0) and np.all(a < np.array([1.0, 2.0, 3.0], np.float32))
+    g = ib_inputs.normal_array(1, (20000,), dtype=np.float64)
+    assert abs(g.mean()) < 0.03 and abs(g.std() - 1.0) < 0.03
+    assert len(ib_inputs.icosphere(4)) == 2562
+    assert abs(ib_inputs.rbc_volume(3.91) - 94.4) < 0.2

@@ -185,7 +185,7 @@ def test_nonfinite_and_out_of_range_positions_are_reported(P, orc):
     Uh = host(U)
     assert np.isnan(Uh[5]).all() and np.isfinite(Uh[keep]).all()
     Xfar = X.copy()
-    Xfar[0, 0] = 3e7   # 3e7 * 16 cells > 2^30
+    Xfar[0, 0] = 1e8   # 1e8 * 16 cells > 2^30
     plan.interpolate(dev(Xfar), dev(u))
     with pytest.raises(IBError) as e:
         plan.check()

@@ -169,8 +169,8 @@ bool plan_sizes(const ib_plan_desc* d, Job* jb, int* tp, int* tc, long long* ntp
   if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
   if (d->max_points < 0 || d->max_points > kMaxPointsTotal) return false;
   if (d->flags & ~IB_PLAN_COMPENSATED) return false;
-  const int tile_plain = spread_tile_side(d->dim, entry_bytes(d->dtype, false), d->ncomp);
-  const int tile_comp = spread_tile_side(d->dim, entry_bytes(d->dtype, true), d->ncomp);
+  const int tile_plain = spread_tile_side(d->dim, entry_bytes(d->dtype, false), false, d->ncomp);
+  const int tile_comp = spread_tile_side(d->dim, entry_bytes(d->dtype, false), true, d->ncomp);
   Job j;
   if (!fill_job(j, d->dim, d->n, d->L, tile_plain)) return false;
   if (j.ncell > kMaxCellsTotal) return false;
@@ -354,7 +354,9 @@ ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u
   J.one.U = U;
   J.njobs = 1;
   const double scale = (flags & IB_ADJOINT) ? p->job.hmd : 1.0;
-  if (launch_interp(J, p->sh, call_bins(p, npts), p->desc.dtype, scale, s) != cudaSuccess) return IB_ERR_CUDA;
+  set_tiles(J.one, p->desc.dim, p->tile_plain);
+  if (launch_interp(J, p->sh, call_bins(p, npts), J.one.ntiles, p->tile_plain, p->desc.dtype, scale, s) != cudaSuccess)
+    return IB_ERR_CUDA;
   return IB_OK;
 }
 
@@ -417,7 +419,7 @@ static bool batch_sizes(const ib_batch_desc* d, int* tile, Layout* L) {
   if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
   if (d->flags != 0 || d->max_jobs < 1 || d->max_points < 0 || d->max_points > kMaxPointsTotal) return false;
   if (d->max_cells < 1 || d->max_cells > kMaxCellsTotal || d->max_tiles < 0) return false;
-  const int t = spread_tile_side(d->dim, entry_bytes(d->dtype, false), d->ncomp);
+  const int t = spread_tile_side(d->dim, entry_bytes(d->dtype, false), false, d->ncomp);
   const size_t boxes = (size_t)d->max_tiles * box_bytes(d->dim, t, entry_bytes(d->dtype, false), d->ncomp);
   if (tile) *tile = t;
   if (L) *L = make_layout(d->max_cells, d->max_points, boxes, sizeof(Job) * (size_t)d->max_jobs);
@@ -541,7 +543,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
   if (launch_bin(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, s) != cudaSuccess)
     return IB_ERR_CUDA;
-  if (launch_interp(J, b->sh, B, b->desc.dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_interp(J, b->sh, B, tiles, b->tile, b->desc.dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
   return IB_OK;
 }
 

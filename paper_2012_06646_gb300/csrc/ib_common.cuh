@@ -99,6 +99,8 @@ template <typename R>
 struct Cell1 {
   int i0, i1;   // cells for xi = 0 and xi = 1/2 (unwrapped)
   R r0, r1;     // offsets in [0, 1] (1 only through rounding of r -> 1-)
+  R c0, c1;     // 1 - r0, 1 - r1, each rounded from its exact value (the small
+                // weight (1 - r)^2 / ... keeps its relative accuracy as r -> 1)
 };
 
 // FP32 position with a short scale (scale = S 2^E, 0 < S < 2^24).  X (N/L) is
@@ -124,20 +126,20 @@ __device__ __forceinline__ uint32_t cell_short(float X, int S, int E, Cell1<floa
   const uint64_t P = M * (uint64_t)S;
   const bool neg = (bits >> 31) != 0u;
   if (P == 0) {  // X = +-0
-    c.i0 = 0; c.r0 = 0.f; c.i1 = -1; c.r1 = 0.5f;
+    c.i0 = 0; c.r0 = 0.f; c.c0 = 1.f; c.i1 = -1; c.r1 = 0.5f; c.c1 = 0.5f;
     return 0;
   }
   if (e >= 0) {  // u is an integer
     if (e >= 30 || (P >> (30 - e)) != 0) return ERR_RANGE;
     const int ip = (int)(P << e);
-    c.i0 = neg ? -ip : ip; c.r0 = 0.f; c.i1 = c.i0 - 1; c.r1 = 0.5f;
+    c.i0 = neg ? -ip : ip; c.r0 = 0.f; c.c0 = 1.f; c.i1 = c.i0 - 1; c.r1 = 0.5f; c.c1 = 0.5f;
     return 0;
   }
   const int k = -e;
   if (k >= 64) {  // |u| < 2^-16
     const float t = ldexpf(__ull2float_rn(P), -k);
-    if (!neg) { c.i0 = 0; c.r0 = t; c.i1 = -1; c.r1 = 0.5f + t; }
-    else      { c.i0 = -1; c.r0 = 1.f - t; c.i1 = -1; c.r1 = 0.5f - t; }
+    if (!neg) { c.i0 = 0; c.r0 = t; c.c0 = 1.f - t; c.i1 = -1; c.r1 = 0.5f + t; c.c1 = 0.5f - t; }
+    else      { c.i0 = -1; c.r0 = 1.f - t; c.c0 = t; c.i1 = -1; c.r1 = 0.5f - t; c.c1 = 0.5f + t; }
     return 0;
   }
   const uint64_t ip = P >> k;
@@ -156,10 +158,13 @@ __device__ __forceinline__ uint32_t cell_short(float X, int S, int E, Cell1<floa
   long long i1;
   uint64_t F1;
   if (F >= half) { i1 = i0; F1 = F - half; } else { i1 = i0 - 1; F1 = F + half; }
+  const uint64_t one = 1ull << k;
   c.i0 = (int)i0;
   c.i1 = (int)i1;
   c.r0 = __ull2float_rn(F) * pow2_neg(k);
+  c.c0 = __ull2float_rn(one - F) * pow2_neg(k);
   c.r1 = __ull2float_rn(F1) * pow2_neg(k);
+  c.c1 = __ull2float_rn(one - F1) * pow2_neg(k);
   return 0;
 }
 
@@ -174,8 +179,11 @@ __device__ __forceinline__ uint32_t cell_fp64(double X, double scale, Cell1<R>& 
   const double f1 = floor(v);
   c.i0 = (int)f0;
   c.i1 = (int)f1;
-  c.r0 = (R)__dsub_rn(u, f0);
-  c.r1 = (R)__dsub_rn(v, f1);
+  const double r0 = __dsub_rn(u, f0), r1 = __dsub_rn(v, f1);
+  c.r0 = (R)r0;
+  c.r1 = (R)r1;
+  c.c0 = (R)__dsub_rn(1.0, r0);
+  c.c1 = (R)__dsub_rn(1.0, r1);
   return 0;
 }
 
@@ -209,58 +217,16 @@ __device__ __forceinline__ int modn(int v, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// Weights w[t+1] = phi(t - r), t in {-1, 0, 1, 2}, r in [0, 1] (Eq. delta-defs).
-// Standard 4-point kernel: with q = sqrt(1 + 4 r (1 - r)),
+// Weights w[t+1] = phi(t - r), t in {-1, 0, 1, 2}, r in [0, 1], rc = 1 - r
+// (Eq. delta-defs).  Standard 4-point kernel, with q = sqrt(1 + 4 r rc):
 //   phi(-1-r) = (3-2r-q)/8, phi(-r) = (3-2r+q)/8, phi(1-r) = (1+2r+q)/8,
 //   phi(2-r) = (1+2r-q)/8,
-// and the two small ones rewritten without cancellation:
-//   (3-2r-q)/8 = (1-r)^2/(3-2r+q),  (1+2r-q)/8 = r^2/(1+2r+q).
+// written with a = 1 + 2 rc + q (= 3 - 2r + q), b = 1 + 2r + q and the two
+// small ones without cancellation: (3-2r-q)/8 = rc^2/a, (1+2r-q)/8 = r^2/b.
 // Cosine kernel phi(x) = cos(pi x/4)^2 / 2: with (s1,c1) = sincospi(r/4) and
-// (s2,c2) = sincospi((1-r)/4) the four weights are s2^2/2, c1^2/2, c2^2/2, s1^2/2.
+// (s2,c2) = sincospi(rc/4) the weights are s2^2/2, c1^2/2, c2^2/2, s1^2/2.
 // dw[t+1] = d phi(t - r) / d r, used by the position gradients.
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ void weights(int kernel, float r, float w[4]) {
-  if (kernel == 0) {
-    const float q = sqrtf(fmaf(4.f * r, 1.f - r, 1.f));
-    const float a = 3.f - 2.f * r + q;
-    const float b = 1.f + 2.f * r + q;
-    const float om = 1.f - r;
-    w[0] = om * om / a;
-    w[1] = 0.125f * a;
-    w[2] = 0.125f * b;
-    w[3] = r * r / b;
-  } else {
-    float s1, c1, s2, c2;
-    sincospif(0.25f * r, &s1, &c1);
-    sincospif(0.25f * (1.f - r), &s2, &c2);
-    w[0] = 0.5f * s2 * s2;
-    w[1] = 0.5f * c1 * c1;
-    w[2] = 0.5f * c2 * c2;
-    w[3] = 0.5f * s1 * s1;
-  }
-}
-
-__device__ __forceinline__ void weights(int kernel, double r, double w[4]) {
-  if (kernel == 0) {
-    const double q = sqrt(fma(4.0 * r, 1.0 - r, 1.0));
-    const double a = 3.0 - 2.0 * r + q;
-    const double b = 1.0 + 2.0 * r + q;
-    const double om = 1.0 - r;
-    w[0] = om * om / a;
-    w[1] = 0.125 * a;
-    w[2] = 0.125 * b;
-    w[3] = r * r / b;
-  } else {
-    double s1, c1, s2, c2;
-    sincospi(0.25 * r, &s1, &c1);
-    sincospi(0.25 * (1.0 - r), &s2, &c2);
-    w[0] = 0.5 * s2 * s2;
-    w[1] = 0.5 * c1 * c1;
-    w[2] = 0.5 * c2 * c2;
-    w[3] = 0.5 * s1 * s1;
-  }
-}
 
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
@@ -270,11 +236,32 @@ __device__ __forceinline__ void msincospi(float x, float* s, float* c) { sincosp
 __device__ __forceinline__ void msincospi(double x, double* s, double* c) { sincospi(x, s, c); }
 
 template <typename R>
-__device__ __forceinline__ void weights_and_derivs(int kernel, R r, R w[4], R dw[4]) {
-  weights(kernel, r, w);
+__device__ __forceinline__ void weights(int kernel, R r, R rc, R w[4]) {
   if (kernel == 0) {
-    const R q = msqrt(mfma((R)4 * r, (R)1 - r, (R)1));
-    const R qp = ((R)2 - (R)4 * r) / q;
+    const R q = msqrt(mfma((R)4 * r, rc, (R)1));
+    const R a = (R)1 + (R)2 * rc + q;
+    const R b = (R)1 + (R)2 * r + q;
+    w[0] = rc * rc / a;
+    w[1] = (R)0.125 * a;
+    w[2] = (R)0.125 * b;
+    w[3] = r * r / b;
+  } else {
+    R s1, c1, s2, c2;
+    msincospi((R)0.25 * r, &s1, &c1);
+    msincospi((R)0.25 * rc, &s2, &c2);
+    w[0] = (R)0.5 * s2 * s2;
+    w[1] = (R)0.5 * c1 * c1;
+    w[2] = (R)0.5 * c2 * c2;
+    w[3] = (R)0.5 * s1 * s1;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void weights_and_derivs(int kernel, R r, R rc, R w[4], R dw[4]) {
+  weights(kernel, r, rc, w);
+  if (kernel == 0) {
+    const R q = msqrt(mfma((R)4 * r, rc, (R)1));
+    const R qp = (R)2 * (rc - r) / q;             // dq/dr
     dw[0] = (R)0.125 * (-(R)2 - qp);
     dw[1] = (R)0.125 * (-(R)2 + qp);
     dw[2] = (R)0.125 * ((R)2 + qp);
@@ -282,7 +269,7 @@ __device__ __forceinline__ void weights_and_derivs(int kernel, R r, R w[4], R dw
   } else {
     R s1, c1, s2, c2;
     msincospi((R)0.25 * r, &s1, &c1);
-    msincospi((R)0.25 * ((R)1 - r), &s2, &c2);
+    msincospi((R)0.25 * rc, &s2, &c2);
     const R k = (R)0.78539816339744830962;  // pi / 4
     dw[0] = -k * s2 * c2;
     dw[1] = -k * s1 * c1;

@@ -8,9 +8,9 @@
 
 namespace ibgb {
 
-// Tile side of the spreading boxes for a plan: 16 in 3-D when the box
-// (side + 4)^3 of every component fits in shared memory, else 8; 32 in 2-D.
-int spread_tile_side(int dim, int entry_bytes, int ncomp);
+// Tile side of the spreading boxes: 16 in 3-D when the box (side + 4)^3 of
+// every component and the staging records fit in shared memory, else 8; 32 in 2-D.
+int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp);
 
 // Bytes of one spreading box (all components) for a tile side.
 size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp);
@@ -27,8 +27,10 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles_total,
                           int tile, int dtype, bool compensated, bool accumulate, cudaStream_t s);
 
-// Interpolation; every value is multiplied by `scale` (1 for plain interpolation).
-cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, int dtype, double scale, cudaStream_t s);
+// Interpolation by tiles (the spreading tile geometry); every value is
+// multiplied by `scale` (1 for plain interpolation).
+cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, long long ntiles, int tile, int dtype,
+                          double scale, cudaStream_t s);
 
 cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,
                             const void* v, double scale, void* D, cudaStream_t s);

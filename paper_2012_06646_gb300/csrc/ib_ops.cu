@@ -15,9 +15,10 @@
 // warp issues its additions in program order.  Every node sum therefore has
 // a fixed order and the result is bit-reproducible run to run.
 //
-// Interpolation (Eq. disc-interp, Algorithm 3) keeps one thread per point,
-// visiting points in cell order (the bins) so neighbouring threads gather
-// neighbouring grid values.
+// Interpolation (Eq. disc-interp, Algorithm 3) keeps one thread per point
+// (each point's sum has one writer), grouped by tile: the tile's grid values
+// plus a 2-node apron are staged in shared memory once, and every point of
+// the tile gathers its support from there.
 #include <math.h>
 
 #include "ib_internal.h"
@@ -111,113 +112,35 @@ __device__ __forceinline__ void point_box(const Job& jb, const Shape& sh, const 
     const int cc = cphys - T0[b];
     P.o0[b] = cc + 1;
     P.o1[b] = cc + (c.i1 - c.i0) + 1;
-    if (sh.mac) weights(sh.kernel, c.r0, P.w0[b]);
-    weights(sh.kernel, c.r1, P.w1[b]);
+    if (sh.mac) weights(sh.kernel, c.r0, c.c0, P.w0[b]);
+    weights(sh.kernel, c.r1, c.c1, P.w1[b]);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Spreading, plain accumulation: shared-memory atomics (red.shared.add),
-// ordered as described at the top of the file.
+// Spreading into a tile box.  Two stages per batch of kBatch points of a cell
+// layer:
+//   1. lanes = points: each lane computes its point's cell, weights and, per
+//      component, the 16 products wx[tx] wy[ty] g (g = h^-d G), the four z
+//      weights and the box offset of the t = -1 corner; it stores them as one
+//      staging record in shared memory;
+//   2. warp = point: the warp walks the batch's points in order; lane
+//      (tx, ty, tzb) owns the support nodes (tx, ty, tzb) and (tx, ty, tzb+2)
+//      of the point's 4x4x4 box (4x4 in 2-D, lanes 16-31 idle), so the 32
+//      lanes touch 64 distinct nodes and a plain read-modify-write is
+//      race-free; __syncwarp separates consecutive points.
+// Compensated mode keeps (sum, error) per node and adds by TwoSum.
 // ---------------------------------------------------------------------------
-template <typename T, int D, int TS>
-__global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constant__ Jobs J, const Shape sh,
-                                                            const Bins B, T* __restrict__ boxes) {
-  using Gm = Geo<D, TS>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* box = reinterpret_cast<T*>(smem_raw);
-  __shared__ uint32_t rstart_s[4][32];
-  __shared__ uint32_t rpre_s[4][32];
-  const int nc = sh.ncomp;
-  const long long gt = blockIdx.x;
-  const Job& jb = job_at(J, job_of_tile(J, gt));
-  if (jb.G == nullptr) return;
-  int T0[3], TE[3];
-  tile_coords<D, TS>(jb, gt - jb.tile_base, T0, TE);
-  for (int i = threadIdx.x; i < nc * Gm::BV; i += kBoxThreads) box[i] = (T)0;
-  __syncthreads();
+constexpr int kBatch = 16;
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nlayers = TE[D - 1];
-  const int rows = (D == 3) ? TE[1] : 1;
-  const T* Gp = (const T*)jb.G;
-  const T hmd = (T)jb.hmd;
-  for (int phase = 0; phase < 5; ++phase) {
-    for (int l = 5 * warp + phase; l < nlayers; l += 20) {
-      const uint32_t M = layer_rows<D>(jb, B, T0, TE, l, lane, rstart_s[warp], rpre_s[warp]);
-      const uint32_t K = (M + 31) / 32;
-      for (uint32_t k = 0; k < K; ++k) {
-        const uint32_t q = lane * K + k;
-        const bool act = q < M;
-        PointBox<T, D> P;
-        T gv[4] = {0, 0, 0, 0};
-        if (act) {
-          const uint32_t g = B.perm[layer_pos(q, rows, rstart_s[warp], rpre_s[warp])];
-          const long long li = (long long)g - jb.pt_base;
-          point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, P);
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-            if (a < nc) gv[a] = hmd * Gp[li * nc + a];
-        } else {
-#pragma unroll
-          for (int b = 0; b < D; ++b) {
-            P.o0[b] = P.o1[b] = 0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) P.w0[b][t] = P.w1[b][t] = (T)0;
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          if (a >= nc) break;
-          int o[3] = {0, 0, 0};
-          T wx[4], wy[4], wz[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            wx[t] = half_stag(sh, a, 0) ? P.w1[0][t] : P.w0[0][t];
-            wy[t] = half_stag(sh, a, 1) ? P.w1[1][t] : P.w0[1][t];
-            wz[t] = (D == 3) ? (half_stag(sh, a, 2) ? P.w1[D - 1][t] : P.w0[D - 1][t]) : (T)1;
-          }
-#pragma unroll
-          for (int b = 0; b < D; ++b) o[b] = half_stag(sh, a, b) ? P.o1[b] : P.o0[b];
-          const uint32_t key = act ? (uint32_t)(o[0] | (o[1] << 8) | (o[2] << 16)) : (0x80000000u | lane);
-          const uint32_t peers = __match_any_sync(0xffffffffu, key);
-          const int rank = __popc(peers & ((1u << lane) - 1u));
-          const int nround = __reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
-          T* bp = box + a * Gm::BV + (o[2] * Gm::BY + o[1]) * Gm::BX + o[0];
-          T wzg[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) wzg[t] = wz[t] * gv[a];
-          for (int rd = 0; rd < nround; ++rd) {
-            if (act && rank == rd) {
-#pragma unroll
-              for (int tz = 0; tz < Gm::NT; ++tz)
-#pragma unroll
-                for (int ty = 0; ty < 4; ++ty) {
-                  const T wyz = wy[ty] * wzg[tz];
-#pragma unroll
-                  for (int tx = 0; tx < 4; ++tx)
-                    atomicAdd(bp + (tz * Gm::BY + ty) * Gm::BX + tx, wx[tx] * wyz);
-                }
-            }
-          }
-        }
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-  // Box -> scratch, 16-byte vectors (nc * BV * sizeof(T) is a multiple of 16).
-  const int nvec = (int)(nc * Gm::BV * sizeof(T) / 16);
-  const uint4* src = reinterpret_cast<const uint4*>(box);
-  uint4* dst = reinterpret_cast<uint4*>(boxes + gt * (long long)(nc * Gm::BV));
-  for (int i = threadIdx.x; i < nvec; i += kBoxThreads) dst[i] = src[i];
+__host__ __device__ constexpr int rec_words(int nc) {
+  // 21 nc words (16 nc products, 4 nc z weights, nc offsets), padded to 2 mod 4 so
+  // that the 16 lanes writing records hit distinct banks.
+  int r = 21 * nc;
+  while (r % 4 != 2) ++r;
+  return r;
 }
 
-// ---------------------------------------------------------------------------
-// Spreading, compensated: every node carries a (sum, error) pair updated by
-// TwoSum (Knuth); one warp processes one point at a time with its lanes on
-// distinct support nodes, so plain read-modify-write is race-free.
-// ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void two_sum_into(T* s, T* e, T v) {
   const T a = *s;
@@ -228,19 +151,16 @@ __device__ __forceinline__ void two_sum_into(T* s, T* e, T v) {
   *e = *e + err;
 }
 
-template <typename T>
-__device__ __forceinline__ T pick4(const T w[4], int t) {
-  return (t == 0) ? w[0] : (t == 1) ? w[1] : (t == 2) ? w[2] : w[3];
-}
-
-template <typename T, int D, int TS>
-__global__ void __launch_bounds__(kBoxThreads) k_spread_box_comp(const __grid_constant__ Jobs J, const Shape sh,
-                                                                 const Bins B, T* __restrict__ boxes) {
+template <typename T, int D, int TS, bool COMP>
+__global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constant__ Jobs J, const Shape sh,
+                                                            const Bins B, T* __restrict__ boxes) {
   using Gm = Geo<D, TS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = sh.ncomp;
+  const int REC = rec_words(nc);
   T* boxS = reinterpret_cast<T*>(smem_raw);
-  T* boxE = boxS + nc * Gm::BV;
+  T* boxE = boxS + nc * Gm::BV;                                   // compensated mode only
+  T* stage_all = boxS + (COMP ? 2 : 1) * nc * Gm::BV;
   __shared__ uint32_t rstart_s[4][32];
   __shared__ uint32_t rpre_s[4][32];
   const long long gt = blockIdx.x;
@@ -248,66 +168,83 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box_comp(const __grid_co
   if (jb.G == nullptr) return;
   int T0[3], TE[3];
   tile_coords<D, TS>(jb, gt - jb.tile_base, T0, TE);
-  for (int i = threadIdx.x; i < 2 * nc * Gm::BV; i += kBoxThreads) boxS[i] = (T)0;
+  for (int i = threadIdx.x; i < (COMP ? 2 : 1) * nc * Gm::BV; i += kBoxThreads) boxS[i] = (T)0;
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* stage = stage_all + warp * kBatch * REC;
   const int nlayers = TE[D - 1];
   const int rows = (D == 3) ? TE[1] : 1;
   const T* Gp = (const T*)jb.G;
   const T hmd = (T)jb.hmd;
-  // Lane -> support node: x = lane & 3, y = (lane >> 2) & 3, z = (lane >> 4) and +2 (3-D).
   const int tx = lane & 3, ty = (lane >> 2) & 3, tzb = lane >> 4;
+  const int lane_off = (D == 3) ? ((tzb * Gm::BY + ty) * Gm::BX + tx) : (ty * Gm::BX + tx);
   const bool lane_on = (D == 3) || lane < 16;
+  constexpr int ZSTEP = 2 * Gm::BY * Gm::BX;
   for (int phase = 0; phase < 5; ++phase) {
     for (int l = 5 * warp + phase; l < nlayers; l += 20) {
       const uint32_t M = layer_rows<D>(jb, B, T0, TE, l, lane, rstart_s[warp], rpre_s[warp]);
-      for (uint32_t base = 0; base < M; base += 32) {
-        // Lane i fetches point base + i; the warp then walks the 32 points in order.
-        const uint32_t q = base + lane;
-        T xs[3] = {0, 0, 0}, gs[4] = {0, 0, 0, 0};
-        if (q < M) {
-          const uint32_t g = B.perm[layer_pos(q, rows, rstart_s[warp], rpre_s[warp])];
+      for (uint32_t base = 0; base < M; base += kBatch) {
+        // Stage 1: lane q < kBatch prepares the record of point base + q.
+        if (lane < kBatch && base + lane < M) {
+          const uint32_t g = B.perm[layer_pos(base + lane, rows, rstart_s[warp], rpre_s[warp])];
           const long long li = (long long)g - jb.pt_base;
-#pragma unroll
-          for (int b = 0; b < D; ++b) xs[b] = ((const T*)jb.X)[li * D + b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-            if (a < nc) gs[a] = hmd * Gp[li * nc + a];
-        }
-        const int cnt = (int)min(32u, M - base);
-        for (int i = 0; i < cnt; ++i) {
-          T xp[D];
-#pragma unroll
-          for (int b = 0; b < D; ++b) xp[b] = __shfl_sync(0xffffffffu, xs[b], i);
-          T gp[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) gp[a] = __shfl_sync(0xffffffffu, gs[a], i);
           PointBox<T, D> P;
-          point_box<T, D>(jb, sh, xp, T0, P);
+          point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, P);
+          T* rec = stage + lane * REC;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (a >= nc) break;
+            const T ga = hmd * Gp[li * nc + a];
+            const bool hx = half_stag(sh, a, 0), hy = half_stag(sh, a, 1);
+            T wxg[4], wy[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              wxg[t] = (hx ? P.w1[0][t] : P.w0[0][t]) * ga;
+              wy[t] = hy ? P.w1[1][t] : P.w0[1][t];
+            }
+#pragma unroll
+            for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
+              for (int xx = 0; xx < 4; ++xx) rec[a * 16 + yy * 4 + xx] = wxg[xx] * wy[yy];
+            int off = (hy ? P.o1[1] : P.o0[1]) * Gm::BX + (hx ? P.o1[0] : P.o0[0]);
+            if (D == 3) {
+              const bool hz = half_stag(sh, a, 2);
+              const T* wz = hz ? P.w1[D - 1] : P.w0[D - 1];
+              T* zr = rec + 16 * nc + 4 * a;
+              zr[0] = wz[0];
+              zr[1] = wz[2];
+              zr[2] = wz[1];
+              zr[3] = wz[3];
+              off += (hz ? P.o1[D - 1] : P.o0[D - 1]) * Gm::BY * Gm::BX;
+            }
+            rec[20 * nc + a] = (T)(a * Gm::BV + off);
+          }
+        }
+        __syncwarp();
+        // Stage 2: the warp adds the points of the batch one by one.
+        const int cnt = (int)min((uint32_t)kBatch, M - base);
+        for (int i = 0; i < cnt; ++i) {
+          const T* rec = stage + i * REC;
           if (lane_on) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
               if (a >= nc) break;
-              const bool hx = half_stag(sh, a, 0), hy = half_stag(sh, a, 1);
-              const int ox = hx ? P.o1[0] : P.o0[0];
-              const int oy = hy ? P.o1[1] : P.o0[1];
-              const T wxv = hx ? pick4(P.w1[0], tx) : pick4(P.w0[0], tx);
-              const T wyv = hy ? pick4(P.w1[1], ty) : pick4(P.w0[1], ty);
-              const T wxy = wxv * wyv * gp[a];
+              const int idx = (int)rec[20 * nc + a] + lane_off;
+              const T pv = rec[a * 16 + (lane & 15)];
               if (D == 3) {
-                const bool hz = half_stag(sh, a, 2);
-                const int oz = hz ? P.o1[D - 1] : P.o0[D - 1];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  const int tz = tzb + 2 * h;
-                  const T wzv = hz ? pick4(P.w1[D - 1], tz) : pick4(P.w0[D - 1], tz);
-                  const int idx = a * Gm::BV + ((oz + tz) * Gm::BY + oy + ty) * Gm::BX + ox + tx;
-                  two_sum_into(boxS + idx, boxE + idx, wxy * wzv);
+                const T z0 = rec[16 * nc + 4 * a + 2 * tzb];
+                const T z1 = rec[16 * nc + 4 * a + 2 * tzb + 1];
+                if (COMP) {
+                  two_sum_into(boxS + idx, boxE + idx, pv * z0);
+                  two_sum_into(boxS + idx + ZSTEP, boxE + idx + ZSTEP, pv * z1);
+                } else {
+                  boxS[idx] += pv * z0;
+                  boxS[idx + ZSTEP] += pv * z1;
                 }
               } else {
-                const int idx = a * Gm::BV + (oy + ty) * Gm::BX + ox + tx;
-                two_sum_into(boxS + idx, boxE + idx, wxy);
+                if (COMP) two_sum_into(boxS + idx, boxE + idx, pv);
+                else boxS[idx] += pv;
               }
             }
           }
@@ -318,9 +255,10 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box_comp(const __grid_co
     }
     __syncthreads();
   }
-  const int nvec = (int)(2 * nc * Gm::BV * sizeof(T) / 16);
+  // Box -> scratch, 16-byte vectors (the box size in bytes is a multiple of 16).
+  const int nvec = (int)((COMP ? 2 : 1) * nc * Gm::BV * sizeof(T) / 16);
   const uint4* src = reinterpret_cast<const uint4*>(boxS);
-  uint4* dst = reinterpret_cast<uint4*>(boxes + gt * (long long)(2 * nc * Gm::BV));
+  uint4* dst = reinterpret_cast<uint4*>(boxes + gt * (long long)((COMP ? 2 : 1) * nc * Gm::BV));
   for (int i = threadIdx.x; i < nvec; i += kBoxThreads) dst[i] = src[i];
 }
 
@@ -358,6 +296,74 @@ __device__ __forceinline__ int cover_list(int x, int n, int ntile, int* tl, int*
   return cnt;
 }
 
+// Fast cover list for n >= TS + 4 (a box never wraps onto its own tile):
+// entries in increasing unwrapped position, then tile -- the periodic copy
+// x - n in tile 0, the previous tile, the node's own tile, the next tile,
+// and the periodic copy x + n in the last tile -- at most 3 of them at once.
+// Kept in three scalar slots so the list stays in registers.
+struct Cover3 {
+  int t0, o0, t1, o1, t2, o2, n;
+  __device__ __forceinline__ void push(int t, int o) {
+    if (n == 0) { t0 = t; o0 = o; } else if (n == 1) { t1 = t; o1 = o; } else { t2 = t; o2 = o; }
+    ++n;
+  }
+  __device__ __forceinline__ int t(int i) const { return i == 0 ? t0 : (i == 1 ? t1 : t2); }
+  __device__ __forceinline__ int o(int i) const { return i == 0 ? o0 : (i == 1 ? o1 : o2); }
+};
+
+template <int TS>
+__device__ __forceinline__ Cover3 cover_fast(int x, int n, int ntile) {
+  Cover3 c;
+  c.n = 0;
+  c.t0 = c.o0 = c.t1 = c.o1 = c.t2 = c.o2 = 0;
+  const int t = x / TS, xl = x - t * TS;
+  if (x >= n - 2) c.push(0, x - n + 2);
+  if (xl < 2 && t >= 1) c.push(t - 1, xl + TS + 2);
+  c.push(t, xl + 2);
+  if (xl >= TS - 2 && t + 1 < ntile) c.push(t + 1, xl - TS + 2);
+  const int vo = x + n - (ntile - 1) * TS + 2;
+  if (vo < TS + 4) c.push(ntile - 1, vo);
+  return c;
+}
+
+template <typename T, int D, int TS, bool CP>
+__device__ __noinline__ void combine_general(const Job& jb, const Shape& sh, const T* __restrict__ boxes,
+                                             const int* x, long long lc, int accumulate) {
+  using Gm = Geo<D, TS>;
+  int tl[3][kMaxCover], of[3][kMaxCover], nco[3];
+  for (int b = 0; b < D; ++b) nco[b] = cover_list<TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
+  if (D == 2) {
+    nco[2] = 1;
+    tl[2][0] = 0;
+    of[2][0] = 0;
+  }
+  const int nc = sh.ncomp;
+  const long long box_elems = (long long)(CP ? 2 : 1) * nc * Gm::BV;
+  T* f = (T*)jb.f;
+  for (int a = 0; a < nc; ++a) {
+    T S = 0, E = 0;
+    for (int iz = 0; iz < nco[2]; ++iz)
+      for (int iy = 0; iy < nco[1]; ++iy)
+        for (int ix = 0; ix < nco[0]; ++ix) {
+          const long long tile = jb.tile_base + tl[0][ix] + (long long)jb.ntile[0] * (tl[1][iy] + (long long)jb.ntile[1] * tl[2][iz]);
+          const long long idx = tile * box_elems + a * Gm::BV + (of[2][iz] * Gm::BY + of[1][iy]) * Gm::BX + of[0][ix];
+          if (CP) {
+            const T sv = boxes[idx];
+            const T ev = boxes[idx + nc * Gm::BV];
+            const T sum = S + sv;
+            const T bb = sum - S;
+            E += ((S - (sum - bb)) + (sv - bb)) + ev;
+            S = sum;
+          } else {
+            S += boxes[idx];
+          }
+        }
+    const T val = CP ? S + E : S;
+    const long long o = a * jb.ncell + lc;
+    f[o] = accumulate ? f[o] + val : val;
+  }
+}
+
 template <typename T, int D, int TS, bool CP>
 __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_constant__ Jobs J, const Shape sh,
                                                              const T* __restrict__ boxes, long long ncell_total,
@@ -372,38 +378,54 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
   x[0] = (int)(lc % jb.n[0]);
   x[1] = (int)((lc / jb.n[0]) % jb.n[1]);
   x[2] = (D == 3) ? (int)(lc / ((long long)jb.n[0] * jb.n[1])) : 0;
-  int tl[3][kMaxCover], of[3][kMaxCover], nco[3];
+  bool fast = true;
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    if (b < D) {
-      nco[b] = cover_list<TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
-    } else {
-      nco[b] = 1;
-      tl[b][0] = 0;
-      of[b][0] = 0;
-    }
+  for (int b = 0; b < D; ++b) fast = fast && jb.n[b] >= TS + 4;
+  if (!fast) {
+    combine_general<T, D, TS, CP>(jb, sh, boxes, x, lc, accumulate);
+    return;
+  }
+  const Cover3 cx = cover_fast<TS>(x[0], jb.n[0], jb.ntile[0]);
+  const Cover3 cy = cover_fast<TS>(x[1], jb.n[1], jb.ntile[1]);
+  Cover3 cz;
+  if (D == 3) {
+    cz = cover_fast<TS>(x[2], jb.n[2], jb.ntile[2]);
+  } else {
+    cz.n = 1;
+    cz.t0 = cz.o0 = cz.t1 = cz.o1 = cz.t2 = cz.o2 = 0;
   }
   const int nc = sh.ncomp;
   const long long box_elems = (long long)(CP ? 2 : 1) * nc * Gm::BV;
   T* f = (T*)jb.f;
-  for (int a = 0; a < nc; ++a) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (a >= nc) break;
     T S = 0, E = 0;
-    for (int iz = 0; iz < nco[2]; ++iz)
-      for (int iy = 0; iy < nco[1]; ++iy)
-        for (int ix = 0; ix < nco[0]; ++ix) {
-          const long long tile = jb.tile_base + tl[0][ix] + (long long)jb.ntile[0] * (tl[1][iy] + (long long)jb.ntile[1] * tl[2][iz]);
-          const long long idx = tile * box_elems + a * Gm::BV + (of[2][iz] * Gm::BY + of[1][iy]) * Gm::BX + of[0][ix];
+#pragma unroll
+    for (int iz = 0; iz < 3; ++iz) {
+      if (iz >= cz.n) break;
+#pragma unroll
+      for (int iy = 0; iy < 3; ++iy) {
+        if (iy >= cy.n) break;
+        const long long trow = jb.tile_base + (long long)jb.ntile[0] * (cy.t(iy) + (long long)jb.ntile[1] * cz.t(iz));
+        const int orow = a * Gm::BV + (cz.o(iz) * Gm::BY + cy.o(iy)) * Gm::BX;
+#pragma unroll
+        for (int ix = 0; ix < 3; ++ix) {
+          if (ix >= cx.n) break;
+          const long long idx = (trow + cx.t(ix)) * box_elems + orow + cx.o(ix);
           if (CP) {
-            const T s = boxes[idx];
-            const T e = boxes[idx + nc * Gm::BV];
-            const T sum = S + s;
+            const T sv = boxes[idx];
+            const T ev = boxes[idx + nc * Gm::BV];
+            const T sum = S + sv;
             const T bb = sum - S;
-            E += ((S - (sum - bb)) + (s - bb)) + e;
+            E += ((S - (sum - bb)) + (sv - bb)) + ev;
             S = sum;
           } else {
             S += boxes[idx];
           }
         }
+      }
+    }
     const T val = CP ? S + E : S;
     const long long o = a * jb.ncell + lc;
     f[o] = accumulate ? f[o] + val : val;
@@ -411,7 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 }
 
 // ---------------------------------------------------------------------------
-// Interpolation (Algorithm 3): one thread per point in cell order.
+// Node offsets of a point's 4 support nodes in one dimension (wrapped).
 // ---------------------------------------------------------------------------
 template <typename T, int D>
 __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long long stride, long long off[4]) {
@@ -421,70 +443,148 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
   for (int t = 0; t < 4; ++t) off[t] = (long long)wrapn(base + t - 1, n) * stride;
 }
 
-template <typename T, int D>
-__global__ void __launch_bounds__(kThreads) k_interp(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
-                                                     const T scale) {
-  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+// ---------------------------------------------------------------------------
+// Interpolation by tiles: the CTA of a tile copies the grid values of the
+// tile plus a 2-node apron (every component) into shared memory, then each
+// thread takes one of the tile's points (cell order) and sums its 4^d
+// support from shared memory.  Points outside every tile (invalid
+// positions) are handled by k_interp_invalid.
+// ---------------------------------------------------------------------------
+constexpr int kInterpThreads = 256;
+
+template <typename T, int D, int TS>
+__global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_constant__ Jobs J, const Shape sh,
+                                                                 const Bins B, const T scale) {
+  using Gm = Geo<D, TS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* box = reinterpret_cast<T*>(smem_raw);
+  __shared__ uint32_t rstart[256];
+  __shared__ uint32_t rpre[257];
+  const long long gt = blockIdx.x;
+  const Job& jb = job_at(J, job_of_tile(J, gt));
+  if (jb.u == nullptr) return;
+  int T0[3], TE[3];
+  tile_coords<D, TS>(jb, gt - jb.tile_base, T0, TE);
+  const int nc = sh.ncomp;
+  const int tid = threadIdx.x;
+
+  // Rows of the tile's own cells (x fastest inside a row): start and count in the bins.
+  const int nrows = (D == 3) ? TE[1] * TE[2] : TE[1];
+  uint32_t cnt = 0, st = 0;
+  if (tid < nrows) {
+    const int y = T0[1] + ((D == 3) ? tid % TE[1] : tid);
+    const int z = (D == 3) ? T0[2] + tid / TE[1] : 0;
+    const long long cell = jb.cell_base + T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
+    st = B.count[cell];
+    cnt = B.count[cell + TE[0]] - st;
+  }
+  // Block-wide exclusive scan of the row counts (256 threads, one row each).
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t yv = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += yv;
+    }
+    __shared__ uint32_t wsum[8];
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t t = (lane < 8) ? wsum[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const uint32_t yv = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += yv;
+      }
+      if (lane < 8) wsum[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t before = (warp > 0) ? wsum[warp - 1] : 0u;
+    rstart[tid] = st;
+    rpre[tid] = before + inc - cnt;
+    if (tid == 0) rpre[256] = wsum[7];
+  }
+
+  // Grid values of the box: nodes T0 - 2 .. T0 + TS + 1 (unwrapped), all components.
+  const T* u = (const T*)jb.u;
+  const int bz_n = (D == 3) ? min(Gm::BZ, TE[2] + 4) : 1;
+  const int by_n = min(Gm::BY, TE[1] + 4);
+  const int bx_n = min(Gm::BX, TE[0] + 4);
+  const long long s1 = jb.n[0], s2 = (long long)jb.n[0] * jb.n[1];
+  for (int a = 0; a < nc; ++a) {
+    const T* ua = u + a * jb.ncell;
+    T* ba = box + a * Gm::BV;
+    for (int r = tid / 32; r < bz_n * by_n; r += kInterpThreads / 32) {
+      const int by = r % by_n, bz = r / by_n;
+      const int y = wrapn(T0[1] - 2 + by, jb.n[1]);
+      const int z = (D == 3) ? wrapn(T0[2] - 2 + bz, jb.n[2]) : 0;
+      const T* row = ua + y * s1 + z * s2;
+      T* brow = ba + (bz * Gm::BY + by) * Gm::BX;
+      for (int bx = tid & 31; bx < bx_n; bx += 32) brow[bx] = __ldg(row + wrapn(T0[0] - 2 + bx, jb.n[0]));
+    }
+  }
+  __syncthreads();
+
+  const uint32_t P = rpre[256];
+  const int nr = nrows;
+  for (uint32_t q = tid; q < P; q += kInterpThreads) {
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rpre[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t g = B.perm[rstart[lo] + (q - rpre[lo])];
+    const long long li = (long long)g - jb.pt_base;
+    PointBox<T, D> Pb;
+    point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, Pb);
+    T* U = (T*)jb.U + li * nc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (a >= nc) break;
+      const bool hx = half_stag(sh, a, 0), hy = half_stag(sh, a, 1);
+      T wx[4], wy[4], wz[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        wx[t] = hx ? Pb.w1[0][t] : Pb.w0[0][t];
+        wy[t] = hy ? Pb.w1[1][t] : Pb.w0[1][t];
+        wz[t] = (D == 3) ? (half_stag(sh, a, 2) ? Pb.w1[D - 1][t] : Pb.w0[D - 1][t]) : (T)1;
+      }
+      const int ox = hx ? Pb.o1[0] : Pb.o0[0];
+      const int oy = hy ? Pb.o1[1] : Pb.o0[1];
+      const int oz = (D == 3) ? (half_stag(sh, a, 2) ? Pb.o1[D - 1] : Pb.o0[D - 1]) : 0;
+      const T* bp = box + a * Gm::BV + (oz * Gm::BY + oy) * Gm::BX + ox;
+      T acc = 0;
+#pragma unroll
+      for (int tz = 0; tz < Gm::NT; ++tz) {
+        T accy = 0;
+#pragma unroll
+        for (int ty = 0; ty < 4; ++ty) {
+          const T* row = bp + (tz * Gm::BY + ty) * Gm::BX;
+          T accx = wx[0] * row[0];
+#pragma unroll
+          for (int tx = 1; tx < 4; ++tx) accx += wx[tx] * row[tx];
+          accy += wy[ty] * accx;
+        }
+        acc += wz[tz] * accy;
+      }
+      U[a] = acc * scale;
+    }
+  }
+}
+
+// Points with an invalid position (after every valid point in the bins): U = NaN.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_interp_invalid(const __grid_constant__ Jobs J, const Shape sh,
+                                                             const Bins B) {
+  const long long first = B.count[B.ncell_total];
+  const long long p = first + (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= B.npts_total) return;
   const uint32_t g = B.perm[p];
   const Job& jb = job_at(J, job_of_point(J, (long long)g));
   if (jb.u == nullptr) return;
-  const long long li = (long long)g - jb.pt_base;
-  const int nc = sh.ncomp;
-  T* U = (T*)jb.U + li * nc;
-  const T* Xp = (const T*)jb.X + li * D;
-  Cell1<T> c[D];
-  uint32_t err = 0;
-#pragma unroll
-  for (int b = 0; b < D; ++b) err |= point_cell<T>(Xp[b], jb, b, c[b]);
-  if (err) {
-    for (int a = 0; a < nc; ++a) U[a] = (T)NAN;
-    return;
-  }
-  T w0[D][4], w1[D][4];
-#pragma unroll
-  for (int b = 0; b < D; ++b) {
-    if (sh.mac) weights(sh.kernel, c[b].r0, w0[b]);
-    weights(sh.kernel, c[b].r1, w1[b]);
-  }
-  const T* u = (const T*)jb.u;
-  const long long s1 = jb.n[0], s2 = (long long)jb.n[0] * jb.n[1];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    if (a >= nc) break;
-    long long ox[4], oy[4], oz[4] = {0, 0, 0, 0};
-    T wx[4], wy[4], wz[4] = {1, 0, 0, 0};
-    const bool hx = half_stag(sh, a, 0), hy = half_stag(sh, a, 1);
-    node_offsets<T, D>(jb, 0, hx ? c[0].i1 : c[0].i0, 1, ox);
-    node_offsets<T, D>(jb, 1, hy ? c[1].i1 : c[1].i0, s1, oy);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      wx[t] = hx ? w1[0][t] : w0[0][t];
-      wy[t] = hy ? w1[1][t] : w0[1][t];
-    }
-    if (D == 3) {
-      const bool hz = half_stag(sh, a, 2);
-      node_offsets<T, D>(jb, D - 1, hz ? c[D - 1].i1 : c[D - 1].i0, s2, oz);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) wz[t] = hz ? w1[D - 1][t] : w0[D - 1][t];
-    }
-    const T* ua = u + a * jb.ncell;
-    T acc = 0;
-#pragma unroll
-    for (int tz = 0; tz < Geo<D, 8>::NT; ++tz) {
-      T accy = 0;
-#pragma unroll
-      for (int ty = 0; ty < 4; ++ty) {
-        const T* row = ua + oz[tz] + oy[ty];
-        T accx = wx[0] * __ldg(row + ox[0]);
-#pragma unroll
-        for (int tx = 1; tx < 4; ++tx) accx += wx[tx] * __ldg(row + ox[tx]);
-        accy += wy[ty] * accx;
-      }
-      acc += wz[tz] * accy;
-    }
-    U[a] = acc * scale;
-  }
+  T* U = (T*)jb.U + ((long long)g - jb.pt_base) * sh.ncomp;
+  for (int a = 0; a < sh.ncomp; ++a) U[a] = (T)NAN;
 }
 
 // ---------------------------------------------------------------------------
@@ -515,8 +615,8 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad(const __grid_constant__ J
   T w0[D][4], w1[D][4], d0[D][4], d1[D][4];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
-    if (sh.mac) weights_and_derivs<T>(sh.kernel, c[b].r0, w0[b], d0[b]);
-    weights_and_derivs<T>(sh.kernel, c[b].r1, w1[b], d1[b]);
+    if (sh.mac) weights_and_derivs<T>(sh.kernel, c[b].r0, c[b].c0, w0[b], d0[b]);
+    weights_and_derivs<T>(sh.kernel, c[b].r1, c[b].c1, w1[b], d1[b]);
   }
   const long long s1 = jb.n[0], s2 = (long long)jb.n[0] * jb.n[1];
   T out[3] = {0, 0, 0};
@@ -599,18 +699,22 @@ void allow_smem(K kernel, size_t bytes) {
 }
 
 template <typename T, int D, int TS>
+size_t spread_smem(int nc, bool comp) {
+  using Gm = Geo<D, TS>;
+  return ((comp ? 2 : 1) * (size_t)nc * Gm::BV + 4 * (size_t)kBatch * rec_words(nc)) * sizeof(T);
+}
+
+template <typename T, int D, int TS>
 cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool comp,
                         bool accumulate, cudaStream_t s) {
-  using Gm = Geo<D, TS>;
   if (ntiles > 0) {
+    const size_t bytes = spread_smem<T, D, TS>(sh.ncomp, comp);
     if (comp) {
-      const size_t bytes = 2 * (size_t)sh.ncomp * Gm::BV * sizeof(T);
-      allow_smem(k_spread_box_comp<T, D, TS>, bytes);
-      k_spread_box_comp<T, D, TS><<<(unsigned)ntiles, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
+      allow_smem(k_spread_box<T, D, TS, true>, bytes);
+      k_spread_box<T, D, TS, true><<<(unsigned)ntiles, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
     } else {
-      const size_t bytes = (size_t)sh.ncomp * Gm::BV * sizeof(T);
-      allow_smem(k_spread_box<T, D, TS>, bytes);
-      k_spread_box<T, D, TS><<<(unsigned)ntiles, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
+      allow_smem(k_spread_box<T, D, TS, false>, bytes);
+      k_spread_box<T, D, TS, false><<<(unsigned)ntiles, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
     }
   }
   if (B.ncell_total > 0) {
@@ -626,9 +730,13 @@ cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* box
 
 }  // namespace
 
-int spread_tile_side(int dim, int entry_bytes, int ncomp) {
+int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp) {
   if (dim == 2) return 32;
-  return (20 * 20 * 20 * (size_t)entry_bytes * ncomp <= 200 * 1024) ? 16 : 8;
+  // 16^3 tiles when the box (20^3 entries per component, two planes when
+  // compensated) and the staging records fit in 220 KB of shared memory.
+  const size_t box = 20 * 20 * 20 * (size_t)elem_bytes * (comp ? 2 : 1) * ncomp;
+  const size_t stage = 4 * (size_t)kBatch * rec_words(ncomp) * elem_bytes;
+  return (box + stage <= 220 * 1024) ? 16 : 8;
 }
 
 size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp) {
@@ -648,17 +756,31 @@ cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* b
   return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, s);
 }
 
-cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, int dtype, double scale, cudaStream_t s) {
-  const long long n = B.npts_total;
-  if (n == 0) return cudaSuccess;
-  if (dtype == 0) {
-    if (sh.dim == 3) k_interp<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, (float)scale);
-    else k_interp<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, (float)scale);
-  } else {
-    if (sh.dim == 3) k_interp<double, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, scale);
-    else k_interp<double, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sh, B, scale);
+template <typename T, int D, int TS>
+cudaError_t interp_impl(const Jobs& J, const Shape& sh, const Bins& B, long long ntiles, double scale,
+                        cudaStream_t s) {
+  using Gm = Geo<D, TS>;
+  if (ntiles > 0) {
+    const size_t bytes = (size_t)sh.ncomp * Gm::BV * sizeof(T);
+    allow_smem(k_interp_tile<T, D, TS>, bytes);
+    k_interp_tile<T, D, TS><<<(unsigned)ntiles, kInterpThreads, bytes, s>>>(J, sh, B, (T)scale);
   }
+  // Invalid points sit after every valid one in the bins; at most npts of them.
+  if (B.npts_total > 0)
+    k_interp_invalid<T><<<grid_for(B.npts_total, kThreads), kThreads, 0, s>>>(J, sh, B);
   return cudaGetLastError();
+}
+
+cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, long long ntiles, int tile, int dtype,
+                          double scale, cudaStream_t s) {
+  if (dtype == 0) {
+    if (sh.dim == 2) return interp_impl<float, 2, 32>(J, sh, B, ntiles, scale, s);
+    if (tile == 16) return interp_impl<float, 3, 16>(J, sh, B, ntiles, scale, s);
+    return interp_impl<float, 3, 8>(J, sh, B, ntiles, scale, s);
+  }
+  if (sh.dim == 2) return interp_impl<double, 2, 32>(J, sh, B, ntiles, scale, s);
+  if (tile == 16) return interp_impl<double, 3, 16>(J, sh, B, ntiles, scale, s);
+  return interp_impl<double, 3, 8>(J, sh, B, ntiles, scale, s);
 }
 
 cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,

@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--serve-jobs", type=int, default=384, help="jobs of the served-batch measurement (0: skip)")
+    ap.add_argument("--serve-load", type=float, default=0.9, help="offered load as a fraction of the loop capacity")
     return ap.parse_args()
 
 
@@ -170,6 +172,38 @@ def cpu_oracle_rate(sample: int, N: int, seed: int):
     oracle.interp(g, X, u)
     dt = time.perf_counter() - t0
     return sample / dt, dt
+
+
+def serving_bench(device, njobs: int, load: float, seed: int = 1):
+    """Served batch: independent spread + interpolate jobs, N in {32, 64, 96, 128}, n log-uniform in
+    [1e3, 1e5], half uniform / half on RBC shells.  The one-job-per-launch loop is first run back to
+    back to measure its capacity; then Poisson arrivals at `load` x that capacity are served by the
+    continuous-batching server and by the loop.  Latency = completion - arrival."""
+    import ib_inputs
+    import torch
+    from paper_2012_06646_gb300 import serve
+    specs = ib_inputs.job_mix(seed, njobs)
+    warm = serve.make_requests(specs[: min(16, njobs)])
+    serve.single_job_loop(warm, realtime=False, device=device)
+    srv = serve.Server(nstreams=3, max_jobs=64, max_points=1 << 22, max_cells=1 << 25, device=device)
+    srv.serve(serve.make_requests(specs[: min(16, njobs)]), realtime=False)
+    reqs = serve.make_requests(specs)
+    cap_run = serve.single_job_loop(reqs, realtime=False, device=device)
+    cap = cap_run.jobs / cap_run.wall_s
+    arrivals = ib_inputs.poisson_arrivals(seed, njobs, load * cap)
+    for r, t in zip(reqs, arrivals):
+        r.arrival, r.t_done, r.U = float(t), -1.0, None
+    st_b = srv.serve(reqs)
+    batched_U = [r.U.clone() for r in reqs]
+    for r in reqs:
+        r.t_done, r.U = -1.0, None
+    st_l = serve.single_job_loop(reqs, device=device)
+    same = all(torch.equal(a, r.U) for a, r in zip(batched_U, reqs))
+    srv.close()
+    return {"jobs": njobs, "offered_load": load, "loop_capacity_jobs_per_s": cap,
+            "points": int(sum(sp.npts for sp in specs)),
+            "batched": st_b.summary(), "single_job_loop": st_l.summary(),
+            "results_identical_alone_and_in_mix": bool(same)}
 
 
 def run_reference(args):
@@ -352,7 +386,15 @@ def run_ours(args):
         except Exception as exc:  # the baseline is reported, never required
             cpu = {"value": None, "unit": "pts/s", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
-    launches_per_step = 6 + 2 + 1 + 1     # bin: count, 3 scan, scatter, stable; spread: box, combine; interp; advect
+    serving = None
+    if args.serve_jobs > 0:
+        try:
+            serving = serving_bench(device, args.serve_jobs, args.serve_load)
+        except Exception as exc:
+            serving = {"error": repr(exc)}
+
+    launches_per_step = 6 + 2 + 2 + 1     # bin: count, 3 scan, scatter, stable; spread: box, combine;
+    #                                        interp: tiles, invalid points; advect
     line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -363,7 +405,8 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
-            "calls_ms": mean_ms}
+            "calls_ms": mean_ms,
+            "serving": serving}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

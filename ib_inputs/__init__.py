@@ -20,6 +20,7 @@ membranes with the Omori reference shape (Section 4.2, the RBC equation).
 
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass
 
@@ -117,6 +118,7 @@ RBC_R0_UM = 3.91          # reference radius R0 in micrometres (Section 4.2)
 BOX_UM = 16.0             # side of the paper's triply periodic box
 
 
+@functools.lru_cache(maxsize=8)
 def icosphere(subdivisions: int) -> np.ndarray:
     """Vertices of a subdivided icosahedron on the unit sphere (10*4^k + 2 of them)."""
     t = (1.0 + math.sqrt(5.0)) / 2.0
@@ -144,22 +146,27 @@ def icosphere(subdivisions: int) -> np.ndarray:
             ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
             new_faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
         faces = new_faces
-    return np.array(verts)
+    out = np.array(verts)
+    out.setflags(write=False)
+    return out
 
 
 def _omori_p(r):
     return 0.105 + r * r - 0.56 * r ** 4
 
 
+@functools.lru_cache(maxsize=16)
 def rbc_surface(R0: float, subdivisions: int = 4) -> np.ndarray:
     """Omori RBC surface points in the body frame, from an icosphere by (theta, phi) = (atan2(y,x), asin z)."""
     s = icosphere(subdivisions)
     theta = np.arctan2(s[:, 1], s[:, 0])
     phi = np.arcsin(np.clip(s[:, 2], -1.0, 1.0))
     cphi = np.cos(phi)
-    return np.stack([R0 * np.cos(theta) * cphi,
-                     R0 * np.sin(theta) * cphi,
-                     R0 * _omori_p(cphi) * np.sin(phi)], axis=1)
+    out = np.stack([R0 * np.cos(theta) * cphi,
+                    R0 * np.sin(theta) * cphi,
+                    R0 * _omori_p(cphi) * np.sin(phi)], axis=1)
+    out.setflags(write=False)
+    return out
 
 
 def rbc_half_thickness(rho: np.ndarray, R0: float) -> np.ndarray:

@@ -57,6 +57,10 @@ bool fill_job(Job& jb, int dim, const int n[3], const double L[3], int tile) {
     jb.scale[b] = (double)nb / Lb;
     if (!isfinite(jb.scale[b]) || !(jb.scale[b] > 0.0)) return false;
     short_scale(jb.scale[b], &jb.sS[b], &jb.sE[b]);
+    jb.fastc[b] = (jb.sS[b] > 0 && jb.sE[b] >= -60 && jb.sE[b] <= 60) ? 1 : 0;
+    jb.sSf[b] = (float)jb.sS[b];
+    jb.p2E[b] = jb.fastc[b] ? ldexpf(1.0f, jb.sE[b]) : 0.0f;
+    jb.itile[b] = live ? (nb + interp_tile_side(dim) - 1) / interp_tile_side(dim) : 1;
     jb.Lf[b] = (float)Lb;
     jb.Ld[b] = Lb;
     if (live) {
@@ -68,6 +72,7 @@ bool fill_job(Job& jb, int dim, const int n[3], const double L[3], int tile) {
   jb.ncell = ncell;
   jb.hmd = hmd;
   jb.ntiles = (long long)jb.ntile[0] * jb.ntile[1] * jb.ntile[2];
+  jb.nitiles = (long long)jb.itile[0] * jb.itile[1] * jb.itile[2];
   return true;
 }
 
@@ -354,8 +359,7 @@ ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u
   J.one.U = U;
   J.njobs = 1;
   const double scale = (flags & IB_ADJOINT) ? p->job.hmd : 1.0;
-  set_tiles(J.one, p->desc.dim, p->tile_plain);
-  if (launch_interp(J, p->sh, call_bins(p, npts), J.one.ntiles, p->tile_plain, p->desc.dtype, scale, s) != cudaSuccess)
+  if (launch_interp(J, p->sh, call_bins(p, npts), J.one.nitiles, p->desc.dtype, scale, s) != cudaSuccess)
     return IB_ERR_CUDA;
   return IB_OK;
 }
@@ -506,7 +510,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
     if (cudaEventSynchronize(b->uploaded) != cudaSuccess) return IB_ERR_CUDA;
     b->pending = false;
   }
-  long long cells = 0, pts = 0, tiles = 0;
+  long long cells = 0, pts = 0, tiles = 0, itiles = 0;
   for (int i = 0; i < njobs; ++i) {
     const ib_job& in = jobs[i];
     Job& jb = b->h_stage[i];
@@ -517,6 +521,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
     jb.cell_base = cells;
     jb.pt_base = pts;
     jb.tile_base = tiles;
+    jb.itile_base = itiles;
     jb.npts = in.npts;
     jb.X = in.X;
     jb.G = in.G;
@@ -526,6 +531,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
     cells += jb.ncell;
     pts += in.npts;
     tiles += jb.ntiles;
+    itiles += jb.nitiles;
     if (cells > b->desc.max_cells || pts > b->desc.max_points || tiles > b->desc.max_tiles) return IB_ERR_CAPACITY;
   }
   if (cudaMemcpyAsync(b->d_table, b->h_stage, sizeof(Job) * (size_t)njobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -543,7 +549,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
   if (launch_bin(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, s) != cudaSuccess)
     return IB_ERR_CUDA;
-  if (launch_interp(J, b->sh, B, tiles, b->tile, b->desc.dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_interp(J, b->sh, B, itiles, b->desc.dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
   return IB_OK;
 }
 

@@ -24,6 +24,11 @@ struct Job {
   int n[3];              // grid points per dimension (n[2] = 1 in 2-D)
   int ntile[3];          // spreading tiles per dimension (ntile[2] = 1 in 2-D)
   int sS[3], sE[3];      // scale_b = sS_b * 2^sE_b exactly when sS_b > 0 ("short" scale)
+  float sSf[3], p2E[3];  // sS_b and 2^sE_b as floats (two-product cell path)
+  int fastc[3];          // 1: the two-product cell path applies to dimension b
+  int itile[3];          // interpolation tiles per dimension
+  long long itile_base;  // first global interpolation tile of this job
+  long long nitiles;
   double scale[3];       // N_b / L_b, computed on the host as (double)N_b / L_b
   double hmd;            // h^-d = prod_b scale_b
   float Lf[3];           // box side per dimension (FP32, for the position update)
@@ -86,6 +91,7 @@ __device__ __forceinline__ const Job& job_at(const Jobs& J, int j) {
 IBGB_JOB_SEARCH(job_of_point, pt_base)
 IBGB_JOB_SEARCH(job_of_cell, cell_base)
 IBGB_JOB_SEARCH(job_of_tile, tile_base)
+IBGB_JOB_SEARCH(job_of_itile, itile_base)
 #undef IBGB_JOB_SEARCH
 
 // ---------------------------------------------------------------------------
@@ -168,6 +174,35 @@ __device__ __forceinline__ uint32_t cell_short(float X, int S, int E, Cell1<floa
   return 0;
 }
 
+// FP32 position with a short scale, the common case: X S = p + e exactly
+// (TwoProduct with one FMA), so u = X scale = (p + e) 2^E exactly.  floor(u)
+// is floor(p), lowered by one when p is an integer and e < 0 (|e| is below
+// half an ulp of p, so it cannot cross any other integer); the same holds for
+// u - 1/2 = (p - 1/2) + e, with p - 1/2 exact while |p| < 2^22.  Offsets are
+// formed as (p - floor) + e and ((floor + 1) - p) - e, so both r and 1 - r
+// keep their relative accuracy.  Outside |p| in [2^-100, 2^22) (or for a
+// non-finite X) the integer path decides.
+__device__ __forceinline__ uint32_t cell_twoprod(float X, const Job& jb, int b, Cell1<float>& c) {
+  const float p0 = X * jb.sSf[b];
+  const float e0 = fmaf(X, jb.sSf[b], -p0);
+  const float p = p0 * jb.p2E[b];
+  const float e = e0 * jb.p2E[b];
+  const float ap = fabsf(p);
+  if (!(ap < 4194304.f) || !(ap >= 7.8886e-31f)) return cell_short(X, jb.sS[b], jb.sE[b], c);
+  float f0 = floorf(p);
+  if (p == f0 && e < 0.f) f0 -= 1.f;
+  const float v = p - 0.5f;
+  float f1 = floorf(v);
+  if (v == f1 && e < 0.f) f1 -= 1.f;
+  c.i0 = (int)f0;
+  c.i1 = (int)f1;
+  c.r0 = (p - f0) + e;
+  c.c0 = ((f0 + 1.f) - p) - e;
+  c.r1 = (v - f1) + e;
+  c.c1 = ((f1 + 1.f) - v) - e;
+  return 0;
+}
+
 // FP64 evaluation, the oracle's formula literally (u = X * scale; u - xi).
 template <typename R>
 __device__ __forceinline__ uint32_t cell_fp64(double X, double scale, Cell1<R>& c) {
@@ -192,6 +227,7 @@ __device__ __forceinline__ uint32_t point_cell(T X, const Job& jb, int b, Cell1<
 
 template <>
 __device__ __forceinline__ uint32_t point_cell<float>(float X, const Job& jb, int b, Cell1<float>& c) {
+  if (jb.fastc[b]) return cell_twoprod(X, jb, b, c);
   if (jb.sS[b] > 0) return cell_short(X, jb.sS[b], jb.sE[b], c);
   return cell_fp64<float>((double)X, jb.scale[b], c);
 }
@@ -234,6 +270,31 @@ __device__ __forceinline__ float mfma(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ double mfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ void msincospi(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void msincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// FP32: q from x rsqrt(x) (x in [1, 2]) and one reciprocal 1/(a b) for the two
+// small weights, rc^2/a = rc^2 b/(a b) and r^2/b = r^2 a/(a b); relative error of
+// a few ulp, far inside the 1e-5 accuracy target.
+__device__ __forceinline__ void weights(int kernel, float r, float rc, float w[4]) {
+  if (kernel == 0) {
+    const float x = fmaf(4.f * r, rc, 1.f);
+    const float q = x * rsqrtf(x);
+    const float a = 1.f + 2.f * rc + q;
+    const float b = 1.f + 2.f * r + q;
+    const float inv = __frcp_rn(a * b);
+    w[0] = rc * rc * b * inv;
+    w[1] = 0.125f * a;
+    w[2] = 0.125f * b;
+    w[3] = r * r * a * inv;
+  } else {
+    float s1, c1, s2, c2;
+    sincospif(0.25f * r, &s1, &c1);
+    sincospif(0.25f * rc, &s2, &c2);
+    w[0] = 0.5f * s2 * s2;
+    w[1] = 0.5f * c1 * c1;
+    w[2] = 0.5f * c2 * c2;
+    w[3] = 0.5f * s1 * s1;
+  }
+}
 
 template <typename R>
 __device__ __forceinline__ void weights(int kernel, R r, R rc, R w[4]) {

@@ -27,10 +27,13 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles_total,
                           int tile, int dtype, bool compensated, bool accumulate, cudaStream_t s);
 
-// Interpolation by tiles (the spreading tile geometry); every value is
-// multiplied by `scale` (1 for plain interpolation).
-cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, long long ntiles, int tile, int dtype,
-                          double scale, cudaStream_t s);
+// Tile side of the interpolation tiles: 8 in 3-D, 32 in 2-D.
+inline int interp_tile_side(int dim) { return dim == 3 ? 8 : 32; }
+
+// Interpolation by tiles (Job::itile geometry); every value is multiplied by
+// `scale` (1 for plain interpolation).
+cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, int dtype, double scale,
+                          cudaStream_t s);
 
 cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,
                             const void* v, double scale, void* D, cudaStream_t s);

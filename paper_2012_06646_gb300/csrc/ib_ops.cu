@@ -19,6 +19,7 @@
 // (each point's sum has one writer), grouped by tile: the tile's grid values
 // plus a 2-node apron are staged in shared memory once, and every point of
 // the tile gathers its support from there.
+#include <cuda_pipeline.h>
 #include <math.h>
 
 #include "ib_internal.h"
@@ -40,19 +41,20 @@ struct Geo {
 
 inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// Tile coordinates of local tile lt of job jb.
+// Tile coordinates of local tile lt of a job with ntile tiles per dimension.
 template <int D, int TS>
-__device__ __forceinline__ void tile_coords(const Job& jb, long long lt, int T0[3], int TE[3]) {
-  const int c0 = (int)(lt % jb.ntile[0]);
-  const long long r = lt / jb.ntile[0];
-  const int c1 = (int)(r % jb.ntile[1]);
-  const int c2 = (int)(r / jb.ntile[1]);
+__device__ __forceinline__ void tile_coords(const int* ntile, const int* n, long long lt, int T0[3], int TE[3]) {
+  const int l = (int)lt;
+  const int c0 = l % ntile[0];
+  const int r = l / ntile[0];
+  const int c1 = r % ntile[1];
+  const int c2 = r / ntile[1];
   T0[0] = c0 * TS;
   T0[1] = c1 * TS;
   T0[2] = (D == 3) ? c2 * TS : 0;
-  TE[0] = min(TS, jb.n[0] - T0[0]);
-  TE[1] = min(TS, jb.n[1] - T0[1]);
-  TE[2] = (D == 3) ? min(TS, jb.n[2] - T0[2]) : 1;
+  TE[0] = min(TS, n[0] - T0[0]);
+  TE[1] = min(TS, n[1] - T0[1]);
+  TE[2] = (D == 3) ? min(TS, n[2] - T0[2]) : 1;
 }
 
 // Rows of one cell layer of a tile, flattened for a warp: lane r < rows
@@ -122,22 +124,24 @@ __device__ __forceinline__ void point_box(const Job& jb, const Shape& sh, const 
 // layer:
 //   1. lanes = points: each lane computes its point's cell, weights and, per
 //      component, the 16 products wx[tx] wy[ty] g (g = h^-d G), the four z
-//      weights and the box offset of the t = -1 corner; it stores them as one
+//      weights, and the box offset of the t = -1 corner; it stores them as one
 //      staging record in shared memory;
 //   2. warp = point: the warp walks the batch's points in order; lane
 //      (tx, ty, tzb) owns the support nodes (tx, ty, tzb) and (tx, ty, tzb+2)
 //      of the point's 4x4x4 box (4x4 in 2-D, lanes 16-31 idle), so the 32
 //      lanes touch 64 distinct nodes and a plain read-modify-write is
-//      race-free; __syncwarp separates consecutive points.
+//      race-free; __syncwarp separates consecutive points.  The next point's
+//      record is read before the current point's additions.
 // Compensated mode keeps (sum, error) per node and adds by TwoSum.
 // ---------------------------------------------------------------------------
 constexpr int kBatch = 16;
 
-__host__ __device__ constexpr int rec_words(int nc) {
-  // 21 nc words (16 nc products, 4 nc z weights, nc offsets), padded to 2 mod 4 so
-  // that the 16 lanes writing records hit distinct banks.
-  int r = 21 * nc;
-  while (r % 4 != 2) ++r;
+// Words of the weight part of a record (16 nc products, 4 nc z weights in 3-D),
+// padded to an odd number of 16-byte chunks so that the lanes' vector stores of
+// stage 1 fall into distinct bank groups.
+__host__ __device__ constexpr int rec_words(int nc, int dim) {
+  int r = 16 * nc + (dim == 3 ? 4 * nc : 0);
+  while ((r / 4) % 2 == 0) r += 4;
   return r;
 }
 
@@ -151,28 +155,64 @@ __device__ __forceinline__ void two_sum_into(T* s, T* e, T v) {
   *e = *e + err;
 }
 
+__device__ __forceinline__ void store4(float* d, float a, float b, float c, float e) {
+  *reinterpret_cast<float4*>(d) = make_float4(a, b, c, e);
+}
+__device__ __forceinline__ void store4(double* d, double a, double b, double c, double e) {
+  reinterpret_cast<double2*>(d)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(d)[1] = make_double2(c, e);
+}
+
+template <typename T>
+struct Rec {        // the part of a record one lane needs in stage 2 (up to 4 components)
+  int base[4];
+  T pv[4], z0[4], z1[4];
+};
+
+template <typename T, int D, int TS>
+__device__ __forceinline__ void load_rec(const T* recT, const int* recI, int REC, int nc, int lane, int tzb,
+                                         Rec<T>& R) {
+  const int4 b4 = *reinterpret_cast<const int4*>(recI);
+  R.base[0] = b4.x;
+  R.base[1] = b4.y;
+  R.base[2] = b4.z;
+  R.base[3] = b4.w;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (a >= nc) break;
+    R.pv[a] = recT[a * 16 + (lane & 15)];
+    if (D == 3) {
+      R.z0[a] = recT[16 * nc + 4 * a + 2 * tzb];
+      R.z1[a] = recT[16 * nc + 4 * a + 2 * tzb + 1];
+    }
+  }
+  (void)REC;
+}
+
 template <typename T, int D, int TS, bool COMP>
 __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constant__ Jobs J, const Shape sh,
                                                             const Bins B, T* __restrict__ boxes) {
   using Gm = Geo<D, TS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = sh.ncomp;
-  const int REC = rec_words(nc);
+  const int REC = rec_words(nc, D);
   T* boxS = reinterpret_cast<T*>(smem_raw);
   T* boxE = boxS + nc * Gm::BV;                                   // compensated mode only
-  T* stage_all = boxS + (COMP ? 2 : 1) * nc * Gm::BV;
+  T* stageT_all = boxS + (COMP ? 2 : 1) * nc * Gm::BV;
+  int* stageI_all = reinterpret_cast<int*>(stageT_all + 4 * kBatch * REC);
   __shared__ uint32_t rstart_s[4][32];
   __shared__ uint32_t rpre_s[4][32];
   const long long gt = blockIdx.x;
   const Job& jb = job_at(J, job_of_tile(J, gt));
   if (jb.G == nullptr) return;
   int T0[3], TE[3];
-  tile_coords<D, TS>(jb, gt - jb.tile_base, T0, TE);
+  tile_coords<D, TS>(jb.ntile, jb.n, gt - jb.tile_base, T0, TE);
   for (int i = threadIdx.x; i < (COMP ? 2 : 1) * nc * Gm::BV; i += kBoxThreads) boxS[i] = (T)0;
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* stage = stage_all + warp * kBatch * REC;
+  T* stageT = stageT_all + warp * kBatch * REC;
+  int* stageI = stageI_all + warp * kBatch * 4;
   const int nlayers = TE[D - 1];
   const int rows = (D == 3) ? TE[1] : 1;
   const T* Gp = (const T*)jb.G;
@@ -191,7 +231,8 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
           const long long li = (long long)g - jb.pt_base;
           PointBox<T, D> P;
           point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, P);
-          T* rec = stage + lane * REC;
+          T* rec = stageT + lane * REC;
+          int offs[4] = {0, 0, 0, 0};
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             if (a >= nc) break;
@@ -205,46 +246,45 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
             }
 #pragma unroll
             for (int yy = 0; yy < 4; ++yy)
-#pragma unroll
-              for (int xx = 0; xx < 4; ++xx) rec[a * 16 + yy * 4 + xx] = wxg[xx] * wy[yy];
+              store4(rec + a * 16 + yy * 4, wxg[0] * wy[yy], wxg[1] * wy[yy], wxg[2] * wy[yy], wxg[3] * wy[yy]);
             int off = (hy ? P.o1[1] : P.o0[1]) * Gm::BX + (hx ? P.o1[0] : P.o0[0]);
             if (D == 3) {
               const bool hz = half_stag(sh, a, 2);
-              const T* wz = hz ? P.w1[D - 1] : P.w0[D - 1];
-              T* zr = rec + 16 * nc + 4 * a;
-              zr[0] = wz[0];
-              zr[1] = wz[2];
-              zr[2] = wz[1];
-              zr[3] = wz[3];
+              T z[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) z[t] = hz ? P.w1[D - 1][t] : P.w0[D - 1][t];
+              store4(rec + 16 * nc + 4 * a, z[0], z[2], z[1], z[3]);
               off += (hz ? P.o1[D - 1] : P.o0[D - 1]) * Gm::BY * Gm::BX;
             }
-            rec[20 * nc + a] = (T)(a * Gm::BV + off);
+            offs[a] = a * Gm::BV + off;
           }
+          *reinterpret_cast<int4*>(stageI + lane * 4) = make_int4(offs[0], offs[1], offs[2], offs[3]);
         }
         __syncwarp();
         // Stage 2: the warp adds the points of the batch one by one.
         const int cnt = (int)min((uint32_t)kBatch, M - base);
+        Rec<T> nxt;
+        load_rec<T, D, TS>(stageT, stageI, REC, nc, lane, tzb, nxt);
         for (int i = 0; i < cnt; ++i) {
-          const T* rec = stage + i * REC;
+          const Rec<T> cur = nxt;
+          if (i + 1 < cnt) load_rec<T, D, TS>(stageT + (i + 1) * REC, stageI + (i + 1) * 4, REC, nc, lane, tzb, nxt);
           if (lane_on) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
               if (a >= nc) break;
-              const int idx = (int)rec[20 * nc + a] + lane_off;
-              const T pv = rec[a * 16 + (lane & 15)];
+              const int idx = cur.base[a] + lane_off;
               if (D == 3) {
-                const T z0 = rec[16 * nc + 4 * a + 2 * tzb];
-                const T z1 = rec[16 * nc + 4 * a + 2 * tzb + 1];
                 if (COMP) {
-                  two_sum_into(boxS + idx, boxE + idx, pv * z0);
-                  two_sum_into(boxS + idx + ZSTEP, boxE + idx + ZSTEP, pv * z1);
+                  two_sum_into(boxS + idx, boxE + idx, cur.pv[a] * cur.z0[a]);
+                  two_sum_into(boxS + idx + ZSTEP, boxE + idx + ZSTEP, cur.pv[a] * cur.z1[a]);
                 } else {
-                  boxS[idx] += pv * z0;
-                  boxS[idx + ZSTEP] += pv * z1;
+                  const T v0 = boxS[idx], v1 = boxS[idx + ZSTEP];
+                  boxS[idx] = v0 + cur.pv[a] * cur.z0[a];
+                  boxS[idx + ZSTEP] = v1 + cur.pv[a] * cur.z1[a];
                 }
               } else {
-                if (COMP) two_sum_into(boxS + idx, boxE + idx, pv);
-                else boxS[idx] += pv;
+                if (COMP) two_sum_into(boxS + idx, boxE + idx, cur.pv[a]);
+                else boxS[idx] += cur.pv[a];
               }
             }
           }
@@ -369,15 +409,16 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
                                                              const T* __restrict__ boxes, long long ncell_total,
                                                              int accumulate) {
   using Gm = Geo<D, TS>;
-  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const int c = blockIdx.x * kThreads + threadIdx.x;    // global cell ids stay below 2^31
   if (c >= ncell_total) return;
   const Job& jb = job_at(J, job_of_cell(J, c));
   if (jb.G == nullptr) return;
-  const long long lc = c - jb.cell_base;
+  const int lc = c - (int)jb.cell_base;
   int x[3];
-  x[0] = (int)(lc % jb.n[0]);
-  x[1] = (int)((lc / jb.n[0]) % jb.n[1]);
-  x[2] = (D == 3) ? (int)(lc / ((long long)jb.n[0] * jb.n[1])) : 0;
+  const int q = lc / jb.n[0];
+  x[0] = lc - q * jb.n[0];
+  x[1] = q % jb.n[1];
+  x[2] = (D == 3) ? q / jb.n[1] : 0;
   bool fast = true;
 #pragma unroll
   for (int b = 0; b < D; ++b) fast = fast && jb.n[b] >= TS + 4;
@@ -445,10 +486,10 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
 
 // ---------------------------------------------------------------------------
 // Interpolation by tiles: the CTA of a tile copies the grid values of the
-// tile plus a 2-node apron (every component) into shared memory, then each
-// thread takes one of the tile's points (cell order) and sums its 4^d
-// support from shared memory.  Points outside every tile (invalid
-// positions) are handled by k_interp_invalid.
+// tile plus a 2-node apron (every component) into shared memory with
+// asynchronous copies, then each thread takes one of the tile's points (cell
+// order) and sums its 4^d support from shared memory.  Points outside every
+// tile (invalid positions) are handled by k_interp_invalid.
 // ---------------------------------------------------------------------------
 constexpr int kInterpThreads = 256;
 
@@ -460,13 +501,35 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   T* box = reinterpret_cast<T*>(smem_raw);
   __shared__ uint32_t rstart[256];
   __shared__ uint32_t rpre[257];
+  __shared__ uint32_t wsum[8];
   const long long gt = blockIdx.x;
-  const Job& jb = job_at(J, job_of_tile(J, gt));
+  const Job& jb = job_at(J, job_of_itile(J, gt));
   if (jb.u == nullptr) return;
   int T0[3], TE[3];
-  tile_coords<D, TS>(jb, gt - jb.tile_base, T0, TE);
+  tile_coords<D, TS>(jb.itile, jb.n, gt - jb.itile_base, T0, TE);
   const int nc = sh.ncomp;
   const int tid = threadIdx.x;
+
+  // Grid values of the box: nodes T0 - 2 .. T0 + TS + 1 (unwrapped), all components,
+  // fetched with cp.async (4- or 8-byte elements) while the row table is built.
+  {
+    const T* u = (const T*)jb.u;
+    const int n0 = jb.n[0], n1 = jb.n[1], n2 = (D == 3) ? jb.n[2] : 1;
+    const int total = nc * Gm::BV;
+    for (int i = tid; i < total; i += kInterpThreads) {
+      const int a = i / Gm::BV;
+      const int rem = i - a * Gm::BV;
+      const int bx = rem % Gm::BX;
+      const int by = (rem / Gm::BX) % Gm::BY;
+      const int bz = rem / (Gm::BX * Gm::BY);
+      const int x = wrapn(T0[0] - 2 + bx, n0);
+      const int y = wrapn(T0[1] - 2 + by, n1);
+      const int z = (D == 3) ? wrapn(T0[2] - 2 + bz, n2) : 0;
+      const T* src = u + (long long)a * jb.ncell + ((long long)z * n1 + y) * n0 + x;
+      __pipeline_memcpy_async(box + i, src, sizeof(T));
+    }
+    __pipeline_commit();
+  }
 
   // Rows of the tile's own cells (x fastest inside a row): start and count in the bins.
   const int nrows = (D == 3) ? TE[1] * TE[2] : TE[1];
@@ -478,7 +541,6 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     st = B.count[cell];
     cnt = B.count[cell + TE[0]] - st;
   }
-  // Block-wide exclusive scan of the row counts (256 threads, one row each).
   {
     const int lane = tid & 31, warp = tid >> 5;
     uint32_t inc = cnt;
@@ -487,7 +549,6 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
       const uint32_t yv = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += yv;
     }
-    __shared__ uint32_t wsum[8];
     if (lane == 31) wsum[warp] = inc;
     __syncthreads();
     if (warp == 0) {
@@ -505,31 +566,12 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     rpre[tid] = before + inc - cnt;
     if (tid == 0) rpre[256] = wsum[7];
   }
-
-  // Grid values of the box: nodes T0 - 2 .. T0 + TS + 1 (unwrapped), all components.
-  const T* u = (const T*)jb.u;
-  const int bz_n = (D == 3) ? min(Gm::BZ, TE[2] + 4) : 1;
-  const int by_n = min(Gm::BY, TE[1] + 4);
-  const int bx_n = min(Gm::BX, TE[0] + 4);
-  const long long s1 = jb.n[0], s2 = (long long)jb.n[0] * jb.n[1];
-  for (int a = 0; a < nc; ++a) {
-    const T* ua = u + a * jb.ncell;
-    T* ba = box + a * Gm::BV;
-    for (int r = tid / 32; r < bz_n * by_n; r += kInterpThreads / 32) {
-      const int by = r % by_n, bz = r / by_n;
-      const int y = wrapn(T0[1] - 2 + by, jb.n[1]);
-      const int z = (D == 3) ? wrapn(T0[2] - 2 + bz, jb.n[2]) : 0;
-      const T* row = ua + y * s1 + z * s2;
-      T* brow = ba + (bz * Gm::BY + by) * Gm::BX;
-      for (int bx = tid & 31; bx < bx_n; bx += 32) brow[bx] = __ldg(row + wrapn(T0[0] - 2 + bx, jb.n[0]));
-    }
-  }
+  __pipeline_wait_prior(0);
   __syncthreads();
 
   const uint32_t P = rpre[256];
-  const int nr = nrows;
   for (uint32_t q = tid; q < P; q += kInterpThreads) {
-    int lo = 0, hi = nr - 1;
+    int lo = 0, hi = nrows - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (rpre[mid] <= q) lo = mid; else hi = mid - 1;
@@ -701,7 +743,8 @@ void allow_smem(K kernel, size_t bytes) {
 template <typename T, int D, int TS>
 size_t spread_smem(int nc, bool comp) {
   using Gm = Geo<D, TS>;
-  return ((comp ? 2 : 1) * (size_t)nc * Gm::BV + 4 * (size_t)kBatch * rec_words(nc)) * sizeof(T);
+  return ((comp ? 2 : 1) * (size_t)nc * Gm::BV + 4 * (size_t)kBatch * rec_words(nc, D)) * sizeof(T) +
+         4 * (size_t)kBatch * 4 * sizeof(int);
 }
 
 template <typename T, int D, int TS>
@@ -735,7 +778,7 @@ int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp) {
   // 16^3 tiles when the box (20^3 entries per component, two planes when
   // compensated) and the staging records fit in 220 KB of shared memory.
   const size_t box = 20 * 20 * 20 * (size_t)elem_bytes * (comp ? 2 : 1) * ncomp;
-  const size_t stage = 4 * (size_t)kBatch * rec_words(ncomp) * elem_bytes;
+  const size_t stage = 4 * (size_t)kBatch * (rec_words(ncomp, dim) * elem_bytes + 4 * sizeof(int));
   return (box + stage <= 220 * 1024) ? 16 : 8;
 }
 
@@ -771,16 +814,14 @@ cudaError_t interp_impl(const Jobs& J, const Shape& sh, const Bins& B, long long
   return cudaGetLastError();
 }
 
-cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, long long ntiles, int tile, int dtype,
-                          double scale, cudaStream_t s) {
+cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, int dtype, double scale,
+                          cudaStream_t s) {
   if (dtype == 0) {
-    if (sh.dim == 2) return interp_impl<float, 2, 32>(J, sh, B, ntiles, scale, s);
-    if (tile == 16) return interp_impl<float, 3, 16>(J, sh, B, ntiles, scale, s);
-    return interp_impl<float, 3, 8>(J, sh, B, ntiles, scale, s);
+    if (sh.dim == 2) return interp_impl<float, 2, 32>(J, sh, B, nitiles, scale, s);
+    return interp_impl<float, 3, 8>(J, sh, B, nitiles, scale, s);
   }
-  if (sh.dim == 2) return interp_impl<double, 2, 32>(J, sh, B, ntiles, scale, s);
-  if (tile == 16) return interp_impl<double, 3, 16>(J, sh, B, ntiles, scale, s);
-  return interp_impl<double, 3, 8>(J, sh, B, ntiles, scale, s);
+  if (sh.dim == 2) return interp_impl<double, 2, 32>(J, sh, B, nitiles, scale, s);
+  return interp_impl<double, 3, 8>(J, sh, B, nitiles, scale, s);
 }
 
 cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,

@@ -120,30 +120,30 @@ __device__ __forceinline__ void point_box(const Job& jb, const Shape& sh, const 
 }
 
 // ---------------------------------------------------------------------------
-// Spreading into a tile box.  Two stages per batch of kBatch points of a cell
+// Spreading into a tile box, one CTA per (tile, component).  The box holds
+// one component of the tile plus a 2-node apron in shared memory (two planes
+// in compensated mode).  Two stages per batch of kBatch points of a cell
 // layer:
-//   1. lanes = points: each lane computes its point's cell, weights and, per
-//      component, the 16 products wx[tx] wy[ty] g (g = h^-d G), the four z
-//      weights, and the box offset of the t = -1 corner; it stores them as one
-//      staging record in shared memory;
+//   1. lanes = points: each lane computes its point's cell in each dimension,
+//      the component's four weights per dimension and, for the component, the
+//      16 products wx[tx] wy[ty] g (g = h^-d G), the four z weights, and the
+//      box offset of the t = -1 corner; it stores them as one staging record;
 //   2. warp = point: the warp walks the batch's points in order; lane
 //      (tx, ty, tzb) owns the support nodes (tx, ty, tzb) and (tx, ty, tzb+2)
 //      of the point's 4x4x4 box (4x4 in 2-D, lanes 16-31 idle), so the 32
 //      lanes touch 64 distinct nodes and a plain read-modify-write is
 //      race-free; __syncwarp separates consecutive points.  The next point's
-//      record is read before the current point's additions.
+//      record is read before the current point's additions, and the next
+//      batch's point data is fetched from global memory before this batch's
+//      additions.
 // Compensated mode keeps (sum, error) per node and adds by TwoSum.
 // ---------------------------------------------------------------------------
-constexpr int kBatch = 16;
+constexpr int kBatch = 32;
 
-// Words of the weight part of a record (16 nc products, 4 nc z weights in 3-D),
-// padded to an odd number of 16-byte chunks so that the lanes' vector stores of
+// Words of a record: 16 products (+ 4 z weights in 3-D) + the box offset,
+// padded to an odd number of 16-byte chunks so the lanes' vector stores of
 // stage 1 fall into distinct bank groups.
-__host__ __device__ constexpr int rec_words(int nc, int dim) {
-  int r = 16 * nc + (dim == 3 ? 4 * nc : 0);
-  while ((r / 4) % 2 == 0) r += 4;
-  return r;
-}
+__host__ __device__ constexpr int rec_words(int dim) { return dim == 3 ? 28 : 20; }
 
 template <typename T>
 __device__ __forceinline__ void two_sum_into(T* s, T* e, T v) {
@@ -163,59 +163,51 @@ __device__ __forceinline__ void store4(double* d, double a, double b, double c, 
   reinterpret_cast<double2*>(d)[1] = make_double2(c, e);
 }
 
-template <typename T>
-struct Rec {        // the part of a record one lane needs in stage 2 (up to 4 components)
-  int base[4];
-  T pv[4], z0[4], z1[4];
-};
-
-template <typename T, int D, int TS>
-__device__ __forceinline__ void load_rec(const T* recT, const int* recI, int REC, int nc, int lane, int tzb,
-                                         Rec<T>& R) {
-  const int4 b4 = *reinterpret_cast<const int4*>(recI);
-  R.base[0] = b4.x;
-  R.base[1] = b4.y;
-  R.base[2] = b4.z;
-  R.base[3] = b4.w;
+// Cell offset (box coordinates of the t = -1 node) and weights of one
+// component of a point, in every dimension.
+template <typename T, int D>
+__device__ __forceinline__ void point_comp(const Job& jb, const Shape& sh, const T* xp, const int T0[3], int a,
+                                           int o[3], T w[3][4]) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    if (a >= nc) break;
-    R.pv[a] = recT[a * 16 + (lane & 15)];
-    if (D == 3) {
-      R.z0[a] = recT[16 * nc + 4 * a + 2 * tzb];
-      R.z1[a] = recT[16 * nc + 4 * a + 2 * tzb + 1];
-    }
+  for (int b = 0; b < D; ++b) {
+    Cell1<T> c;
+    point_cell<T>(xp[b], jb, b, c);
+    const int n = jb.n[b];
+    const int cphys = ((unsigned)c.i0 < (unsigned)n) ? c.i0 : modn(c.i0, n);
+    const bool h = half_stag(sh, a, b);
+    o[b] = cphys - T0[b] + 1 + (h ? (c.i1 - c.i0) : 0);
+    if (h) weights(sh.kernel, c.r1, c.c1, w[b]);
+    else weights(sh.kernel, c.r0, c.c0, w[b]);
   }
-  (void)REC;
 }
 
 template <typename T, int D, int TS, bool COMP>
 __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constant__ Jobs J, const Shape sh,
                                                             const Bins B, T* __restrict__ boxes) {
   using Gm = Geo<D, TS>;
+  constexpr int REC = rec_words(D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nc = sh.ncomp;
-  const int REC = rec_words(nc, D);
   T* boxS = reinterpret_cast<T*>(smem_raw);
-  T* boxE = boxS + nc * Gm::BV;                                   // compensated mode only
-  T* stageT_all = boxS + (COMP ? 2 : 1) * nc * Gm::BV;
-  int* stageI_all = reinterpret_cast<int*>(stageT_all + 4 * kBatch * REC);
+  T* boxE = boxS + Gm::BV;                                        // compensated mode only
+  T* stage_all = boxS + (COMP ? 2 : 1) * Gm::BV;
   __shared__ uint32_t rstart_s[4][32];
   __shared__ uint32_t rpre_s[4][32];
-  const long long gt = blockIdx.x;
+  const int nc = sh.ncomp;
+  const long long gt = blockIdx.x / nc;
+  const int a = blockIdx.x - (int)gt * nc;
   const Job& jb = job_at(J, job_of_tile(J, gt));
   if (jb.G == nullptr) return;
   int T0[3], TE[3];
   tile_coords<D, TS>(jb.ntile, jb.n, gt - jb.tile_base, T0, TE);
-  for (int i = threadIdx.x; i < (COMP ? 2 : 1) * nc * Gm::BV; i += kBoxThreads) boxS[i] = (T)0;
+  for (int i = threadIdx.x; i < (COMP ? 2 : 1) * Gm::BV; i += kBoxThreads) boxS[i] = (T)0;
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* stageT = stageT_all + warp * kBatch * REC;
-  int* stageI = stageI_all + warp * kBatch * 4;
+  T* stage = stage_all + warp * kBatch * REC;
   const int nlayers = TE[D - 1];
   const int rows = (D == 3) ? TE[1] : 1;
   const T* Gp = (const T*)jb.G;
+  const T* Xg = (const T*)jb.X;
   const T hmd = (T)jb.hmd;
   const int tx = lane & 3, ty = (lane >> 2) & 3, tzb = lane >> 4;
   const int lane_off = (D == 3) ? ((tzb * Gm::BY + ty) * Gm::BX + tx) : (ty * Gm::BX + tx);
@@ -224,68 +216,77 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
   for (int phase = 0; phase < 5; ++phase) {
     for (int l = 5 * warp + phase; l < nlayers; l += 20) {
       const uint32_t M = layer_rows<D>(jb, B, T0, TE, l, lane, rstart_s[warp], rpre_s[warp]);
+      // point data of the first batch
+      T xs[D], gs = (T)0;
+      if (lane < M) {
+        const long long li = (long long)B.perm[layer_pos(lane, rows, rstart_s[warp], rpre_s[warp])] - jb.pt_base;
+#pragma unroll
+        for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
+        gs = Gp[li * nc + a];
+      }
       for (uint32_t base = 0; base < M; base += kBatch) {
-        // Stage 1: lane q < kBatch prepares the record of point base + q.
-        if (lane < kBatch && base + lane < M) {
-          const uint32_t g = B.perm[layer_pos(base + lane, rows, rstart_s[warp], rpre_s[warp])];
-          const long long li = (long long)g - jb.pt_base;
-          PointBox<T, D> P;
-          point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, P);
-          T* rec = stageT + lane * REC;
-          int offs[4] = {0, 0, 0, 0};
+        // Stage 1: lane q prepares the record of point base + q.
+        if (base + lane < M) {
+          int o[3] = {0, 0, 0};
+          T w[3][4];
+          point_comp<T, D>(jb, sh, xs, T0, a, o, w);
+          const T ga = hmd * gs;
+          T* rec = stage + lane * REC;
+          T wxg[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            if (a >= nc) break;
-            const T ga = hmd * Gp[li * nc + a];
-            const bool hx = half_stag(sh, a, 0), hy = half_stag(sh, a, 1);
-            T wxg[4], wy[4];
+          for (int t = 0; t < 4; ++t) wxg[t] = w[0][t] * ga;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              wxg[t] = (hx ? P.w1[0][t] : P.w0[0][t]) * ga;
-              wy[t] = hy ? P.w1[1][t] : P.w0[1][t];
-            }
-#pragma unroll
-            for (int yy = 0; yy < 4; ++yy)
-              store4(rec + a * 16 + yy * 4, wxg[0] * wy[yy], wxg[1] * wy[yy], wxg[2] * wy[yy], wxg[3] * wy[yy]);
-            int off = (hy ? P.o1[1] : P.o0[1]) * Gm::BX + (hx ? P.o1[0] : P.o0[0]);
-            if (D == 3) {
-              const bool hz = half_stag(sh, a, 2);
-              T z[4];
-#pragma unroll
-              for (int t = 0; t < 4; ++t) z[t] = hz ? P.w1[D - 1][t] : P.w0[D - 1][t];
-              store4(rec + 16 * nc + 4 * a, z[0], z[2], z[1], z[3]);
-              off += (hz ? P.o1[D - 1] : P.o0[D - 1]) * Gm::BY * Gm::BX;
-            }
-            offs[a] = a * Gm::BV + off;
+          for (int yy = 0; yy < 4; ++yy)
+            store4(rec + yy * 4, wxg[0] * w[1][yy], wxg[1] * w[1][yy], wxg[2] * w[1][yy], wxg[3] * w[1][yy]);
+          int off = o[1] * Gm::BX + o[0];
+          if (D == 3) {
+            store4(rec + 16, w[D - 1][0], w[D - 1][2], w[D - 1][1], w[D - 1][3]);
+            off += o[D - 1] * Gm::BY * Gm::BX;
           }
-          *reinterpret_cast<int4*>(stageI + lane * 4) = make_int4(offs[0], offs[1], offs[2], offs[3]);
+          *reinterpret_cast<int*>(rec + (REC - 1)) = off;     // the record's last slot
+        }
+        // fetch the next batch's point data while this batch is added
+        const uint32_t nq = base + kBatch + lane;
+        if (nq < M) {
+          const long long li = (long long)B.perm[layer_pos(nq, rows, rstart_s[warp], rpre_s[warp])] - jb.pt_base;
+#pragma unroll
+          for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
+          gs = Gp[li * nc + a];
         }
         __syncwarp();
         // Stage 2: the warp adds the points of the batch one by one.
         const int cnt = (int)min((uint32_t)kBatch, M - base);
-        Rec<T> nxt;
-        load_rec<T, D, TS>(stageT, stageI, REC, nc, lane, tzb, nxt);
+        const T* r0 = stage;
+        int nb = *reinterpret_cast<const int*>(r0 + (REC - 1));
+        T npv = r0[lane & 15];
+        T nz0 = (D == 3) ? r0[16 + 2 * tzb] : (T)1;
+        T nz1 = (D == 3) ? r0[17 + 2 * tzb] : (T)0;
         for (int i = 0; i < cnt; ++i) {
-          const Rec<T> cur = nxt;
-          if (i + 1 < cnt) load_rec<T, D, TS>(stageT + (i + 1) * REC, stageI + (i + 1) * 4, REC, nc, lane, tzb, nxt);
+          const int cb = nb;
+          const T pv = npv, z0 = nz0, z1 = nz1;
+          if (i + 1 < cnt) {
+            const T* rn = stage + (i + 1) * REC;
+            nb = *reinterpret_cast<const int*>(rn + (REC - 1));
+            npv = rn[lane & 15];
+            if (D == 3) {
+              nz0 = rn[16 + 2 * tzb];
+              nz1 = rn[17 + 2 * tzb];
+            }
+          }
           if (lane_on) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-              if (a >= nc) break;
-              const int idx = cur.base[a] + lane_off;
-              if (D == 3) {
-                if (COMP) {
-                  two_sum_into(boxS + idx, boxE + idx, cur.pv[a] * cur.z0[a]);
-                  two_sum_into(boxS + idx + ZSTEP, boxE + idx + ZSTEP, cur.pv[a] * cur.z1[a]);
-                } else {
-                  const T v0 = boxS[idx], v1 = boxS[idx + ZSTEP];
-                  boxS[idx] = v0 + cur.pv[a] * cur.z0[a];
-                  boxS[idx + ZSTEP] = v1 + cur.pv[a] * cur.z1[a];
-                }
+            const int idx = cb + lane_off;
+            if (D == 3) {
+              if (COMP) {
+                two_sum_into(boxS + idx, boxE + idx, pv * z0);
+                two_sum_into(boxS + idx + ZSTEP, boxE + idx + ZSTEP, pv * z1);
               } else {
-                if (COMP) two_sum_into(boxS + idx, boxE + idx, cur.pv[a]);
-                else boxS[idx] += cur.pv[a];
+                const T v0 = boxS[idx], v1 = boxS[idx + ZSTEP];
+                boxS[idx] = v0 + pv * z0;
+                boxS[idx + ZSTEP] = v1 + pv * z1;
               }
+            } else {
+              if (COMP) two_sum_into(boxS + idx, boxE + idx, pv);
+              else boxS[idx] += pv;
             }
           }
           __syncwarp();
@@ -295,10 +296,10 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
     }
     __syncthreads();
   }
-  // Box -> scratch, 16-byte vectors (the box size in bytes is a multiple of 16).
-  const int nvec = (int)((COMP ? 2 : 1) * nc * Gm::BV * sizeof(T) / 16);
+  // Box -> scratch [tile][comp][plane][BV], 16-byte vectors.
+  const int nvec = (int)((COMP ? 2 : 1) * Gm::BV * sizeof(T) / 16);
   const uint4* src = reinterpret_cast<const uint4*>(boxS);
-  uint4* dst = reinterpret_cast<uint4*>(boxes + gt * (long long)((COMP ? 2 : 1) * nc * Gm::BV));
+  uint4* dst = reinterpret_cast<uint4*>(boxes + (gt * nc + a) * (long long)((COMP ? 2 : 1) * Gm::BV));
   for (int i = threadIdx.x; i < nvec; i += kBoxThreads) dst[i] = src[i];
 }
 
@@ -378,7 +379,7 @@ __device__ __noinline__ void combine_general(const Job& jb, const Shape& sh, con
     of[2][0] = 0;
   }
   const int nc = sh.ncomp;
-  const long long box_elems = (long long)(CP ? 2 : 1) * nc * Gm::BV;
+  const long long plane = (long long)(CP ? 2 : 1) * Gm::BV;
   T* f = (T*)jb.f;
   for (int a = 0; a < nc; ++a) {
     T S = 0, E = 0;
@@ -386,10 +387,10 @@ __device__ __noinline__ void combine_general(const Job& jb, const Shape& sh, con
       for (int iy = 0; iy < nco[1]; ++iy)
         for (int ix = 0; ix < nco[0]; ++ix) {
           const long long tile = jb.tile_base + tl[0][ix] + (long long)jb.ntile[0] * (tl[1][iy] + (long long)jb.ntile[1] * tl[2][iz]);
-          const long long idx = tile * box_elems + a * Gm::BV + (of[2][iz] * Gm::BY + of[1][iy]) * Gm::BX + of[0][ix];
+          const long long idx = (tile * nc + a) * plane + (of[2][iz] * Gm::BY + of[1][iy]) * Gm::BX + of[0][ix];
           if (CP) {
             const T sv = boxes[idx];
-            const T ev = boxes[idx + nc * Gm::BV];
+            const T ev = boxes[idx + Gm::BV];
             const T sum = S + sv;
             const T bb = sum - S;
             E += ((S - (sum - bb)) + (sv - bb)) + ev;
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
     cz.t0 = cz.o0 = cz.t1 = cz.o1 = cz.t2 = cz.o2 = 0;
   }
   const int nc = sh.ncomp;
-  const long long box_elems = (long long)(CP ? 2 : 1) * nc * Gm::BV;
+  const long long plane = (long long)(CP ? 2 : 1) * Gm::BV;
   T* f = (T*)jb.f;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -449,14 +450,14 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
       for (int iy = 0; iy < 3; ++iy) {
         if (iy >= cy.n) break;
         const long long trow = jb.tile_base + (long long)jb.ntile[0] * (cy.t(iy) + (long long)jb.ntile[1] * cz.t(iz));
-        const int orow = a * Gm::BV + (cz.o(iz) * Gm::BY + cy.o(iy)) * Gm::BX;
+        const int orow = (cz.o(iz) * Gm::BY + cy.o(iy)) * Gm::BX;
 #pragma unroll
         for (int ix = 0; ix < 3; ++ix) {
           if (ix >= cx.n) break;
-          const long long idx = (trow + cx.t(ix)) * box_elems + orow + cx.o(ix);
+          const long long idx = ((trow + cx.t(ix)) * nc + a) * plane + orow + cx.o(ix);
           if (CP) {
             const T sv = boxes[idx];
-            const T ev = boxes[idx + nc * Gm::BV];
+            const T ev = boxes[idx + Gm::BV];
             const T sum = S + sv;
             const T bb = sum - S;
             E += ((S - (sum - bb)) + (sv - bb)) + ev;
@@ -741,23 +742,23 @@ void allow_smem(K kernel, size_t bytes) {
 }
 
 template <typename T, int D, int TS>
-size_t spread_smem(int nc, bool comp) {
+size_t spread_smem(bool comp) {
   using Gm = Geo<D, TS>;
-  return ((comp ? 2 : 1) * (size_t)nc * Gm::BV + 4 * (size_t)kBatch * rec_words(nc, D)) * sizeof(T) +
-         4 * (size_t)kBatch * 4 * sizeof(int);
+  return ((comp ? 2 : 1) * (size_t)Gm::BV + 4 * (size_t)kBatch * rec_words(D)) * sizeof(T);
 }
 
 template <typename T, int D, int TS>
 cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool comp,
                         bool accumulate, cudaStream_t s) {
   if (ntiles > 0) {
-    const size_t bytes = spread_smem<T, D, TS>(sh.ncomp, comp);
+    const size_t bytes = spread_smem<T, D, TS>(comp);
+    const unsigned grid = (unsigned)(ntiles * sh.ncomp);
     if (comp) {
       allow_smem(k_spread_box<T, D, TS, true>, bytes);
-      k_spread_box<T, D, TS, true><<<(unsigned)ntiles, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
+      k_spread_box<T, D, TS, true><<<grid, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
     } else {
       allow_smem(k_spread_box<T, D, TS, false>, bytes);
-      k_spread_box<T, D, TS, false><<<(unsigned)ntiles, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
+      k_spread_box<T, D, TS, false><<<grid, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
     }
   }
   if (B.ncell_total > 0) {
@@ -774,12 +775,12 @@ cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* box
 }  // namespace
 
 int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp) {
-  if (dim == 2) return 32;
-  // 16^3 tiles when the box (20^3 entries per component, two planes when
-  // compensated) and the staging records fit in 220 KB of shared memory.
-  const size_t box = 20 * 20 * 20 * (size_t)elem_bytes * (comp ? 2 : 1) * ncomp;
-  const size_t stage = 4 * (size_t)kBatch * (rec_words(ncomp, dim) * elem_bytes + 4 * sizeof(int));
-  return (box + stage <= 220 * 1024) ? 16 : 8;
+  (void)elem_bytes;
+  (void)comp;
+  (void)ncomp;
+  // One CTA per (tile, component): a 20^3 box of one component (two planes
+  // when compensated, FP64 at most 128 KB) and the staging records always fit.
+  return dim == 2 ? 32 : 16;
 }
 
 size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp) {

@@ -27,7 +27,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B) {
   const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (g >= B.npts_total) return;
-  const Job& jb = job_at(J, job_of_point(J, g));
+  const Job jb = job_at(J, job_of_point(J, g));
   const T* X = (const T*)jb.X + (g - jb.pt_base) * D;
   uint32_t err = 0;
   long long key = 0, stride = 1;

@@ -193,9 +193,12 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
   __shared__ uint32_t rstart_s[4][32];
   __shared__ uint32_t rpre_s[4][32];
   const int nc = sh.ncomp;
+  __shared__ Job sjob;                  // one copy of the job per CTA (broadcast reads)
   const long long gt = blockIdx.x / nc;
   const int a = blockIdx.x - (int)gt * nc;
-  const Job& jb = job_at(J, job_of_tile(J, gt));
+  if (threadIdx.x == 0) sjob = job_at(J, job_of_tile(J, gt));
+  __syncthreads();
+  const Job& jb = sjob;
   if (jb.G == nullptr) return;
   int T0[3], TE[3];
   tile_coords<D, TS>(jb.ntile, jb.n, gt - jb.tile_base, T0, TE);
@@ -368,9 +371,10 @@ __device__ __forceinline__ Cover3 cover_fast(int x, int n, int ntile) {
 }
 
 template <typename T, int D, int TS, bool CP>
-__device__ __noinline__ void combine_general(const Job& jb, const Shape& sh, const T* __restrict__ boxes,
+__device__ __noinline__ void combine_general(const Jobs& J, int j, const Shape& sh, const T* __restrict__ boxes,
                                              const int* x, long long lc, int accumulate) {
   using Gm = Geo<D, TS>;
+  const Job& jb = job_at(J, j);
   int tl[3][kMaxCover], of[3][kMaxCover], nco[3];
   for (int b = 0; b < D; ++b) nco[b] = cover_list<TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
   if (D == 2) {
@@ -412,7 +416,8 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
   using Gm = Geo<D, TS>;
   const int c = blockIdx.x * kThreads + threadIdx.x;    // global cell ids stay below 2^31
   if (c >= ncell_total) return;
-  const Job& jb = job_at(J, job_of_cell(J, c));
+  const int jj = job_of_cell(J, c);
+  const Job jb = job_at(J, jj);
   if (jb.G == nullptr) return;
   const int lc = c - (int)jb.cell_base;
   int x[3];
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 #pragma unroll
   for (int b = 0; b < D; ++b) fast = fast && jb.n[b] >= TS + 4;
   if (!fast) {
-    combine_general<T, D, TS, CP>(jb, sh, boxes, x, lc, accumulate);
+    combine_general<T, D, TS, CP>(J, jj, sh, boxes, x, lc, accumulate);
     return;
   }
   const Cover3 cx = cover_fast<TS>(x[0], jb.n[0], jb.ntile[0]);
@@ -503,8 +508,11 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   __shared__ uint32_t rstart[256];
   __shared__ uint32_t rpre[257];
   __shared__ uint32_t wsum[8];
+  __shared__ Job sjob;                  // one copy of the job per CTA (broadcast reads)
   const long long gt = blockIdx.x;
-  const Job& jb = job_at(J, job_of_itile(J, gt));
+  if (threadIdx.x == 0) sjob = job_at(J, job_of_itile(J, gt));
+  __syncthreads();
+  const Job& jb = sjob;
   if (jb.u == nullptr) return;
   int T0[3], TE[3];
   tile_coords<D, TS>(jb.itile, jb.n, gt - jb.itile_base, T0, TE);
@@ -624,7 +632,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_invalid(const __grid_consta
   const long long p = first + (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= B.npts_total) return;
   const uint32_t g = B.perm[p];
-  const Job& jb = job_at(J, job_of_point(J, (long long)g));
+  const Job jb = job_at(J, job_of_point(J, (long long)g));
   if (jb.u == nullptr) return;
   T* U = (T*)jb.U + ((long long)g - jb.pt_base) * sh.ncomp;
   for (int a = 0; a < sh.ncomp; ++a) U[a] = (T)NAN;
@@ -641,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad(const __grid_constant__ J
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= B.npts_total) return;
   const uint32_t g = B.perm[p];
-  const Job& jb = job_at(J, job_of_point(J, (long long)g));
+  const Job jb = job_at(J, job_of_point(J, (long long)g));
   const long long li = (long long)g - jb.pt_base;
   const int nc = sh.ncomp;
   const T* Xp = (const T*)jb.X + li * D;
@@ -723,7 +731,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_advect(const __grid_constant__ Jobs J, const T* __restrict__ U, T dt,
                                                      T* __restrict__ Xout) {
   const long long e = (long long)blockIdx.x * kThreads + threadIdx.x;
-  const Job& jb = J.one;
+  const Job jb = J.one;
   if (e >= jb.npts * D) return;
   const int b = (int)(e % D);
   const T L = (T)jb.Ld[b];

@@ -58,6 +58,7 @@ bool fill_job(Job& jb, int dim, const int n[3], const double L[3], int tile) {
     if (!isfinite(jb.scale[b]) || !(jb.scale[b] > 0.0)) return false;
     short_scale(jb.scale[b], &jb.sS[b], &jb.sE[b]);
     jb.fastc[b] = (jb.sS[b] > 0 && jb.sE[b] >= -60 && jb.sE[b] <= 60) ? 1 : 0;
+    jb.mg[b] = nb >= 2 ? (~0ull) / (unsigned long long)nb + 1ull : 0ull;
     jb.sSf[b] = (float)jb.sS[b];
     jb.p2E[b] = jb.fastc[b] ? ldexpf(1.0f, jb.sE[b]) : 0.0f;
     jb.itile[b] = live ? (nb + interp_tile_side(dim) - 1) / interp_tile_side(dim) : 1;

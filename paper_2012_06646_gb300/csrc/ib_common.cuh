@@ -26,6 +26,7 @@ struct Job {
   int sS[3], sE[3];      // scale_b = sS_b * 2^sE_b exactly when sS_b > 0 ("short" scale)
   float sSf[3], p2E[3];  // sS_b and 2^sE_b as floats (two-product cell path)
   int fastc[3];          // 1: the two-product cell path applies to dimension b
+  unsigned long long mg[3];  // floor(2^64 / n_b) + 1 (exact division of 32-bit values by n_b >= 2)
   int itile[3];          // interpolation tiles per dimension
   long long itile_base;  // first global interpolation tile of this job
   long long nitiles;
@@ -235,6 +236,12 @@ __device__ __forceinline__ uint32_t point_cell<float>(float X, const Job& jb, in
 template <>
 __device__ __forceinline__ uint32_t point_cell<double>(double X, const Job& jb, int b, Cell1<double>& c) {
   return cell_fp64<double>(X, jb.scale[b], c);
+}
+
+// x / d for 0 <= x < 2^32 and d >= 1, with M = floor(2^64 / d) + 1 (M unused for
+// d = 1): floor(x M / 2^64) = floor(x / d) because x d < 2^64.
+__device__ __forceinline__ int udiv(int x, int d, unsigned long long M) {
+  return d == 1 ? x : (int)__umul64hi((unsigned long long)(unsigned)x, M);
 }
 
 // Periodic wrap of v into [0, n) for v in [-2n, 3n).

@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
         T npv = r0[lane & 15];
         T nz0 = (D == 3) ? r0[16 + 2 * tzb] : (T)1;
         T nz1 = (D == 3) ? r0[17 + 2 * tzb] : (T)0;
+#pragma unroll 4
         for (int i = 0; i < cnt; ++i) {
           const int cb = nb;
           const T pv = npv, z0 = nz0, z1 = nz1;
@@ -421,10 +422,15 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
   if (jb.G == nullptr) return;
   const int lc = c - (int)jb.cell_base;
   int x[3];
-  const int q = lc / jb.n[0];
+  const int q = udiv(lc, jb.n[0], jb.mg[0]);
   x[0] = lc - q * jb.n[0];
-  x[1] = q % jb.n[1];
-  x[2] = (D == 3) ? q / jb.n[1] : 0;
+  if (D == 3) {
+    x[2] = udiv(q, jb.n[1], jb.mg[1]);
+    x[1] = q - x[2] * jb.n[1];
+  } else {
+    x[1] = q;
+    x[2] = 0;
+  }
   bool fast = true;
 #pragma unroll
   for (int b = 0; b < D; ++b) fast = fast && jb.n[b] >= TS + 4;
@@ -443,37 +449,43 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
   }
   const int nc = sh.ncomp;
   const long long plane = (long long)(CP ? 2 : 1) * Gm::BV;
-  T* f = (T*)jb.f;
+  T S[4] = {0, 0, 0, 0}, E[4] = {0, 0, 0, 0};
+  // Covering boxes in increasing (z, y, x) unwrapped order; every component
+  // sums them in that same order.
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    if (a >= nc) break;
-    T S = 0, E = 0;
+  for (int iz = 0; iz < 3; ++iz) {
+    if (iz >= cz.n) break;
 #pragma unroll
-    for (int iz = 0; iz < 3; ++iz) {
-      if (iz >= cz.n) break;
+    for (int iy = 0; iy < 3; ++iy) {
+      if (iy >= cy.n) break;
+      const int trow = (int)jb.tile_base + jb.ntile[0] * (cy.t(iy) + jb.ntile[1] * cz.t(iz));
+      const int orow = (cz.o(iz) * Gm::BY + cy.o(iy)) * Gm::BX;
 #pragma unroll
-      for (int iy = 0; iy < 3; ++iy) {
-        if (iy >= cy.n) break;
-        const long long trow = jb.tile_base + (long long)jb.ntile[0] * (cy.t(iy) + (long long)jb.ntile[1] * cz.t(iz));
-        const int orow = (cz.o(iz) * Gm::BY + cy.o(iy)) * Gm::BX;
+      for (int ix = 0; ix < 3; ++ix) {
+        if (ix >= cx.n) break;
+        const T* bp = boxes + (long long)(trow + cx.t(ix)) * nc * plane + (orow + cx.o(ix));
 #pragma unroll
-        for (int ix = 0; ix < 3; ++ix) {
-          if (ix >= cx.n) break;
-          const long long idx = ((trow + cx.t(ix)) * nc + a) * plane + orow + cx.o(ix);
+        for (int a = 0; a < 4; ++a) {
+          if (a >= nc) break;
           if (CP) {
-            const T sv = boxes[idx];
-            const T ev = boxes[idx + Gm::BV];
-            const T sum = S + sv;
-            const T bb = sum - S;
-            E += ((S - (sum - bb)) + (sv - bb)) + ev;
-            S = sum;
+            const T sv = bp[a * plane];
+            const T ev = bp[a * plane + Gm::BV];
+            const T sum = S[a] + sv;
+            const T bb = sum - S[a];
+            E[a] += ((S[a] - (sum - bb)) + (sv - bb)) + ev;
+            S[a] = sum;
           } else {
-            S += boxes[idx];
+            S[a] += bp[a * plane];
           }
         }
       }
     }
-    const T val = CP ? S + E : S;
+  }
+  T* f = (T*)jb.f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (a >= nc) break;
+    const T val = CP ? S[a] + E[a] : S[a];
     const long long o = a * jb.ncell + lc;
     f[o] = accumulate ? f[o] + val : val;
   }
@@ -520,22 +532,30 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   const int tid = threadIdx.x;
 
   // Grid values of the box: nodes T0 - 2 .. T0 + TS + 1 (unwrapped), all components,
-  // fetched with cp.async (4- or 8-byte elements) while the row table is built.
+  // fetched with cp.async.  Wrapped row offsets come from two small tables; each
+  // thread keeps one x position (BXP, the row length rounded up to a power of
+  // two, divides the block size), so an element costs a few integer operations.
   {
+    constexpr int BXP = (Gm::BX <= 16) ? 16 : 64;
+    constexpr int RSTEP = kInterpThreads / BXP;         // rows per block iteration
+    __shared__ int yoff_s[Gm::BY];
+    __shared__ int zoff_s[Gm::BZ];
+    const int n0 = jb.n[0], n1 = jb.n[1];
+    if (tid < Gm::BY) yoff_s[tid] = wrapn(T0[1] - 2 + tid, n1) * n0;
+    if (tid < Gm::BZ) zoff_s[tid] = (D == 3) ? wrapn(T0[2] - 2 + tid, jb.n[2]) * n0 * n1 : 0;
+    __syncthreads();
     const T* u = (const T*)jb.u;
-    const int n0 = jb.n[0], n1 = jb.n[1], n2 = (D == 3) ? jb.n[2] : 1;
-    const int total = nc * Gm::BV;
-    for (int i = tid; i < total; i += kInterpThreads) {
-      const int a = i / Gm::BV;
-      const int rem = i - a * Gm::BV;
-      const int bx = rem % Gm::BX;
-      const int by = (rem / Gm::BX) % Gm::BY;
-      const int bz = rem / (Gm::BX * Gm::BY);
-      const int x = wrapn(T0[0] - 2 + bx, n0);
-      const int y = wrapn(T0[1] - 2 + by, n1);
-      const int z = (D == 3) ? wrapn(T0[2] - 2 + bz, n2) : 0;
-      const T* src = u + (long long)a * jb.ncell + ((long long)z * n1 + y) * n0 + x;
-      __pipeline_memcpy_async(box + i, src, sizeof(T));
+    const int nrows_box = nc * Gm::BZ * Gm::BY;
+    for (int bx0 = tid % BXP; bx0 < Gm::BX; bx0 += BXP) {
+      const int xw = wrapn(T0[0] - 2 + bx0, n0);
+      for (int row = tid / BXP; row < nrows_box; row += RSTEP) {
+        const int a = row / (Gm::BZ * Gm::BY);
+        const int rem = row - a * (Gm::BZ * Gm::BY);
+        const int bz = rem / Gm::BY;
+        const int by = rem - bz * Gm::BY;
+        const T* src = u + (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
+        __pipeline_memcpy_async(box + row * Gm::BX + bx0, src, sizeof(T));
+      }
     }
     __pipeline_commit();
   }

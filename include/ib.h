@@ -210,6 +210,36 @@ ib_status ib_batch_run(ib_batch batch, int njobs, const ib_job* jobs, unsigned f
 /* As ib_plan_check, for the batch object's device error word. */
 ib_status ib_batch_check(ib_batch batch, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Interpolation for callers that cannot allocate device memory.  The paper
+ * has no counterpart: it exists for callers that may not call cudaMalloc,
+ * such as code running inside a CUDA graph being captured, a host callback,
+ * or a process whose allocator is owned by someone else.  Same result as
+ * ib_plan_create + ib_interpolate + ib_plan_destroy for the grid `desc`, but
+ * the binning scratch is a fixed device array compiled into the library
+ * (about 24 MB, held on every GPU that loads the library until the process
+ * exits), so nothing is allocated or freed: no cudaMalloc, cudaFree or
+ * allocating library routine runs.
+ *   - desc: grid description as for ib_plan_create (max_points and flags are
+ *     not used; flags must be 0).  X (npts, dim), u [ncomp][grid] read,
+ *     U (npts, ncomp) written; device pointers owned by the caller.
+ *   - Limits: n0 n1 n2 <= IB_NOALLOC_MAX_CELLS and npts <= IB_NOALLOC_MAX_POINTS,
+ *     else IB_ERR_CAPACITY with nothing enqueued.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call on each
+ *     device before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; each call clears what must start at zero.  Calls whose work
+ *     overlaps on the GPU (different streams, or host threads) race on the
+ *     array: order them on one stream.
+ *   - Non-finite or out-of-range positions interpolate to NaN (no error word
+ *     is read back).
+ * ------------------------------------------------------------------------- */
+#define IB_NOALLOC_MAX_CELLS (1ll << 21)
+#define IB_NOALLOC_MAX_POINTS (1ll << 20)
+ib_status ib_interpolate_noalloc(const ib_plan_desc* desc, long long npts, const void* X, const void* u, void* U,
+                                 void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* ib_status_string(ib_status status);
 

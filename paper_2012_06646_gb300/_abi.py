@@ -37,6 +37,9 @@ IB_COMPENSATED = 0x2
 IB_REUSE_BINS = 0x4
 IB_ADJOINT = 0x8
 
+IB_NOALLOC_MAX_CELLS = 1 << 21
+IB_NOALLOC_MAX_POINTS = 1 << 20
+
 
 class ib_plan_desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3),
@@ -80,6 +83,7 @@ SIGNATURES = {
     "ib_batch_destroy": (_st, [_vp]),
     "ib_batch_run": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_job), ctypes.c_uint, _vp]),
     "ib_batch_check": (_st, [_vp, _vp]),
+    "ib_interpolate_noalloc": (_st, [ctypes.POINTER(ib_plan_desc), _ll, _vp, _vp, _vp, _vp]),
     "ib_status_string": (ctypes.c_char_p, [_st]),
     "ib_version": (ctypes.c_char_p, []),
 }

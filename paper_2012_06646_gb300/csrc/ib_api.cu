@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "../../include/ib.h"
@@ -560,3 +561,82 @@ ib_status ib_batch_check(ib_batch b, void* stream) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Interpolation without any allocation.  Its binning scratch is a fixed
+// device array in this file, sized for IB_NOALLOC_MAX_CELLS cells and
+// IB_NOALLOC_MAX_POINTS points; every GPU that loads the library holds it
+// until the process exits.  Host code may not pass the array's name to a
+// kernel (on the host it only stands for the symbol); the device address is
+// looked up once per device with cudaGetSymbolAddress on the first call made
+// on that device.
+// ------------------------------------------------------------------------
+namespace {
+
+constexpr long long kNaCells = IB_NOALLOC_MAX_CELLS;
+constexpr long long kNaPoints = IB_NOALLOC_MAX_POINTS;
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kNaBytes =
+    na_align(sizeof(uint32_t) * (size_t)(kNaCells + 2)) +                          // counts / cell starts
+    4 * na_align(sizeof(uint32_t) * (size_t)kNaPoints) +                            // key, rank, perm_tmp, perm
+    na_align(sizeof(uint32_t) * (size_t)((kNaCells + 1 + kScanChunkCells - 1) / kScanChunkCells + 1)) +
+    na_align(sizeof(uint32_t));                                                     // error word
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" ib_status ib_interpolate_noalloc(const ib_plan_desc* desc, long long npts, const void* X, const void* u,
+                                            void* U, void* stream) {
+  if (!desc || !valid_shape(desc->dim, desc->grid, desc->kernel, desc->dtype, desc->ncomp)) return IB_ERR_INVALID_ARG;
+  if (desc->flags != 0 || npts < 0 || (npts > 0 && (!X || !u || !U))) return IB_ERR_INVALID_ARG;
+  Job jb;
+  if (!fill_job(jb, desc->dim, desc->n, desc->L, spread_tile_side(desc->dim, entry_bytes(desc->dtype, false), false,
+                                                                  desc->ncomp)))
+    return IB_ERR_INVALID_ARG;
+  if (jb.ncell > kNaCells || npts > kNaPoints) return IB_ERR_CAPACITY;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IB_ERR_CUDA;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return IB_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  const Layout L = make_layout(jb.ncell, npts, 0, 0);
+  if (L.total > kNaBytes) return IB_ERR_CAPACITY;
+  Bins B = carve((char*)base, L);
+  B.ncell_total = jb.ncell;
+  B.npts_total = npts;
+  Shape sh;
+  sh.dim = desc->dim;
+  sh.ncomp = desc->ncomp;
+  sh.mac = desc->grid == IB_GRID_MAC ? 1 : 0;
+  sh.kernel = desc->kernel;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = jb;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.one.u = u;
+  J.one.U = U;
+  J.njobs = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  // The array keeps the previous call's contents: the counts and the error word start from zero.
+  if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(jb.ncell + 2), s) != cudaSuccess) return IB_ERR_CUDA;
+  if (cudaMemsetAsync(B.err, 0, sizeof(uint32_t), s) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_bin(J, sh, B, desc->dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_interp(J, sh, B, J.one.nitiles, desc->dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
+  return IB_OK;
+}

@@ -22,6 +22,7 @@ constexpr int kThreads = 256;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
+static_assert(kScanChunk == kScanChunkCells, "scan chunk size shared with the scratch layout");
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B) {

@@ -15,7 +15,8 @@ int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp);
 // Bytes of one spreading box (all components) for a tile side.
 size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp);
 
-// Number of blocks of the cell-count scan for m entries.
+// Cells per block of the cell-count scan, and the number of blocks for m entries.
+constexpr long long kScanChunkCells = 8192;
 long long scan_blocks(long long m);
 
 // Binning (Algorithm 4 keys, sort and unique-key offsets): count, scan,

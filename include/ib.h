@@ -217,7 +217,7 @@ ib_status ib_batch_check(ib_batch batch, void* stream);
  * or a process whose allocator is owned by someone else.  Same result as
  * ib_plan_create + ib_interpolate + ib_plan_destroy for the grid `desc`, but
  * the binning scratch is a fixed device array compiled into the library
- * (about 24 MB, held on every GPU that loads the library until the process
+ * (about 28 MB, held on every GPU that loads the library until the process
  * exits), so nothing is allocated or freed: no cudaMalloc, cudaFree or
  * allocating library routine runs.
  *   - desc: grid description as for ib_plan_create (max_points and flags are

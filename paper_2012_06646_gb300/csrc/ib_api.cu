@@ -104,7 +104,7 @@ Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t t
   L.count = off;      off += align_up(sizeof(uint32_t) * (size_t)(ncell + 2));
   L.key = off;        off += align_up(sizeof(uint32_t) * (size_t)npts);
   L.rank = off;       off += align_up(sizeof(uint32_t) * (size_t)npts);
-  L.perm_tmp = off;   off += align_up(sizeof(uint32_t) * (size_t)npts);
+  L.perm_tmp = off;   off += align_up(sizeof(uint2) * (size_t)npts);
   L.perm = off;       off += align_up(sizeof(uint32_t) * (size_t)npts);
   L.block_sums = off; off += align_up(sizeof(uint32_t) * (size_t)(scan_blocks(ncell + 1) + 1));
   L.err = off;        off += align_up(sizeof(uint32_t));
@@ -119,7 +119,7 @@ Bins carve(char* base, const Layout& L) {
   B.count = (uint32_t*)(base + L.count);
   B.key = (uint32_t*)(base + L.key);
   B.rank = (uint32_t*)(base + L.rank);
-  B.perm_tmp = (uint32_t*)(base + L.perm_tmp);
+  B.perm_tmp = (uint2*)(base + L.perm_tmp);
   B.perm = (uint32_t*)(base + L.perm);
   B.block_sums = (uint32_t*)(base + L.block_sums);
   B.err = (uint32_t*)(base + L.err);
@@ -338,7 +338,7 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   if (flags & IB_ADJOINT) J.one.hmd = 1.0;
   J.njobs = 1;
   if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp,
-                    (flags & IB_ACCUMULATE) != 0, s) != cudaSuccess)
+                    (flags & IB_ACCUMULATE) != 0, (p->job.n[0] & 1) == 0, s) != cudaSuccess)
     return IB_ERR_CUDA;
   return IB_OK;
 }
@@ -513,8 +513,10 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
     b->pending = false;
   }
   long long cells = 0, pts = 0, tiles = 0, itiles = 0;
+  bool even_n0 = true;
   for (int i = 0; i < njobs; ++i) {
     const ib_job& in = jobs[i];
+    even_n0 = even_n0 && (in.n[0] % 2 == 0);
     Job& jb = b->h_stage[i];
     if (in.npts < 0 || !fill_job(jb, b->desc.dim, in.n, in.L, b->tile)) return IB_ERR_INVALID_ARG;
     if (in.npts > 0 && !in.X) return IB_ERR_INVALID_ARG;
@@ -549,7 +551,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
   B.npts_total = pts;
   if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(cells + 2), s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_bin(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
-  if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, s) != cudaSuccess)
+  if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, even_n0, s) != cudaSuccess)
     return IB_ERR_CUDA;
   if (launch_interp(J, b->sh, B, itiles, b->desc.dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
   return IB_OK;
@@ -578,7 +580,8 @@ constexpr long long kNaPoints = IB_NOALLOC_MAX_POINTS;
 constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kNaBytes =
     na_align(sizeof(uint32_t) * (size_t)(kNaCells + 2)) +                          // counts / cell starts
-    4 * na_align(sizeof(uint32_t) * (size_t)kNaPoints) +                            // key, rank, perm_tmp, perm
+    3 * na_align(sizeof(uint32_t) * (size_t)kNaPoints) +                            // key, rank, perm
+    na_align(sizeof(uint2) * (size_t)kNaPoints) +                                   // perm_tmp
     na_align(sizeof(uint32_t) * (size_t)((kNaCells + 1 + kScanChunkCells - 1) / kScanChunkCells + 1)) +
     na_align(sizeof(uint32_t));                                                     // error word
 

@@ -6,10 +6,12 @@
 //                    (plus the job's cell base), atomic per-cell count; the
 //                    value returned by the atomic is the point's arrival rank.
 //   2. scan          exclusive prefix of the counts -> cell_start.
-//   3. k_bin_scatter perm_tmp[cell_start[key] + rank] = point (any order in a cell).
-//   4. k_bin_stable  perm[cell_start[key] + #(same-cell points with a smaller
-//                    index)] = point: ties keep index order, as in Fig. 2
-//                    where X3 precedes X5 in cell 5.
+//   3. k_bin_scatter perm_tmp[cell_start[key] + rank] = (point, key) (any order
+//                    in a cell).
+//   4. k_bin_stable  per sorted position: perm[cell_start[key] + #(same-cell
+//                    points with a smaller index)] = point: ties keep index
+//                    order, as in Fig. 2 where X3 precedes X5 in cell 5.  Walking
+//                    sorted positions keeps every access but one coalesced.
 // Invalid points (non-finite or out of range) get the sentinel cell
 // ncell_total and end up after every valid point.
 #include "ib_internal.h"
@@ -81,13 +83,27 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t* total)
   return before + x - v;
 }
 
+// Eight consecutive entries from index base on (two 16-byte loads when they
+// are all in range; base is a multiple of 8, so the vectors are aligned).
+__device__ __forceinline__ void load8(const uint32_t* __restrict__ a, long long base, long long m, uint32_t v[8]) {
+  if (base + kScanItems <= m) {
+    const uint4 x = *reinterpret_cast<const uint4*>(a + base);
+    const uint4 y = *reinterpret_cast<const uint4*>(a + base + 4);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) v[i] = (base + i < m) ? a[base + i] : 0u;
+  }
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ a, long long m,
                                                                uint32_t* __restrict__ sums) {
   const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
-  uint32_t s = 0;
+  uint32_t v[kScanItems], s = 0;
+  load8(a, base, m, v);
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i)
-    if (base + i < m) s += a[base + i];
+  for (int i = 0; i < kScanItems; ++i) s += v[i];
   uint32_t tot;
   block_exclusive(s, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
@@ -120,17 +136,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restric
                                                               const uint32_t* __restrict__ sums, long long nb) {
   const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
   uint32_t v[kScanItems], s = 0;
+  load8(a, base, m, v);
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    v[i] = (base + i < m) ? a[base + i] : 0u;
-    s += v[i];
-  }
+  for (int i = 0; i < kScanItems; ++i) s += v[i];
   uint32_t tot;
   uint32_t off = sums[blockIdx.x] + block_exclusive(s, &tot);
+  uint32_t o[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    if (base + i < m) a[base + i] = off;
+    o[i] = off;
     off += v[i];
+  }
+  if (base + kScanItems <= m) {
+    *reinterpret_cast<uint4*>(a + base) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4*>(a + base + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+      if (base + i < m) a[base + i] = o[i];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) a[m] = sums[nb];
 }
@@ -139,25 +162,27 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter(const Bins B) {
   const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (g >= B.npts_total) return;
   const uint32_t k = B.key[g];
-  B.perm_tmp[B.count[k] + B.rank[g]] = (uint32_t)g;
+  B.perm_tmp[B.count[k] + B.rank[g]] = make_uint2((uint32_t)g, k);
 }
 
-// Stable order inside a cell: the rank of point g among the points of its
-// cell is the number of them with a smaller index.  O(cell size) per point;
-// cells hold a handful of points in every workload of interest, and the
-// cost stays bounded (quadratic in the largest cell) for adversarial input.
+// Stable order inside a cell, one thread per sorted position q: the point at
+// q ranks, among the points of its cell, by the number of them with a smaller
+// index.  O(cell size) per point; cells hold a handful of points in every
+// workload of interest, and the cost stays bounded (quadratic in the largest
+// cell) for adversarial input.
 __global__ void __launch_bounds__(kThreads) k_bin_stable(const Bins B) {
-  const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (g >= B.npts_total) return;
-  const uint32_t k = B.key[g];
-  const uint32_t s = B.count[k];
-  const uint32_t e = B.count[k + 1];
-  uint32_t r = 0;
-  if (e - s > 1) {
-    const uint32_t me = (uint32_t)g;
-    for (uint32_t q = s; q < e; ++q) r += (B.perm_tmp[q] < me) ? 1u : 0u;
+  const long long q = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (q >= B.npts_total) return;
+  const uint2 e = B.perm_tmp[q];
+  const uint32_t s = B.count[e.y];
+  const uint32_t t = B.count[e.y + 1];
+  if (t - s == 1) {
+    B.perm[q] = e.x;
+    return;
   }
-  B.perm[s + r] = (uint32_t)g;
+  uint32_t r = 0;
+  for (uint32_t j = s; j < t; ++j) r += (B.perm_tmp[j].x < e.x) ? 1u : 0u;
+  B.perm[s + r] = e.x;
 }
 
 inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }

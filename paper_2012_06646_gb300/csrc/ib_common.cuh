@@ -66,7 +66,7 @@ struct Bins {
   uint32_t* count;       // [ncell_total + 2]: per-cell counts, then exclusive prefix (cell_start)
   uint32_t* key;         // [npts_total]: global cell id of each point (ncell_total = invalid point)
   uint32_t* rank;        // [npts_total]: arrival rank of the point inside its cell
-  uint32_t* perm_tmp;    // [npts_total]: points in cell order, arbitrary order inside a cell
+  uint2* perm_tmp;       // [npts_total]: (point, cell) in cell order, arbitrary order inside a cell
   uint32_t* perm;        // [npts_total]: points in cell order, index order inside a cell (stable)
   uint32_t* block_sums;  // scan scratch
   uint32_t* err;         // device error word

@@ -25,8 +25,10 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
 
 // Spreading in two launches: per-tile boxes in shared memory written to
 // `boxes`, then the fixed-order combination of overlapping boxes into f.
+// even_n0: every job of the launch has an even n0 (the combination then
+// handles two x-adjacent nodes per thread).
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles_total,
-                          int tile, int dtype, bool compensated, bool accumulate, cudaStream_t s);
+                          int tile, int dtype, bool compensated, bool accumulate, bool even_n0, cudaStream_t s);
 
 // Tile side of the interpolation tiles: 8 in 3-D, 32 in 2-D.
 inline int interp_tile_side(int dim) { return dim == 3 ? 8 : 32; }

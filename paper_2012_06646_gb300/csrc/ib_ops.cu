@@ -29,6 +29,7 @@ namespace ibgb {
 namespace {
 
 constexpr int kBoxThreads = 128;   // 4 warps: one per group of 5 cell layers
+
 constexpr int kThreads = 256;
 
 template <int D, int TS>
@@ -140,10 +141,11 @@ __device__ __forceinline__ void point_box(const Job& jb, const Shape& sh, const 
 // ---------------------------------------------------------------------------
 constexpr int kBatch = 32;
 
-// Words of a record: 16 products (+ 4 z weights in 3-D) + the box offset,
-// padded to an odd number of 16-byte chunks so the lanes' vector stores of
-// stage 1 fall into distinct bank groups.
-__host__ __device__ constexpr int rec_words(int dim) { return dim == 3 ? 28 : 20; }
+// Words of a record: 16 products (+ 4 z weights in 3-D), an odd number of
+// 16-byte chunks so the lanes' vector stores of stage 1 fall into distinct
+// bank groups; the box offsets of a batch sit in a separate array.  Small
+// records keep five CTAs of 16^3 tiles resident per SM.
+__host__ __device__ constexpr int rec_words(int dim) { return dim == 3 ? 20 : 20; }
 
 template <typename T>
 __device__ __forceinline__ void two_sum_into(T* s, T* e, T v) {
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
   T* stage_all = boxS + (COMP ? 2 : 1) * Gm::BV;
   __shared__ uint32_t rstart_s[4][32];
   __shared__ uint32_t rpre_s[4][32];
+  __shared__ int off_s[4][kBatch];      // box offset of each record's t = -1 corner
   const int nc = sh.ncomp;
   __shared__ Job sjob;                  // one copy of the job per CTA (broadcast reads)
   const long long gt = blockIdx.x / nc;
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
             store4(rec + 16, w[D - 1][0], w[D - 1][2], w[D - 1][1], w[D - 1][3]);
             off += o[D - 1] * Gm::BY * Gm::BX;
           }
-          *reinterpret_cast<int*>(rec + (REC - 1)) = off;     // the record's last slot
+          off_s[warp][lane] = off;
         }
         // fetch the next batch's point data while this batch is added
         const uint32_t nq = base + kBatch + lane;
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
         // Stage 2: the warp adds the points of the batch one by one.
         const int cnt = (int)min((uint32_t)kBatch, M - base);
         const T* r0 = stage;
-        int nb = *reinterpret_cast<const int*>(r0 + (REC - 1));
+        int nb = off_s[warp][0];
         T npv = r0[lane & 15];
         T nz0 = (D == 3) ? r0[16 + 2 * tzb] : (T)1;
         T nz1 = (D == 3) ? r0[17 + 2 * tzb] : (T)0;
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
           const T pv = npv, z0 = nz0, z1 = nz1;
           if (i + 1 < cnt) {
             const T* rn = stage + (i + 1) * REC;
-            nb = *reinterpret_cast<const int*>(rn + (REC - 1));
+            nb = off_s[warp][i + 1];
             npv = rn[lane & 15];
             if (D == 3) {
               nz0 = rn[16 + 2 * tzb];
@@ -410,12 +413,46 @@ __device__ __noinline__ void combine_general(const Jobs& J, int j, const Shape& 
   }
 }
 
-template <typename T, int D, int TS, bool CP>
+// V consecutive x nodes per thread (V = 2 needs every job's n0 even: then the
+// two nodes of an even-aligned pair have the same covering boxes at
+// consecutive, 2-element-aligned offsets, and each box is read with one
+// vector load).
+template <typename T, int V>
+struct Vec;
+template <> struct Vec<float, 1> { using type = float; };
+template <> struct Vec<double, 1> { using type = double; };
+template <> struct Vec<float, 2> { using type = float2; };
+template <> struct Vec<double, 2> { using type = double2; };
+
+template <typename T, int V>
+__device__ __forceinline__ void load_v(const T* p, T* out) {
+  if constexpr (V == 1) {
+    out[0] = *p;
+  } else {
+    const typename Vec<T, 2>::type q = *reinterpret_cast<const typename Vec<T, 2>::type*>(p);
+    out[0] = q.x;
+    out[1] = q.y;
+  }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void store_v(T* p, const T* v) {
+  if constexpr (V == 1) {
+    *p = v[0];
+  } else {
+    typename Vec<T, 2>::type q;
+    q.x = v[0];
+    q.y = v[1];
+    *reinterpret_cast<typename Vec<T, 2>::type*>(p) = q;
+  }
+}
+
+template <typename T, int D, int TS, bool CP, int V>
 __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_constant__ Jobs J, const Shape sh,
                                                              const T* __restrict__ boxes, long long ncell_total,
                                                              int accumulate) {
   using Gm = Geo<D, TS>;
-  const int c = blockIdx.x * kThreads + threadIdx.x;    // global cell ids stay below 2^31
+  const int c = (blockIdx.x * kThreads + threadIdx.x) * V;   // global cell ids stay below 2^31
   if (c >= ncell_total) return;
   const int jj = job_of_cell(J, c);
   const Job jb = job_at(J, jj);
@@ -435,7 +472,11 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 #pragma unroll
   for (int b = 0; b < D; ++b) fast = fast && jb.n[b] >= TS + 4;
   if (!fast) {
-    combine_general<T, D, TS, CP>(J, jj, sh, boxes, x, lc, accumulate);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      int xv[3] = {x[0] + v, x[1], x[2]};
+      combine_general<T, D, TS, CP>(J, jj, sh, boxes, xv, lc + v, accumulate);
+    }
     return;
   }
   const Cover3 cx = cover_fast<TS>(x[0], jb.n[0], jb.ntile[0]);
@@ -449,7 +490,11 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
   }
   const int nc = sh.ncomp;
   const long long plane = (long long)(CP ? 2 : 1) * Gm::BV;
-  T S[4] = {0, 0, 0, 0}, E[4] = {0, 0, 0, 0};
+  T S[4][V], E[4][V];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int v = 0; v < V; ++v) S[a][v] = E[a][v] = (T)0;
   // Covering boxes in increasing (z, y, x) unwrapped order; every component
   // sums them in that same order.
 #pragma unroll
@@ -467,15 +512,21 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           if (a >= nc) break;
+          T sv[V];
+          load_v<T, V>(bp + a * plane, sv);
           if (CP) {
-            const T sv = bp[a * plane];
-            const T ev = bp[a * plane + Gm::BV];
-            const T sum = S[a] + sv;
-            const T bb = sum - S[a];
-            E[a] += ((S[a] - (sum - bb)) + (sv - bb)) + ev;
-            S[a] = sum;
+            T ev[V];
+            load_v<T, V>(bp + a * plane + Gm::BV, ev);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const T sum = S[a][v] + sv[v];
+              const T bb = sum - S[a][v];
+              E[a][v] += ((S[a][v] - (sum - bb)) + (sv[v] - bb)) + ev[v];
+              S[a][v] = sum;
+            }
           } else {
-            S[a] += bp[a * plane];
+#pragma unroll
+            for (int v = 0; v < V; ++v) S[a][v] += sv[v];
           }
         }
       }
@@ -485,9 +536,17 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     if (a >= nc) break;
-    const T val = CP ? S[a] + E[a] : S[a];
-    const long long o = a * jb.ncell + lc;
-    f[o] = accumulate ? f[o] + val : val;
+    T val[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) val[v] = CP ? S[a][v] + E[a][v] : S[a][v];
+    T* o = f + a * jb.ncell + lc;
+    if (accumulate) {
+      T old[V];
+      load_v<T, V>(o, old);
+#pragma unroll
+      for (int v = 0; v < V; ++v) val[v] = old[v] + val[v];
+    }
+    store_v<T, V>(o, val);
   }
 }
 
@@ -777,25 +836,31 @@ size_t spread_smem(bool comp) {
 
 template <typename T, int D, int TS>
 cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool comp,
-                        bool accumulate, cudaStream_t s) {
+                        bool accumulate, bool pairs, cudaStream_t s) {
   if (ntiles > 0) {
     const size_t bytes = spread_smem<T, D, TS>(comp);
     const unsigned grid = (unsigned)(ntiles * sh.ncomp);
     if (comp) {
+      cudaFuncSetAttribute(k_spread_box<T, D, TS, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       allow_smem(k_spread_box<T, D, TS, true>, bytes);
       k_spread_box<T, D, TS, true><<<grid, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
     } else {
+      cudaFuncSetAttribute(k_spread_box<T, D, TS, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       allow_smem(k_spread_box<T, D, TS, false>, bytes);
       k_spread_box<T, D, TS, false><<<grid, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
     }
   }
   if (B.ncell_total > 0) {
-    if (comp)
-      k_spread_combine<T, D, TS, true><<<grid_for(B.ncell_total, kThreads), kThreads, 0, s>>>(
-          J, sh, (const T*)boxes, B.ncell_total, accumulate ? 1 : 0);
-    else
-      k_spread_combine<T, D, TS, false><<<grid_for(B.ncell_total, kThreads), kThreads, 0, s>>>(
-          J, sh, (const T*)boxes, B.ncell_total, accumulate ? 1 : 0);
+    const int acc = accumulate ? 1 : 0;
+    if (pairs) {
+      const unsigned g = grid_for((B.ncell_total + 1) / 2, kThreads);
+      if (comp) k_spread_combine<T, D, TS, true, 2><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
+      else k_spread_combine<T, D, TS, false, 2><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
+    } else {
+      const unsigned g = grid_for(B.ncell_total, kThreads);
+      if (comp) k_spread_combine<T, D, TS, true, 1><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
+      else k_spread_combine<T, D, TS, false, 1><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
+    }
   }
   return cudaGetLastError();
 }
@@ -817,15 +882,16 @@ size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp) {
 }
 
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, int tile,
-                          int dtype, bool comp, bool accumulate, cudaStream_t s) {
+                          int dtype, bool comp, bool accumulate, bool even_n0, cudaStream_t s) {
+  const bool p = even_n0;
   if (dtype == 0) {
-    if (sh.dim == 2) return spread_impl<float, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, s);
-    if (tile == 16) return spread_impl<float, 3, 16>(J, sh, B, boxes, ntiles, comp, accumulate, s);
-    return spread_impl<float, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, s);
+    if (sh.dim == 2) return spread_impl<float, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+    if (tile == 16) return spread_impl<float, 3, 16>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+    return spread_impl<float, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
   }
-  if (sh.dim == 2) return spread_impl<double, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, s);
-  if (tile == 16) return spread_impl<double, 3, 16>(J, sh, B, boxes, ntiles, comp, accumulate, s);
-  return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, s);
+  if (sh.dim == 2) return spread_impl<double, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+  if (tile == 16) return spread_impl<double, 3, 16>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+  return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
 }
 
 template <typename T, int D, int TS>

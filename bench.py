@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--clock-window", type=float, default=1.0,
                     help="seconds of clock sampling from the start of the timed steps")
     ap.add_argument("--serve-jobs", type=int, default=384, help="jobs of the served-batch measurement (0: skip)")
-    ap.add_argument("--serve-load", type=float, default=0.9, help="offered load as a fraction of the loop capacity")
+    ap.add_argument("--serve-loads", default="0.9,2.0",
+                    help="offered loads as multiples of the one-job loop's capacity, comma separated")
     return ap.parse_args()
 
 
@@ -209,11 +210,12 @@ def cpu_oracle_rate(sample: int, N: int, seed: int):
     return sample / dt, dt
 
 
-def serving_bench(device, njobs: int, load: float, seed: int = 1):
+def serving_bench(device, njobs: int, loads, seed: int = 1):
     """Served batch: independent spread + interpolate jobs, N in {32, 64, 96, 128}, n log-uniform in
     [1e3, 1e5], half uniform / half on RBC shells.  The one-job-per-launch loop is first run back to
-    back to measure its capacity; then Poisson arrivals at `load` x that capacity are served by the
-    continuous-batching server and by the loop.  Latency = completion - arrival."""
+    back to measure its capacity, and the continuous-batching server likewise; then Poisson arrivals
+    at each offered load (a multiple of the loop's capacity) are served by the server and by the
+    loop.  Latency = completion - arrival."""
     import ib_inputs
     import torch
     from paper_2012_06646_gb300 import serve
@@ -223,22 +225,26 @@ def serving_bench(device, njobs: int, load: float, seed: int = 1):
     srv = serve.Server(nstreams=3, max_jobs=64, max_points=1 << 22, max_cells=1 << 25, device=device)
     srv.serve(serve.make_requests(specs[: min(16, njobs)]), realtime=False)
     reqs = serve.make_requests(specs)
-    cap_run = serve.single_job_loop(reqs, realtime=False, device=device)
-    cap = cap_run.jobs / cap_run.wall_s
-    arrivals = ib_inputs.poisson_arrivals(seed, njobs, load * cap)
-    for r, t in zip(reqs, arrivals):
-        r.arrival, r.t_done, r.U = float(t), -1.0, None
-    st_b = srv.serve(reqs)
-    batched_U = [r.U.clone() for r in reqs]
-    for r in reqs:
-        r.t_done, r.U = -1.0, None
-    st_l = serve.single_job_loop(reqs, device=device)
-    same = all(torch.equal(a, r.U) for a, r in zip(batched_U, reqs))
+    cap_loop = serve.single_job_loop(reqs, realtime=False, device=device)
+    loop_U = [r.U.clone() for r in reqs]
+    cap_srv = srv.serve(reqs, realtime=False)
+    same = all(torch.equal(a, r.U) for a, r in zip(loop_U, reqs))
+    cap = cap_loop.jobs / cap_loop.wall_s
+    out = {"jobs": njobs, "points": int(sum(sp.npts for sp in specs)),
+           "capacity_jobs_per_s": {"single_job_loop": cap, "batched": cap_srv.jobs / cap_srv.wall_s},
+           "results_identical_alone_and_in_mix": bool(same), "loads": []}
+    for load in loads:
+        arrivals = ib_inputs.poisson_arrivals(seed, njobs, load * cap)
+        for r, t in zip(reqs, arrivals):
+            r.arrival, r.t_done = float(t), -1.0
+        st_b = srv.serve(reqs)
+        for r in reqs:
+            r.t_done = -1.0
+        st_l = serve.single_job_loop(reqs, device=device)
+        out["loads"].append({"offered_load_x_loop_capacity": load, "offered_jobs_per_s": load * cap,
+                             "batched": st_b.summary(), "single_job_loop": st_l.summary()})
     srv.close()
-    return {"jobs": njobs, "offered_load": load, "loop_capacity_jobs_per_s": cap,
-            "points": int(sum(sp.npts for sp in specs)),
-            "batched": st_b.summary(), "single_job_loop": st_l.summary(),
-            "results_identical_alone_and_in_mix": bool(same)}
+    return out
 
 
 def run_reference(args):
@@ -443,7 +449,7 @@ def run_ours(args):
     serving = None
     if args.serve_jobs > 0:
         try:
-            serving = serving_bench(device, args.serve_jobs, args.serve_load)
+            serving = serving_bench(device, args.serve_jobs, [float(x) for x in args.serve_loads.split(",")])
         except Exception as exc:
             serving = {"error": repr(exc)}
 

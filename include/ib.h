@@ -62,7 +62,9 @@ typedef enum {
   IB_ERR_NOT_IMPLEMENTED = 6,
   IB_ERR_NONFINITE = 7,       /* a position was NaN or infinite (reported by ib_plan_check) */
   IB_ERR_RANGE = 8,           /* a position was 2^30 or more cells away from the box */
-  IB_ERR_NO_BINS = 9          /* IB_REUSE_BINS without a matching ib_bin call */
+  IB_ERR_NO_BINS = 9,         /* IB_REUSE_BINS without a matching ib_bin call */
+  IB_ERR_BINS_STALE = 10      /* positions changed after binning (or X aliased an output):
+                                 the points concerned spread nothing and interpolate to NaN */
 } ib_status;
 
 enum { IB_KERNEL_PESKIN4 = 0, IB_KERNEL_COSINE4 = 1 };   /* standard 4-point / cosine 4-point phi (Section 2) */
@@ -145,8 +147,8 @@ ib_status ib_advect(ib_plan plan, long long npts, const void* X, const void* U, 
                     void* stream);
 
 /* Synchronise `stream`, then read and clear the plan's device error word:
- * IB_OK, IB_ERR_NONFINITE or IB_ERR_RANGE (or IB_ERR_CUDA if the stream
- * reports an error). */
+ * IB_OK, IB_ERR_NONFINITE, IB_ERR_RANGE or IB_ERR_BINS_STALE (or IB_ERR_CUDA
+ * if the stream reports an error). */
 ib_status ib_plan_check(ib_plan plan, void* stream);
 
 /* Device pointers to the bins of the last ib_bin on this plan (for
@@ -173,8 +175,13 @@ typedef struct {
   long long max_points;                  /* total points per wave */
   long long max_cells;                   /* total grid cells per wave (sum of n0 n1 n2), < 2^31 */
   long long max_tiles;                   /* total spreading tiles per wave (see ib_batch_job_footprint) */
-  unsigned flags;                        /* reserved, must be 0 */
+  unsigned flags;                        /* 0 or IB_BATCH_HOST_IO */
 } ib_batch_desc;
+
+/* ib_batch_desc.flags: the batch also owns device buffers for every job's
+ * points, forces, velocities and grid (max_points x (dim + 2 ncomp) plus
+ * max_cells x ncomp entries), used by ib_batch_run_host. */
+#define IB_BATCH_HOST_IO 0x1u
 
 typedef struct {
   int n[3];              /* grid points per dimension */
@@ -206,6 +213,27 @@ ib_status ib_batch_destroy(ib_batch batch);
  * before reusing its staging buffer.  IB_ERR_CAPACITY if the wave exceeds
  * the batch capacity. */
 ib_status ib_batch_run(ib_batch batch, int njobs, const ib_job* jobs, unsigned flags, void* stream);
+
+/* A served job with host-resident data (see ib_batch_run_host). */
+typedef struct {
+  int n[3];              /* grid points per dimension */
+  double L[3];           /* box side per dimension */
+  long long npts;        /* points of this job, >= 0 */
+  const void* X;         /* (npts, dim), host (pinned for asynchronous copies) */
+  const void* G;         /* (npts, ncomp), host: the forces to spread */
+  void* U;               /* (npts, ncomp), host: receives the interpolated velocities */
+} ib_host_job;
+
+/* One served wave with host-resident inputs and outputs, in one call: on
+ * `stream`, copy each job's X and G into the batch's own device buffers,
+ * run the wave (bin, spread G -> f onto the job's grid, interpolate f -> U;
+ * the grid stays on the device), and copy each job's U back to the host.
+ * Requires a batch created with IB_BATCH_HOST_IO.  Host buffers must stay
+ * valid and unchanged until the stream has passed this wave (an event or a
+ * stream synchronisation); with pageable host memory the copies are not
+ * asynchronous.  IB_ERR_CAPACITY as for ib_batch_run.  Paper counterpart:
+ * none (serving form). */
+ib_status ib_batch_run_host(ib_batch batch, int njobs, const ib_host_job* jobs, void* stream);
 
 /* As ib_plan_check, for the batch object's device error word. */
 ib_status ib_batch_check(ib_batch batch, void* stream);

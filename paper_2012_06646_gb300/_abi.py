@@ -23,6 +23,7 @@ IB_ERR_NOT_IMPLEMENTED = 6
 IB_ERR_NONFINITE = 7
 IB_ERR_RANGE = 8
 IB_ERR_NO_BINS = 9
+IB_ERR_BINS_STALE = 10
 
 IB_KERNEL_PESKIN4 = 0
 IB_KERNEL_COSINE4 = 1
@@ -36,6 +37,8 @@ IB_ACCUMULATE = 0x1
 IB_COMPENSATED = 0x2
 IB_REUSE_BINS = 0x4
 IB_ADJOINT = 0x8
+
+IB_BATCH_HOST_IO = 0x1
 
 IB_NOALLOC_MAX_CELLS = 1 << 21
 IB_NOALLOC_MAX_POINTS = 1 << 20
@@ -58,6 +61,11 @@ class ib_job(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3), ("npts", ctypes.c_longlong),
                 ("X", ctypes.c_void_p), ("G", ctypes.c_void_p), ("f", ctypes.c_void_p),
                 ("u", ctypes.c_void_p), ("U", ctypes.c_void_p)]
+
+
+class ib_host_job(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3), ("npts", ctypes.c_longlong),
+                ("X", ctypes.c_void_p), ("G", ctypes.c_void_p), ("U", ctypes.c_void_p)]
 
 
 _vp = ctypes.c_void_p
@@ -83,6 +91,7 @@ SIGNATURES = {
     "ib_batch_destroy": (_st, [_vp]),
     "ib_batch_run": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_job), ctypes.c_uint, _vp]),
     "ib_batch_check": (_st, [_vp, _vp]),
+    "ib_batch_run_host": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_host_job), _vp]),
     "ib_interpolate_noalloc": (_st, [ctypes.POINTER(ib_plan_desc), _ll, _vp, _vp, _vp, _vp]),
     "ib_status_string": (ctypes.c_char_p, [_st]),
     "ib_version": (ctypes.c_char_p, []),

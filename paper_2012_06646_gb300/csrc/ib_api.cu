@@ -43,6 +43,13 @@ void short_scale(double s, int* S, int* E) {
 
 int entry_bytes(int dtype, bool comp) { return (dtype == IB_F64 ? 8 : 4) * (comp ? 2 : 1); }
 
+// The box combination may handle two x-adjacent nodes per thread: needs an
+// even n0 and a grid pointer aligned to two entries.
+bool pair_aligned(int n0, const void* f, int dtype) {
+  const uintptr_t a = 2u * (uintptr_t)entry_bytes(dtype, false);
+  return (n0 % 2 == 0) && ((uintptr_t)f % a == 0);
+}
+
 // Fill the geometry part of a job for a grid of n points and sides L.
 bool fill_job(Job& jb, int dim, const int n[3], const double L[3], int tile) {
   memset(&jb, 0, sizeof(jb));
@@ -95,10 +102,10 @@ bool valid_shape(int dim, int grid, int kernel, int dtype, int ncomp) {
 
 // Arena layout shared by plans and batches.
 struct Layout {
-  size_t count, key, rank, perm_tmp, perm, block_sums, err, boxes, table, total;
+  size_t count, key, rank, perm_tmp, perm, block_sums, err, boxes, table, io, total;
 };
 
-Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t table_bytes) {
+Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t table_bytes, size_t io_bytes = 0) {
   Layout L;
   size_t off = 0;
   L.count = off;      off += align_up(sizeof(uint32_t) * (size_t)(ncell + 2));
@@ -110,6 +117,7 @@ Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t t
   L.err = off;        off += align_up(sizeof(uint32_t));
   L.boxes = off;      off += align_up(boxes_bytes);
   L.table = off;      off += align_up(table_bytes);
+  L.io = off;         off += align_up(io_bytes);
   L.total = off;
   return L;
 }
@@ -135,6 +143,7 @@ ib_status check_error_word(uint32_t* err_dev, cudaStream_t s) {
   if (e != 0 && cudaMemset(err_dev, 0, sizeof(uint32_t)) != cudaSuccess) return IB_ERR_CUDA;
   if (e & ERR_NONFINITE) return IB_ERR_NONFINITE;
   if (e & ERR_RANGE) return IB_ERR_RANGE;
+  if (e & ERR_STALE) return IB_ERR_BINS_STALE;
   return IB_OK;
 }
 
@@ -168,6 +177,8 @@ struct ib_batch_s {
   Job* h_stage;        // pinned staging buffer of the job table
   cudaEvent_t uploaded;
   bool pending;
+  char* io;            // IB_BATCH_HOST_IO: device X, G, U (max_points) and grids (max_cells)
+  ib_job* h_jobs;      // IB_BATCH_HOST_IO: device-pointer job array of the current wave
 };
 
 namespace {
@@ -257,6 +268,7 @@ const char* ib_status_string(ib_status st) {
     case IB_ERR_NONFINITE: return "IB_ERR_NONFINITE";
     case IB_ERR_RANGE: return "IB_ERR_RANGE";
     case IB_ERR_NO_BINS: return "IB_ERR_NO_BINS";
+    case IB_ERR_BINS_STALE: return "IB_ERR_BINS_STALE";
   }
   return "IB_ERR_UNKNOWN";
 }
@@ -338,7 +350,7 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   if (flags & IB_ADJOINT) J.one.hmd = 1.0;
   J.njobs = 1;
   if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp,
-                    (flags & IB_ACCUMULATE) != 0, (p->job.n[0] & 1) == 0, s) != cudaSuccess)
+                    (flags & IB_ACCUMULATE) != 0, pair_aligned(p->job.n[0], f, p->desc.dtype), s) != cudaSuccess)
     return IB_ERR_CUDA;
   return IB_OK;
 }
@@ -423,12 +435,18 @@ ib_status ib_plan_bins(ib_plan p, const void** perm, const void** cell_start, lo
 
 static bool batch_sizes(const ib_batch_desc* d, int* tile, Layout* L) {
   if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
-  if (d->flags != 0 || d->max_jobs < 1 || d->max_points < 0 || d->max_points > kMaxPointsTotal) return false;
+  if ((d->flags & ~IB_BATCH_HOST_IO) || d->max_jobs < 1 || d->max_points < 0 || d->max_points > kMaxPointsTotal)
+    return false;
   if (d->max_cells < 1 || d->max_cells > kMaxCellsTotal || d->max_tiles < 0) return false;
   const int t = spread_tile_side(d->dim, entry_bytes(d->dtype, false), false, d->ncomp);
   const size_t boxes = (size_t)d->max_tiles * box_bytes(d->dim, t, entry_bytes(d->dtype, false), d->ncomp);
+  const size_t eb = (size_t)entry_bytes(d->dtype, false);
+  const size_t io = (d->flags & IB_BATCH_HOST_IO)
+                        ? eb * ((size_t)d->max_points * (size_t)(d->dim + 2 * d->ncomp) +
+                                (size_t)d->max_cells * (size_t)d->ncomp) + 3 * 256
+                        : 0;
   if (tile) *tile = t;
-  if (L) *L = make_layout(d->max_cells, d->max_points, boxes, sizeof(Job) * (size_t)d->max_jobs);
+  if (L) *L = make_layout(d->max_cells, d->max_points, boxes, sizeof(Job) * (size_t)d->max_jobs, io);
   return true;
 }
 
@@ -483,6 +501,17 @@ ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out) {
     delete b;
     return IB_ERR_CUDA;
   }
+  if (desc->flags & IB_BATCH_HOST_IO) {
+    b->h_jobs = new (std::nothrow) ib_job[desc->max_jobs];
+    if (!b->h_jobs) {
+      cudaEventDestroy(b->uploaded);
+      cudaFreeHost(b->h_stage);
+      cudaFree(b->arena);
+      delete b;
+      return IB_ERR_OOM;
+    }
+    b->io = (char*)b->arena + b->layout.io;
+  }
   b->bins = carve((char*)b->arena, b->layout);
   b->boxes = (char*)b->arena + b->layout.boxes;
   b->d_table = (Job*)((char*)b->arena + b->layout.table);
@@ -497,6 +526,7 @@ ib_status ib_batch_destroy(ib_batch b) {
   cudaEventDestroy(b->uploaded);
   cudaFreeHost(b->h_stage);
   cudaFree(b->arena);
+  delete[] b->h_jobs;
   delete b;
   return IB_OK;
 }
@@ -516,7 +546,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
   bool even_n0 = true;
   for (int i = 0; i < njobs; ++i) {
     const ib_job& in = jobs[i];
-    even_n0 = even_n0 && (in.n[0] % 2 == 0);
+    even_n0 = even_n0 && (!in.G || pair_aligned(in.n[0], in.f, b->desc.dtype));
     Job& jb = b->h_stage[i];
     if (in.npts < 0 || !fill_job(jb, b->desc.dim, in.n, in.L, b->tile)) return IB_ERR_INVALID_ARG;
     if (in.npts > 0 && !in.X) return IB_ERR_INVALID_ARG;
@@ -554,6 +584,63 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
   if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, even_n0, s) != cudaSuccess)
     return IB_ERR_CUDA;
   if (launch_interp(J, b->sh, B, itiles, b->desc.dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;
+  return IB_OK;
+}
+
+ib_status ib_batch_run_host(ib_batch b, int njobs, const ib_host_job* jobs, void* stream) {
+  if (!b || njobs < 0 || (njobs > 0 && !jobs)) return IB_ERR_INVALID_ARG;
+  if (!(b->desc.flags & IB_BATCH_HOST_IO) || !b->io) return IB_ERR_INVALID_ARG;
+  if (njobs > b->desc.max_jobs) return IB_ERR_CAPACITY;
+  if (njobs == 0) return IB_OK;
+  const ib_batch_desc& d = b->desc;
+  const size_t eb = (size_t)entry_bytes(d.dtype, false);
+  // device buffers: X [max_points][dim], G and U [max_points][ncomp], grids [max_cells][ncomp]
+  char* Xb = b->io;
+  char* Gb = Xb + align_up(eb * (size_t)d.max_points * (size_t)d.dim);
+  char* Ub = Gb + align_up(eb * (size_t)d.max_points * (size_t)d.ncomp);
+  char* Fb = Ub + align_up(eb * (size_t)d.max_points * (size_t)d.ncomp);
+  long long pts = 0, cells = 0;
+  for (int i = 0; i < njobs; ++i) {
+    const ib_host_job& in = jobs[i];
+    if (in.npts < 0 || (in.npts > 0 && (!in.X || !in.G || !in.U))) return IB_ERR_INVALID_ARG;
+    long long nc = 1;
+    for (int k = 0; k < d.dim; ++k) {
+      if (in.n[k] < 1) return IB_ERR_INVALID_ARG;
+      nc *= in.n[k];
+    }
+    if (pts + in.npts > d.max_points || cells + nc > d.max_cells) return IB_ERR_CAPACITY;
+    ib_job& jo = b->h_jobs[i];
+    memcpy(jo.n, in.n, sizeof(jo.n));
+    memcpy(jo.L, in.L, sizeof(jo.L));
+    jo.npts = in.npts;
+    jo.X = Xb + eb * (size_t)pts * (size_t)d.dim;
+    jo.G = Gb + eb * (size_t)pts * (size_t)d.ncomp;
+    jo.U = Ub + eb * (size_t)pts * (size_t)d.ncomp;
+    jo.f = Fb + eb * (size_t)cells * (size_t)d.ncomp;
+    jo.u = jo.f;
+    pts += in.npts;
+    cells += nc;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < njobs; ++i) {
+    const ib_host_job& in = jobs[i];
+    if (in.npts == 0) continue;
+    const ib_job& jo = b->h_jobs[i];
+    if (cudaMemcpyAsync((void*)jo.X, in.X, eb * (size_t)in.npts * (size_t)d.dim, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync((void*)jo.G, in.G, eb * (size_t)in.npts * (size_t)d.ncomp, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+      return IB_ERR_CUDA;
+  }
+  const ib_status st = ib_batch_run(b, njobs, b->h_jobs, 0, stream);
+  if (st != IB_OK) return st;
+  for (int i = 0; i < njobs; ++i) {
+    const ib_host_job& in = jobs[i];
+    if (in.npts == 0) continue;
+    if (cudaMemcpyAsync(in.U, b->h_jobs[i].U, eb * (size_t)in.npts * (size_t)d.ncomp, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+      return IB_ERR_CUDA;
+  }
   return IB_OK;
 }
 

@@ -16,6 +16,7 @@ namespace ibgb {
 
 constexpr uint32_t ERR_NONFINITE = 1u;
 constexpr uint32_t ERR_RANGE = 2u;
+constexpr uint32_t ERR_STALE = 4u;   // a point's cell no longer matches its bin (X changed after binning)
 
 // Positions are accepted while |X_b N_b / L_b| < 2^30 (cell indices fit in int).
 constexpr double kMaxCells = 1073741824.0;

@@ -103,21 +103,26 @@ struct PointBox {
   T w0[D][4], w1[D][4];
 };
 
+// Returns false when the point's cell (xi = 0) is not inside the tile (X
+// changed after binning).
 template <typename T, int D>
-__device__ __forceinline__ void point_box(const Job& jb, const Shape& sh, const T* Xp, const int T0[3],
-                                          PointBox<T, D>& P) {
+__device__ __forceinline__ bool point_box(const Job& jb, const Shape& sh, const T* Xp, const int T0[3],
+                                          const int TE[3], PointBox<T, D>& P) {
+  bool inside = true;
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     Cell1<T> c;
-    point_cell<T>(Xp[b], jb, b, c);
+    const uint32_t e = point_cell<T>(Xp[b], jb, b, c);
     const int n = jb.n[b];
     const int cphys = ((unsigned)c.i0 < (unsigned)n) ? c.i0 : modn(c.i0, n);
     const int cc = cphys - T0[b];
+    inside = inside && e == 0 && (unsigned)cc < (unsigned)TE[b] && (c.i1 - c.i0) >= -1 && (c.i1 - c.i0) <= 0;
     P.o0[b] = cc + 1;
     P.o1[b] = cc + (c.i1 - c.i0) + 1;
     if (sh.mac) weights(sh.kernel, c.r0, c.c0, P.w0[b]);
     weights(sh.kernel, c.r1, c.c1, P.w1[b]);
   }
+  return inside;
 }
 
 // ---------------------------------------------------------------------------
@@ -167,20 +172,26 @@ __device__ __forceinline__ void store4(double* d, double a, double b, double c, 
 
 // Cell offset (box coordinates of the t = -1 node) and weights of one
 // component of a point, in every dimension.
+// Returns false when the point's cell (xi = 0) is not inside the tile, which
+// happens only if X changed after binning; the caller then drops the point.
 template <typename T, int D>
-__device__ __forceinline__ void point_comp(const Job& jb, const Shape& sh, const T* xp, const int T0[3], int a,
-                                           int o[3], T w[3][4]) {
+__device__ __forceinline__ bool point_comp(const Job& jb, const Shape& sh, const T* xp, const int T0[3],
+                                           const int TE[3], int a, int o[3], T w[3][4]) {
+  bool inside = true;
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     Cell1<T> c;
-    point_cell<T>(xp[b], jb, b, c);
+    const uint32_t e = point_cell<T>(xp[b], jb, b, c);
     const int n = jb.n[b];
     const int cphys = ((unsigned)c.i0 < (unsigned)n) ? c.i0 : modn(c.i0, n);
+    inside = inside && e == 0 && (unsigned)(cphys - T0[b]) < (unsigned)TE[b] && (c.i1 - c.i0) >= -1 &&
+             (c.i1 - c.i0) <= 0;
     const bool h = half_stag(sh, a, b);
     o[b] = cphys - T0[b] + 1 + (h ? (c.i1 - c.i0) : 0);
     if (h) weights(sh.kernel, c.r1, c.c1, w[b]);
     else weights(sh.kernel, c.r0, c.c0, w[b]);
   }
+  return inside;
 }
 
 template <typename T, int D, int TS, bool COMP>
@@ -235,8 +246,18 @@ __global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constan
         if (base + lane < M) {
           int o[3] = {0, 0, 0};
           T w[3][4];
-          point_comp<T, D>(jb, sh, xs, T0, a, o, w);
-          const T ga = hmd * gs;
+          const bool inside = point_comp<T, D>(jb, sh, xs, T0, TE, a, o, w);
+          T ga = hmd * gs;
+          if (!inside) {                 // X changed after binning: contribute nothing, report
+            atomicOr(B.err, ERR_STALE);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              o[b] = 1;
+#pragma unroll
+              for (int t = 0; t < 4; ++t) w[b][t] = (T)0;
+            }
+            ga = (T)0;
+          }
           T* rec = stage + lane * REC;
           T wxg[4];
 #pragma unroll
@@ -667,8 +688,12 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     const uint32_t g = B.perm[rstart[lo] + (q - rpre[lo])];
     const long long li = (long long)g - jb.pt_base;
     PointBox<T, D> Pb;
-    point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, Pb);
     T* U = (T*)jb.U + li * nc;
+    if (!point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, TE, Pb)) {
+      atomicOr(B.err, ERR_STALE);        // X changed after binning: no gather outside the box
+      for (int a = 0; a < nc; ++a) U[a] = (T)NAN;
+      continue;
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       if (a >= nc) break;

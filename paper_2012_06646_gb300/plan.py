@@ -189,7 +189,7 @@ class Batch:
     """An `ib_batch`: one wave of independent spread + interpolate jobs per `run` call."""
 
     def __init__(self, dim=3, grid="mac", kernel="peskin4", dtype=torch.float32, ncomp=None, max_jobs=64,
-                 max_points=1 << 22, max_cells=1 << 24, max_tiles=None, device=None):
+                 max_points=1 << 22, max_cells=1 << 24, max_tiles=None, host_io=False, device=None):
         self.lib = _abi.load()
         self.dim = dim
         self.ncomp = ncomp if ncomp is not None else dim
@@ -205,7 +205,7 @@ class Batch:
         d.max_points = int(max_points)
         d.max_cells = int(max_cells)
         d.max_tiles = int(max_tiles if max_tiles is not None else max_cells // 512 + 8 * max_jobs)
-        d.flags = 0
+        d.flags = _abi.IB_BATCH_HOST_IO if host_io else 0
         self.desc = d
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -240,6 +240,20 @@ class Batch:
     def run(self, jobs, stream=None) -> None:
         arr = (_abi.ib_job * len(jobs))(*jobs)
         check(self.lib.ib_batch_run(self.handle, len(jobs), arr, 0, _stream_ptr(stream)), "ib_batch_run")
+
+    def run_host(self, jobs, stream=None) -> None:
+        """One served wave with host-resident data: jobs = [(n, L, X, G, U)], X/G/U host tensors
+        (pinned for asynchronous copies) of shapes (npts, dim), (npts, ncomp), (npts, ncomp)."""
+        arr = (_abi.ib_host_job * len(jobs))()
+        for j, (n, L, X, G, U) in zip(arr, jobs):
+            for b in range(3):
+                j.n[b] = int(n[b]) if b < self.dim else 1
+                j.L[b] = float(L[b]) if b < self.dim else 1.0
+            j.npts = X.shape[0]
+            j.X = X.data_ptr()
+            j.G = G.data_ptr()
+            j.U = U.data_ptr()
+        check(self.lib.ib_batch_run_host(self.handle, len(jobs), arr, _stream_ptr(stream)), "ib_batch_run_host")
 
     def check(self, stream=None) -> None:
         check(self.lib.ib_batch_check(self.handle, _stream_ptr(stream)), "ib_batch_check")

@@ -10,13 +10,15 @@ never leaves the device).  The loop
     the in-flight HBM footprint (I/O buffers + scratch share) fits the
     budget -- requests that arrive while other waves run on the GPU join
     the next free slot, so their work overlaps on the device;
-  * runs a wave as one ib_batch_run (a fixed number of launches for any
-    number of jobs), with the job's inputs copied in and U copied out on
-    the slot's stream;
+  * runs a wave as one ib_batch_run_host call: the jobs' inputs are copied
+    from pinned host memory into the slot's device buffers, the wave runs
+    in a fixed number of launches for any number of jobs, and U is copied
+    back, all on the slot's stream;
   * retires a wave when its completion event fires and records each
     request's latency (completion minus arrival).
 
-`single_job_loop` is the comparison: one ib_spread + ib_interpolate per job.
+`single_job_loop` is the comparison: per job, copy in, ib_spread +
+ib_interpolate on a plan for its grid size, copy U out, wait.
 A job's result is the same whether it runs alone or in a mix: the batched
 kernels give each job its own bins, tiles and summation order.
 """
@@ -116,7 +118,7 @@ class Server:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nstreams = nstreams
         self.batches = [Batch(dim=3, grid="mac", max_jobs=max_jobs, max_points=max_points, max_cells=max_cells,
-                              max_tiles=max_cells // 4096 + 8 * max_jobs, device=self.device)
+                              max_tiles=max_cells // 4096 + 8 * max_jobs, host_io=True, device=self.device)
                         for _ in range(nstreams)]
         self.streams = [torch.cuda.Stream(self.device) for _ in range(nstreams)]
         self.cap = (max_jobs, max_points, max_cells)
@@ -132,25 +134,13 @@ class Server:
 
     def _launch(self, slot: int, reqs: list, footprint: int) -> _Wave:
         s = self.streams[slot]
-        bufs, jobs = [], []
-        with torch.cuda.stream(s):
-            for r in reqs:
-                X = torch.empty((r.npts, 3), dtype=torch.float32, device=self.device)
-                G = torch.empty_like(X)
-                U = torch.empty_like(X)
-                f = torch.empty((3, r.N, r.N, r.N), dtype=torch.float32, device=self.device)
-                X.copy_(r.X, non_blocking=True)
-                G.copy_(r.G, non_blocking=True)
-                bufs.append((X, G, U, f))
-                jobs.append(self.batches[slot].job_struct((r.N, r.N, r.N), (r.L, r.L, r.L), X, G=G, f=f, u=f, U=U))
-            self.batches[slot].run(jobs, stream=s)
-            for r, (X, G, U, f) in zip(reqs, bufs):
-                if r.U is None:
-                    r.U = torch.empty((r.npts, 3), dtype=torch.float32).pin_memory()
-                r.U.copy_(U, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        return _Wave(reqs=reqs, bufs=bufs, event=ev, footprint=footprint)
+        for r in reqs:
+            if r.U is None:
+                r.U = torch.empty((r.npts, 3), dtype=torch.float32).pin_memory()
+        self.batches[slot].run_host([((r.N, r.N, r.N), (r.L, r.L, r.L), r.X, r.G, r.U) for r in reqs], stream=s)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        return _Wave(reqs=reqs, bufs=[], event=ev, footprint=footprint)
 
     def serve(self, requests: list, realtime: bool = True) -> ServeStats:
         """Serve `requests` (sorted by arrival).  realtime=False admits everything at t = 0."""
@@ -223,15 +213,22 @@ class StatsAccumulator:
 
 
 def single_job_loop(requests: list, realtime: bool = True, device=None) -> ServeStats:
-    """One job per launch sequence: for each request in arrival order, copy in, ib_spread +
+    """One job per launch sequence: for each request in arrival order, copy X and G in, ib_spread +
     ib_interpolate on a plan for its grid size, copy U out, wait."""
     device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    plans = {}
+    plans, bufs = {}, {}
     maxn = collections.defaultdict(int)
     for r in requests:
         maxn[r.N] = max(maxn[r.N], r.npts)
     for N, m in maxn.items():
         plans[N] = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", max_points=m, device=device)
+        bufs[N] = (torch.empty((m, 3), dtype=torch.float32, device=device),
+                   torch.empty((m, 3), dtype=torch.float32, device=device),
+                   torch.empty((m, 3), dtype=torch.float32, device=device),
+                   torch.empty((3, N, N, N), dtype=torch.float32, device=device))
+    for r in requests:
+        if r.U is None:
+            r.U = torch.empty((r.npts, 3), dtype=torch.float32).pin_memory()
     stats = StatsAccumulator()
     s = torch.cuda.Stream(device)
     order = sorted(requests, key=lambda r: r.arrival)
@@ -242,12 +239,12 @@ def single_job_loop(requests: list, realtime: bool = True, device=None) -> Serve
                 while time.perf_counter() - t0 < r.arrival:
                     pass
             p = plans[r.N]
-            X = r.X.to(device, non_blocking=True)
-            G = r.G.to(device, non_blocking=True)
-            f = p.spread(X, G, stream=s)
-            U = p.interpolate(X, f, reuse_bins=True, stream=s)
-            if r.U is None:
-                r.U = torch.empty((r.npts, 3), dtype=torch.float32).pin_memory()
+            Xb, Gb, Ub, f = bufs[r.N]
+            X, G, U = Xb[: r.npts], Gb[: r.npts], Ub[: r.npts]
+            X.copy_(r.X, non_blocking=True)
+            G.copy_(r.G, non_blocking=True)
+            p.spread(X, G, f=f, stream=s)
+            p.interpolate(X, f, U=U, reuse_bins=True, stream=s)
             r.U.copy_(U, non_blocking=True)
             s.synchronize()
             r.t_done = time.perf_counter() - t0
@@ -266,5 +263,6 @@ def make_requests(specs, L: float = 1.0, arrivals=None) -> list:
         X = ib_inputs.job_points(sp, L)
         G = ib_inputs.normal_array(sp.seed, (sp.npts, 3), purpose="job-G")
         out.append(Request(rid=i, N=sp.N, X=torch.from_numpy(X).pin_memory(), G=torch.from_numpy(G).pin_memory(),
-                           arrival=float(arrivals[i]) if arrivals is not None else 0.0, L=L))
+                           arrival=float(arrivals[i]) if arrivals is not None else 0.0, L=L,
+                           U=torch.empty((sp.npts, 3), dtype=torch.float32).pin_memory()))
     return out

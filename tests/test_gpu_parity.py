@@ -192,6 +192,35 @@ def test_nonfinite_and_out_of_range_positions_are_reported(P, orc):
     assert e.value.status == IB_ERR_RANGE
 
 
+def test_positions_changed_after_binning_are_reported(P):
+    from paper_2012_06646_gb300._abi import IB_ERR_BINS_STALE, IBError
+    n = (32, 32, 32)
+    plan = P(3, n, (1.0, 1.0, 1.0), max_points=500)
+    X = ib_inputs.uniform_points(21, 500, (1.0, 1.0, 1.0), 3)
+    G = ib_inputs.normal_array(22, (500, 3))
+    u = ib_inputs.normal_array(23, plan.grid_shape())
+    Xd, Gd, ud = dev(X), dev(G), dev(u)
+    plan.bin(Xd)
+    f_ok = plan.spread(Xd, Gd, reuse_bins=True)
+    plan.check()
+    Xd[7] = torch.tensor([(X[7, 0] + 0.5) % 1.0, X[7, 1], X[7, 2]], dtype=torch.float32)   # another tile
+    f = plan.spread(Xd, Gd, reuse_bins=True)
+    U = plan.interpolate(Xd, ud, reuse_bins=True)
+    with pytest.raises(IBError) as e:
+        plan.check()
+    assert e.value.status == IB_ERR_BINS_STALE
+    Uh = host(U)
+    assert np.isnan(Uh[7]).all() and np.isfinite(np.delete(Uh, 7, axis=0)).all()
+    # the moved point contributes nothing; every other contribution is as before
+    Xk = X.copy()
+    Gk = G.copy()
+    Gk[7] = 0.0
+    plan.bin(dev(Xk))
+    f_ref = plan.spread(dev(Xk), dev(Gk), reuse_bins=False)
+    assert np.allclose(host(f), host(f_ref), rtol=1e-5, atol=1e-5 * float(np.abs(host(f_ok)).max()))
+    plan.check()
+
+
 def test_compensated_spread_on_membranes(P, orc):
     """Clustered RBC membranes (red-cell packing), FP32 with TwoSum node sums."""
     mem = ib_inputs.pack_membranes(0, target_cells=6, max_attempts=2000)

@@ -52,6 +52,39 @@ def test_batched_wave_equals_single_jobs_and_oracle(mods, orc):
         plan.close()
 
 
+def test_batch_run_host_equals_device_batch(mods):
+    Plan, Batch, serve = mods
+    specs = _jobs(7, 10)
+    dbatch = Batch(dim=3, max_jobs=16, max_points=1 << 16, max_cells=1 << 20)
+    hbatch = Batch(dim=3, max_jobs=16, max_points=1 << 16, max_cells=1 << 20, host_io=True)
+    jobs, outs, hjobs, keep = [], [], [], []
+    for sp in specs:
+        X = ib_inputs.job_points(sp)
+        G = ib_inputs.normal_array(sp.seed, (sp.npts, 3), purpose="job-G")
+        Xd, Gd = dev(X), dev(G)
+        f = torch.empty((3, sp.N, sp.N, sp.N), device="cuda")
+        U = torch.empty_like(Xd)
+        keep.append((Xd, Gd, f))             # the device batch reads them when it runs
+        outs.append(U)
+        jobs.append(dbatch.job_struct((sp.N,) * 3, (1.0,) * 3, Xd, G=Gd, f=f, u=f, U=U))
+        Uh = torch.full((sp.npts, 3), float("nan")).pin_memory()
+        hjobs.append(((sp.N,) * 3, (1.0,) * 3, torch.from_numpy(X).pin_memory(), torch.from_numpy(G).pin_memory(), Uh))
+    dbatch.run(jobs)
+    hbatch.run_host(hjobs)
+    torch.cuda.synchronize()
+    dbatch.check()
+    hbatch.check()
+    for U, (_, _, _, _, Uh) in zip(outs, hjobs):
+        assert torch.equal(U.cpu(), Uh)
+    # two waves in a row on the same batch object reuse its buffers
+    hbatch.run_host(hjobs[:3])
+    torch.cuda.synchronize()
+    for U, (_, _, _, _, Uh) in zip(outs[:3], hjobs[:3]):
+        assert torch.equal(U.cpu(), Uh)
+    dbatch.close()
+    hbatch.close()
+
+
 def test_server_continuous_batching_matches_single_loop(mods):
     Plan, Batch, serve = mods
     specs = _jobs(9, 60)

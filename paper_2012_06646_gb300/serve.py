@@ -118,7 +118,7 @@ class Server:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nstreams = nstreams
         self.batches = [Batch(dim=3, grid="mac", max_jobs=max_jobs, max_points=max_points, max_cells=max_cells,
-                              max_tiles=max_cells // 4096 + 8 * max_jobs, host_io=True, device=self.device)
+                              max_tiles=max_cells // 512 + 8 * max_jobs, host_io=True, device=self.device)
                         for _ in range(nstreams)]
         self.streams = [torch.cuda.Stream(self.device) for _ in range(nstreams)]
         self.cap = (max_jobs, max_points, max_cells)

@@ -52,8 +52,8 @@ def test_footprint_and_validation_on_host(abi):
     lib = abi.load()
     size = ctypes.c_size_t()
     assert lib.ib_plan_footprint(ctypes.byref(_desc(abi)), ctypes.byref(size)) == abi.IB_OK
-    # 128^3 MAC, 10^6 points: cells 8.4 MB, 4 point arrays 16 MB, boxes 512 x 3 x 20^3 x 4 B
-    assert 60e6 < size.value < 80e6
+    # 128^3 MAC, 10^6 points: cells 8.4 MB, point arrays 20 MB, boxes 4096 x 3 x 12^3 x 4 B (84.9 MB)
+    assert 105e6 < size.value < 120e6
     comp = ctypes.c_size_t()
     assert lib.ib_plan_footprint(ctypes.byref(_desc(abi, flags=abi.IB_PLAN_COMPENSATED)), ctypes.byref(comp)) == 0
     assert comp.value > size.value
@@ -85,8 +85,8 @@ def test_batch_footprints_on_host(abi):
     jb = ctypes.c_size_t()
     tiles = ctypes.c_longlong()
     assert lib.ib_batch_job_footprint(ctypes.byref(d), ctypes.byref(job), ctypes.byref(jb), ctypes.byref(tiles)) == 0
-    assert tiles.value == 6 ** 3                  # 96 / 16 tiles per dimension
-    assert jb.value == 4 * (96 ** 3 + 4 * 5000) + 216 * 3 * 20 ** 3 * 4
+    assert tiles.value == 12 ** 3                 # 96 / 8 tiles per dimension
+    assert jb.value == 4 * (96 ** 3 + 4 * 5000) + 12 ** 3 * 3 * 12 ** 3 * 4
     d.max_cells = 0
     assert lib.ib_batch_footprint(ctypes.byref(d), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG
 

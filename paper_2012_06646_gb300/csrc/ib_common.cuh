@@ -279,16 +279,17 @@ __device__ __forceinline__ double mfma(double a, double b, double c) { return fm
 __device__ __forceinline__ void msincospi(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void msincospi(double x, double* s, double* c) { sincospi(x, s, c); }
 
-// FP32: q from x rsqrt(x) (x in [1, 2]) and one reciprocal 1/(a b) for the two
-// small weights, rc^2/a = rc^2 b/(a b) and r^2/b = r^2 a/(a b); relative error of
-// a few ulp, far inside the 1e-5 accuracy target.
+// FP32: q from x rsqrt(x) (x in [1, 2]) and one approximate reciprocal
+// 1/(a b) (a b in [4, 16]) for the two small weights, rc^2/a = rc^2 b/(a b) and
+// r^2/b = r^2 a/(a b); relative error of a few ulp, far inside the 1e-5
+// accuracy target.
 __device__ __forceinline__ void weights(int kernel, float r, float rc, float w[4]) {
   if (kernel == 0) {
     const float x = fmaf(4.f * r, rc, 1.f);
     const float q = x * rsqrtf(x);
     const float a = 1.f + 2.f * rc + q;
     const float b = 1.f + 2.f * r + q;
-    const float inv = __frcp_rn(a * b);
+    const float inv = __fdividef(1.f, a * b);
     w[0] = rc * rc * b * inv;
     w[1] = 0.125f * a;
     w[2] = 0.125f * b;

@@ -4,16 +4,14 @@
 //
 // Spreading (Eq. disc-spread) is the paper's parallel spread re-designed for
 // one GPU with shared memory instead of a per-shift sort and segmented
-// reduce (Algorithm 4): the grid is cut into tiles; the CTA of a tile takes
-// the points binned into the tile's cells (no duplication) and adds their
-// s^d support contributions into a shared-memory box covering the tile plus
-// a 2-node apron on every side, then writes the box to scratch.  A second
-// kernel forms every grid node as the sum of the (at most 2^d) boxes that
-// cover it, in a fixed tile order.  Inside a box, warps work on cell layers
-// that are 5 layers apart at any moment (the support of a cell layer spans 5
-// node layers), so no two warps touch the same node concurrently, and each
-// warp issues its additions in program order.  Every node sum therefore has
-// a fixed order and the result is bit-reproducible run to run.
+// reduce (Algorithm 4): the grid is cut into 8^3 tiles; one warp takes the
+// points binned into a tile's cells (each point exactly once, in cell order)
+// and adds their s^d support contributions into shared-memory boxes covering
+// the tile plus a 2-node apron on every side, then writes the boxes to
+// scratch.  A second kernel forms every grid node as the sum of the (at most
+// 2^d) boxes that cover it, in a fixed tile order.  A box has a single writer
+// (its warp), which adds the points in a fixed order, so every node sum has a
+// fixed order and the result is bit-reproducible run to run.
 //
 // Interpolation (Eq. disc-interp, Algorithm 3) keeps one thread per point
 // (each point's sum has one writer), grouped by tile: the tile's grid values
@@ -27,8 +25,6 @@
 namespace ibgb {
 
 namespace {
-
-constexpr int kBoxThreads = 128;   // 4 warps: one per group of 5 cell layers
 
 constexpr int kThreads = 256;
 
@@ -56,43 +52,6 @@ __device__ __forceinline__ void tile_coords(const int* ntile, const int* n, long
   TE[0] = min(TS, n[0] - T0[0]);
   TE[1] = min(TS, n[1] - T0[1]);
   TE[2] = (D == 3) ? min(TS, n[2] - T0[2]) : 1;
-}
-
-// Rows of one cell layer of a tile, flattened for a warp: lane r < rows
-// holds the sorted start and count of row r; returns the layer's point count.
-template <int D>
-__device__ __forceinline__ uint32_t layer_rows(const Job& jb, const Bins& B, const int T0[3], const int TE[3],
-                                               int l, int lane, uint32_t* rstart, uint32_t* rpre) {
-  const int rows = (D == 3) ? TE[1] : 1;
-  uint32_t st = 0, cnt = 0;
-  if (lane < rows) {
-    long long cell;
-    if (D == 3) cell = T0[0] + (long long)jb.n[0] * ((T0[1] + lane) + (long long)jb.n[1] * (T0[2] + l));
-    else cell = T0[0] + (long long)jb.n[0] * (T0[1] + l);
-    cell += jb.cell_base;
-    st = B.count[cell];
-    cnt = B.count[cell + TE[0]] - st;
-  }
-  uint32_t inc = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  rstart[lane] = st;
-  rpre[lane] = inc - cnt;
-  __syncwarp();
-  return __shfl_sync(0xffffffffu, inc, 31);
-}
-
-// Sorted position of flattened index q of a layer.
-__device__ __forceinline__ uint32_t layer_pos(uint32_t q, int rows, const uint32_t* rstart, const uint32_t* rpre) {
-  int lo = 0, hi = rows - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (rpre[mid] <= q) lo = mid; else hi = mid - 1;
-  }
-  return rstart[lo] + (q - rpre[lo]);
 }
 
 // Per-point cell data relative to a tile box: offsets of the t = -1 node for
@@ -126,31 +85,44 @@ __device__ __forceinline__ bool point_box(const Job& jb, const Shape& sh, const 
 }
 
 // ---------------------------------------------------------------------------
-// Spreading into a tile box, one CTA per (tile, component).  The box holds
-// one component of the tile plus a 2-node apron in shared memory (two planes
-// in compensated mode).  Two stages per batch of kBatch points of a cell
-// layer:
+// Spreading into tile boxes, one warp per (tile, component).  The warp owns a
+// shared-memory box holding one component of the tile plus a 2-node apron on
+// every side (two planes in compensated mode), so no other warp touches it
+// and no block-wide barrier is needed.  The warp walks the points binned in
+// the tile's cells (each point exactly once, cell order, index order inside a
+// cell) in batches of kSpreadBatch, two stages per batch:
 //   1. lanes = points: each lane computes its point's cell in each dimension,
-//      the component's four weights per dimension and, for the component, the
-//      16 products wx[tx] wy[ty] g (g = h^-d G), the four z weights, and the
-//      box offset of the t = -1 corner; it stores them as one staging record;
-//   2. warp = point: the warp walks the batch's points in order; lane
+//      the component's four weights per dimension and, with g = h^-d G, the
+//      16 products wx[tx] wy[ty] g, the four z weights and the box offset of
+//      the t = -1 corner; it stores them as one staging record;
+//   2. warp = point: the warp walks the batch's records in order; lane
 //      (tx, ty, tzb) owns the support nodes (tx, ty, tzb) and (tx, ty, tzb+2)
 //      of the point's 4x4x4 box (4x4 in 2-D, lanes 16-31 idle), so the 32
 //      lanes touch 64 distinct nodes and a plain read-modify-write is
-//      race-free; __syncwarp separates consecutive points.  The next point's
-//      record is read before the current point's additions, and the next
-//      batch's point data is fetched from global memory before this batch's
-//      additions.
+//      race-free; __syncwarp orders consecutive points.  Each node's additions
+//      therefore happen in the fixed point order.  The next record is read
+//      before the current point's additions, and the next batch's point data
+//      is fetched from global memory before this batch's additions.
+// With 8^3 tiles the 32 lanes of one addition hit 32 distinct banks (rows 12
+// entries apart, the two z planes 144 = 16 mod 32 apart).
 // Compensated mode keeps (sum, error) per node and adds by TwoSum.
 // ---------------------------------------------------------------------------
-constexpr int kBatch = 32;
+constexpr int kSpreadWarps = 2;   // independent (tile, component) units per CTA (W below)
+constexpr int kSpreadBatch = 32;  // points per staging batch (one per lane in stage 1)
 
-// Words of a record: 16 products (+ 4 z weights in 3-D), an odd number of
-// 16-byte chunks so the lanes' vector stores of stage 1 fall into distinct
-// bank groups; the box offsets of a batch sit in a separate array.  Small
-// records keep five CTAs of 16^3 tiles resident per SM.
-__host__ __device__ constexpr int rec_words(int dim) { return dim == 3 ? 20 : 20; }
+// Record of one point-component: the 16 products, then in 3-D two groups
+// (w0, w2, off, 0) and (w1, w3, off, 0) -- lane half tzb reads group tzb
+// with one vector load -- and in 2-D (off, 0, 0, 0).  7 (5) 16-byte chunks,
+// an odd number, so the stage-1 vector stores of 8 lanes hit distinct banks.
+template <int D>
+struct WRec {
+  static constexpr int words = D == 3 ? 28 : 20;
+};
+
+__device__ __forceinline__ float off_bits(int o, float) { return __int_as_float(o); }
+__device__ __forceinline__ double off_bits(int o, double) { return __longlong_as_double((long long)o); }
+__device__ __forceinline__ int bits_off(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int bits_off(double v) { return (int)__double_as_longlong(v); }
 
 template <typename T>
 __device__ __forceinline__ void two_sum_into(T* s, T* e, T v) {
@@ -168,6 +140,15 @@ __device__ __forceinline__ void store4(float* d, float a, float b, float c, floa
 __device__ __forceinline__ void store4(double* d, double a, double b, double c, double e) {
   reinterpret_cast<double2*>(d)[0] = make_double2(a, b);
   reinterpret_cast<double2*>(d)[1] = make_double2(c, e);
+}
+__device__ __forceinline__ void load3(const float* s, float& a, float& b, float& c) {
+  const float4 q = *reinterpret_cast<const float4*>(s);
+  a = q.x; b = q.y; c = q.z;
+}
+__device__ __forceinline__ void load3(const double* s, double& a, double& b, double& c) {
+  const double2 q = reinterpret_cast<const double2*>(s)[0];
+  a = q.x; b = q.y;
+  c = s[2];
 }
 
 // Cell offset (box coordinates of the t = -1 node) and weights of one
@@ -194,141 +175,411 @@ __device__ __forceinline__ bool point_comp(const Job& jb, const Shape& sh, const
   return inside;
 }
 
-template <typename T, int D, int TS, bool COMP>
-__global__ void __launch_bounds__(kBoxThreads) k_spread_box(const __grid_constant__ Jobs J, const Shape sh,
-                                                            const Bins B, T* __restrict__ boxes) {
+template <typename T, int D, int TS, bool COMP, int W = kSpreadWarps>
+__global__ void __launch_bounds__(32 * W) k_spread_warp(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
+                                                         T* __restrict__ boxes, long long nunits) {
   using Gm = Geo<D, TS>;
-  constexpr int REC = rec_words(D);
+  constexpr int REC = WRec<D>::words;
+  constexpr int PLANES = COMP ? 2 : 1;
+  constexpr int NROWS = (D == 3) ? TS * TS : TS;     // cell rows (x runs) of a full tile
+  static_assert(NROWS % 32 == 0 && (NROWS & (NROWS - 1)) == 0, "rows: a power of two, at least 32");
+  constexpr int WARP_T = PLANES * Gm::BV + kSpreadBatch * REC;
+  static_assert((PLANES * Gm::BV * sizeof(T)) % 16 == 0 && (WARP_T * sizeof(T)) % 16 == 0, "16-byte sections");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* boxS = reinterpret_cast<T*>(smem_raw);
-  T* boxE = boxS + Gm::BV;                                        // compensated mode only
-  T* stage_all = boxS + (COMP ? 2 : 1) * Gm::BV;
-  __shared__ uint32_t rstart_s[4][32];
-  __shared__ uint32_t rpre_s[4][32];
-  __shared__ int off_s[4][kBatch];      // box offset of each record's t = -1 corner
+  __shared__ uint32_t rstart_s[W][NROWS];
+  __shared__ uint32_t rpre_s[W][NROWS + 1];
+  __shared__ Job sjob[W];                          // one copy of the job per warp (broadcast reads)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long unit = (long long)blockIdx.x * W + warp;
+  if (unit >= nunits) return;                      // the whole warp leaves; no block barrier follows
+  T* boxS = reinterpret_cast<T*>(smem_raw) + warp * WARP_T;
+  T* boxE = boxS + Gm::BV;                         // compensated mode only
+  T* rec_s = boxS + PLANES * Gm::BV;
+  uint32_t* rstart = rstart_s[warp];
+  uint32_t* rpre = rpre_s[warp];
   const int nc = sh.ncomp;
-  __shared__ Job sjob;                  // one copy of the job per CTA (broadcast reads)
-  const long long gt = blockIdx.x / nc;
-  const int a = blockIdx.x - (int)gt * nc;
-  if (threadIdx.x == 0) sjob = job_at(J, job_of_tile(J, gt));
-  __syncthreads();
-  const Job& jb = sjob;
+  const long long gt = unit / nc;
+  const int a = (int)(unit - gt * nc);
+  {
+    const int j = __shfl_sync(0xffffffffu, lane == 0 ? job_of_tile(J, gt) : 0, 0);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&job_at(J, j));
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sjob[warp]);
+    for (int w = lane; w < (int)(sizeof(Job) / 4); w += 32) dst[w] = src[w];
+    __syncwarp();
+  }
+  const Job& jb = sjob[warp];
   if (jb.G == nullptr) return;
   int T0[3], TE[3];
   tile_coords<D, TS>(jb.ntile, jb.n, gt - jb.tile_base, T0, TE);
-  for (int i = threadIdx.x; i < (COMP ? 2 : 1) * Gm::BV; i += kBoxThreads) boxS[i] = (T)0;
-  __syncthreads();
+  {
+    constexpr int NV = (int)(PLANES * Gm::BV * sizeof(T) / 16);
+    uint4* z = reinterpret_cast<uint4*>(boxS);
+    for (int i = lane; i < NV; i += 32) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  // Rows of the tile's cells (x fastest inside a row): sorted start and exclusive prefix of the counts.
+  const int rows = (D == 3) ? TE[1] * TE[2] : TE[1];
+  uint32_t M = 0;
+#pragma unroll
+  for (int k = 0; k < NROWS / 32; ++k) {
+    const int r = lane + 32 * k;
+    uint32_t st = 0, cnt = 0;
+    if (r < rows) {
+      const int y = T0[1] + ((D == 3) ? r % TE[1] : r);
+      const int z = (D == 3) ? T0[2] + r / TE[1] : 0;
+      const long long cell = jb.cell_base + T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
+      st = B.count[cell];
+      cnt = B.count[cell + TE[0]] - st;
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    rstart[r] = st;
+    rpre[r] = M + inc - cnt;
+    M += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* stage = stage_all + warp * kBatch * REC;
-  const int nlayers = TE[D - 1];
-  const int rows = (D == 3) ? TE[1] : 1;
-  const T* Gp = (const T*)jb.G;
   const T* Xg = (const T*)jb.X;
+  const T* Gp = (const T*)jb.G;
   const T hmd = (T)jb.hmd;
+  // Sorted point q of the tile -> its coordinates and component-a value.
+  auto load_point = [&](uint32_t q, T xs[D], T& gs) {
+    int lo = 0;
+#pragma unroll
+    for (int step = NROWS / 2; step >= 1; step >>= 1)
+      if (lo + step < rows && rpre[lo + step] <= q) lo += step;
+    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])] - jb.pt_base;
+#pragma unroll
+    for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
+    gs = Gp[li * nc + a];
+  };
+
   const int tx = lane & 3, ty = (lane >> 2) & 3, tzb = lane >> 4;
   const int lane_off = (D == 3) ? ((tzb * Gm::BY + ty) * Gm::BX + tx) : (ty * Gm::BX + tx);
   const bool lane_on = (D == 3) || lane < 16;
   constexpr int ZSTEP = 2 * Gm::BY * Gm::BX;
-  for (int phase = 0; phase < 5; ++phase) {
-    for (int l = 5 * warp + phase; l < nlayers; l += 20) {
-      const uint32_t M = layer_rows<D>(jb, B, T0, TE, l, lane, rstart_s[warp], rpre_s[warp]);
-      // point data of the first batch
-      T xs[D], gs = (T)0;
-      if (lane < M) {
-        const long long li = (long long)B.perm[layer_pos(lane, rows, rstart_s[warp], rpre_s[warp])] - jb.pt_base;
+  const int zsel = (D == 3) ? 16 + 4 * tzb : 16;   // this lane's (z0, z1, off) group of a record
+  T xs[D], gs = (T)0;
+  if (lane < M) load_point(lane, xs, gs);
+  for (uint32_t base = 0; base < M; base += kSpreadBatch) {
+    // Stage 1: lane q prepares the record of point base + q.
+    if (base + lane < M) {
+      int o[3] = {0, 0, 0};
+      T w[3][4];
+      const bool inside = point_comp<T, D>(jb, sh, xs, T0, TE, a, o, w);
+      T ga = hmd * gs;
+      if (!inside) {                 // X changed after binning: contribute nothing, report
+        atomicOr(B.err, ERR_STALE);
 #pragma unroll
-        for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
-        gs = Gp[li * nc + a];
+        for (int b = 0; b < 3; ++b) {
+          o[b] = 1;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) w[b][t] = (T)0;
+        }
+        ga = (T)0;
       }
-      for (uint32_t base = 0; base < M; base += kBatch) {
-        // Stage 1: lane q prepares the record of point base + q.
-        if (base + lane < M) {
-          int o[3] = {0, 0, 0};
-          T w[3][4];
-          const bool inside = point_comp<T, D>(jb, sh, xs, T0, TE, a, o, w);
-          T ga = hmd * gs;
-          if (!inside) {                 // X changed after binning: contribute nothing, report
-            atomicOr(B.err, ERR_STALE);
+      T* rec = rec_s + lane * REC;
+      T wxg[4];
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-              o[b] = 1;
+      for (int t = 0; t < 4; ++t) wxg[t] = w[0][t] * ga;
 #pragma unroll
-              for (int t = 0; t < 4; ++t) w[b][t] = (T)0;
-            }
-            ga = (T)0;
-          }
-          T* rec = stage + lane * REC;
-          T wxg[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) wxg[t] = w[0][t] * ga;
-#pragma unroll
-          for (int yy = 0; yy < 4; ++yy)
-            store4(rec + yy * 4, wxg[0] * w[1][yy], wxg[1] * w[1][yy], wxg[2] * w[1][yy], wxg[3] * w[1][yy]);
-          int off = o[1] * Gm::BX + o[0];
-          if (D == 3) {
-            store4(rec + 16, w[D - 1][0], w[D - 1][2], w[D - 1][1], w[D - 1][3]);
-            off += o[D - 1] * Gm::BY * Gm::BX;
-          }
-          off_s[warp][lane] = off;
-        }
-        // fetch the next batch's point data while this batch is added
-        const uint32_t nq = base + kBatch + lane;
-        if (nq < M) {
-          const long long li = (long long)B.perm[layer_pos(nq, rows, rstart_s[warp], rpre_s[warp])] - jb.pt_base;
-#pragma unroll
-          for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
-          gs = Gp[li * nc + a];
-        }
-        __syncwarp();
-        // Stage 2: the warp adds the points of the batch one by one.
-        const int cnt = (int)min((uint32_t)kBatch, M - base);
-        const T* r0 = stage;
-        int nb = off_s[warp][0];
-        T npv = r0[lane & 15];
-        T nz0 = (D == 3) ? r0[16 + 2 * tzb] : (T)1;
-        T nz1 = (D == 3) ? r0[17 + 2 * tzb] : (T)0;
+      for (int yy = 0; yy < 4; ++yy)
+        store4(rec + yy * 4, wxg[0] * w[1][yy], wxg[1] * w[1][yy], wxg[2] * w[1][yy], wxg[3] * w[1][yy]);
+      int off = o[1] * Gm::BX + o[0];
+      if (D == 3) {
+        off += o[D - 1] * Gm::BY * Gm::BX;
+        const T ob = off_bits(off, (T)0);
+        store4(rec + 16, w[D - 1][0], w[D - 1][2], ob, (T)0);
+        store4(rec + 20, w[D - 1][1], w[D - 1][3], ob, (T)0);
+      } else {
+        store4(rec + 16, off_bits(off, (T)0), (T)0, (T)0, (T)0);
+      }
+    }
+    // fetch the next batch's point data while this batch is added
+    const uint32_t nq = base + kSpreadBatch + lane;
+    if (nq < M) load_point(nq, xs, gs);
+    __syncwarp();
+    // Stage 2: the warp adds the points of the batch one by one.
+    const int cnt = (int)min((uint32_t)kSpreadBatch, M - base);
+    T npv = rec_s[lane & 15];
+    T nz0, nz1, nob;
+    if (D == 3) {
+      load3(rec_s + zsel, nz0, nz1, nob);
+    } else {
+      nz0 = (T)1;
+      nz1 = (T)0;
+      nob = rec_s[16];
+    }
 #pragma unroll 4
-        for (int i = 0; i < cnt; ++i) {
-          const int cb = nb;
-          const T pv = npv, z0 = nz0, z1 = nz1;
-          if (i + 1 < cnt) {
-            const T* rn = stage + (i + 1) * REC;
-            nb = off_s[warp][i + 1];
-            npv = rn[lane & 15];
-            if (D == 3) {
-              nz0 = rn[16 + 2 * tzb];
-              nz1 = rn[17 + 2 * tzb];
-            }
+    for (int i = 0; i < cnt; ++i) {
+      const int idx = bits_off(nob) + lane_off;
+      const T pv = npv, z0 = nz0, z1 = nz1;
+      if (i + 1 < cnt) {
+        const T* rn = rec_s + (i + 1) * REC;
+        npv = rn[lane & 15];
+        if (D == 3) load3(rn + zsel, nz0, nz1, nob);
+        else nob = rn[16];
+      }
+      if (lane_on) {
+        if (D == 3) {
+          if (COMP) {
+            two_sum_into(boxS + idx, boxE + idx, pv * z0);
+            two_sum_into(boxS + idx + ZSTEP, boxE + idx + ZSTEP, pv * z1);
+          } else {
+            const T v0 = boxS[idx], v1 = boxS[idx + ZSTEP];
+            boxS[idx] = v0 + pv * z0;
+            boxS[idx + ZSTEP] = v1 + pv * z1;
           }
-          if (lane_on) {
-            const int idx = cb + lane_off;
-            if (D == 3) {
-              if (COMP) {
-                two_sum_into(boxS + idx, boxE + idx, pv * z0);
-                two_sum_into(boxS + idx + ZSTEP, boxE + idx + ZSTEP, pv * z1);
-              } else {
-                const T v0 = boxS[idx], v1 = boxS[idx + ZSTEP];
-                boxS[idx] = v0 + pv * z0;
-                boxS[idx + ZSTEP] = v1 + pv * z1;
-              }
-            } else {
-              if (COMP) two_sum_into(boxS + idx, boxE + idx, pv);
-              else boxS[idx] += pv;
-            }
-          }
-          __syncwarp();
+        } else {
+          if (COMP) two_sum_into(boxS + idx, boxE + idx, pv);
+          else boxS[idx] += pv;
         }
       }
       __syncwarp();
     }
-    __syncthreads();
   }
+  __syncwarp();
   // Box -> scratch [tile][comp][plane][BV], 16-byte vectors.
-  const int nvec = (int)((COMP ? 2 : 1) * Gm::BV * sizeof(T) / 16);
+  constexpr int NV = (int)(PLANES * Gm::BV * sizeof(T) / 16);
   const uint4* src = reinterpret_cast<const uint4*>(boxS);
-  uint4* dst = reinterpret_cast<uint4*>(boxes + (gt * nc + a) * (long long)((COMP ? 2 : 1) * Gm::BV));
-  for (int i = threadIdx.x; i < nvec; i += kBoxThreads) dst[i] = src[i];
+  uint4* dst = reinterpret_cast<uint4*>(boxes + unit * (long long)(PLANES * Gm::BV));
+  for (int i = lane; i < NV; i += 32) dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Spreading of three-component fields in 3-D (the MAC velocity grid, or three
+// cell-centred components): one warp per 8^3 tile owns the three component
+// boxes of the tile, so each point's cell map and weights are computed once
+// for all components, and the three components' read-modify-writes of a point
+// are independent of one another (loads first, then stores).  The same two
+// stages and per-node order of additions as k_spread_warp.
+// Record of a point (76 words, 19 16-byte chunks, an odd number so the
+// stage-1 vector stores of 8 lanes hit distinct banks):
+//   chunk j = ty*4 + tx (j < 16): (p0, p1, p2, pk), p_a = wx_a[tx] wy_a[ty] g_a
+//     and pk the three box offsets (o_0 in bits 0-11, o_1 - o_0 + 512 in bits
+//     12-21, o_2 - o_0 + 512 in bits 22-31);
+//   chunk 16 + tzb: (wz[tzb], wz[tzb+2]) for xi_z = 1/2 (components 0 and 1),
+//     then the same for component 2 (xi_z = 0 on the MAC grid);
+// so stage 2 reads two vectors per point and lane.  Point data is fetched two
+// batches ahead (sorted position and point index for batch b + 2, coordinates
+// and forces for batch b + 1), so stage 1 never waits on a dependent gather.
+// ---------------------------------------------------------------------------
+constexpr int kRec3 = 76;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+__device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ double4 load4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// Stage 1 for one point: the record at rec.
+template <typename T, bool MAC>
+__device__ __forceinline__ void tile3_record(const Job& jb, const Shape& sh, const Bins& B, const T xs[3],
+                                             const T gs[3], const int T0[3], const int TE[3], T* rec) {
+  using Gm = Geo<3, 8>;
+  int o0[3], dl[3];
+  T w0[3][4], w1[3][4];
+  bool inside = true;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    Cell1<T> c;
+    const uint32_t e = point_cell<T>(xs[b], jb, b, c);
+    const int n = jb.n[b];
+    const int cphys = ((unsigned)c.i0 < (unsigned)n) ? c.i0 : modn(c.i0, n);
+    dl[b] = c.i1 - c.i0;
+    inside = inside && e == 0 && (unsigned)(cphys - T0[b]) < (unsigned)TE[b] && dl[b] >= -1 && dl[b] <= 0;
+    o0[b] = cphys - T0[b] + 1;
+    if (MAC) weights(sh.kernel, c.r0, c.c0, w0[b]);
+    weights(sh.kernel, c.r1, c.c1, w1[b]);
+  }
+  const T hmd = (T)jb.hmd;
+  T g[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[a] = hmd * gs[a];
+  if (!inside) {                 // X changed after binning: contribute nothing, report
+    atomicOr(B.err, ERR_STALE);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      o0[b] = 1;
+      dl[b] = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) w0[b][t] = w1[b][t] = (T)0;
+    }
+  }
+  // component a: xi = 0 in dimension a on the MAC grid, 1/2 elsewhere
+  int oa[3];
+  T wxg[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const bool hx = !MAC || a != 0, hy = !MAC || a != 1, hz = !MAC || a != 2;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wxg[a][t] = (hx ? w1[0][t] : w0[0][t]) * g[a];
+    oa[a] = (o0[0] + (hx ? dl[0] : 0)) + (o0[1] + (hy ? dl[1] : 0)) * Gm::BX +
+            (o0[2] + (hz ? dl[2] : 0)) * (Gm::BY * Gm::BX);
+  }
+  const T pkb = off_bits(oa[0] | ((oa[1] - oa[0] + 512) << 12) | ((oa[2] - oa[0] + 512) << 22), (T)0);
+  const T* wy1 = MAC ? w0[1] : w1[1];   // component 1's y weights
+#pragma unroll
+  for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
+    for (int xx = 0; xx < 4; ++xx)
+      store4(rec + 4 * (yy * 4 + xx), wxg[0][xx] * w1[1][yy], wxg[1][xx] * wy1[yy], wxg[2][xx] * w1[1][yy], pkb);
+  const T* wz2 = MAC ? w0[2] : w1[2];   // component 2's z weights
+  store4(rec + 64, w1[2][0], w1[2][2], wz2[0], wz2[2]);
+  store4(rec + 68, w1[2][1], w1[2][3], wz2[1], wz2[3]);
+}
+
+// Stage 2 for one batch of cnt records starting at rb (one record past the
+// batch is allocated, so the look-ahead read of record cnt stays in bounds).
+template <typename T, bool COMP>
+__device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane) {
+  using Gm = Geo<3, 8>;
+  constexpr int PLANES = COMP ? 2 : 1;
+  constexpr int ZSTEP = 2 * Gm::BY * Gm::BX;
+  const int tx = lane & 3, ty = (lane >> 2) & 3, tzb = lane >> 4;
+  const int lane_off = (tzb * Gm::BY + ty) * Gm::BX + tx;
+  const int ch = 4 * (lane & 15);
+  const int zc = 64 + 4 * tzb;
+  typename Vec4<T>::type q = load4(rb + ch);
+  typename Vec4<T>::type z = load4(rb + zc);
+#pragma unroll 2
+  for (int i = 0; i < cnt; ++i) {
+    const T c0 = q.x, c1 = q.y, c2 = q.z;
+    const int pk = bits_off(q.w);
+    const T z0 = z.x, z1 = z.y, z20 = z.z, z21 = z.w;
+    const T* rn = rb + (i + 1) * kRec3;
+    q = load4(rn + ch);
+    z = load4(rn + zc);
+    const int q0 = (pk & 4095) + lane_off;
+    const int q1 = q0 + ((pk >> 12) & 1023) - 512 + PLANES * Gm::BV;
+    const int q2 = q0 + (int)((unsigned)pk >> 22) - 512 + 2 * PLANES * Gm::BV;
+    if (COMP) {
+      two_sum_into(box + q0, box + q0 + Gm::BV, c0 * z0);
+      two_sum_into(box + q0 + ZSTEP, box + q0 + ZSTEP + Gm::BV, c0 * z1);
+      two_sum_into(box + q1, box + q1 + Gm::BV, c1 * z0);
+      two_sum_into(box + q1 + ZSTEP, box + q1 + ZSTEP + Gm::BV, c1 * z1);
+      two_sum_into(box + q2, box + q2 + Gm::BV, c2 * z20);
+      two_sum_into(box + q2 + ZSTEP, box + q2 + ZSTEP + Gm::BV, c2 * z21);
+    } else {
+      const T v00 = box[q0], v01 = box[q0 + ZSTEP];
+      const T v10 = box[q1], v11 = box[q1 + ZSTEP];
+      const T v20 = box[q2], v21 = box[q2 + ZSTEP];
+      box[q0] = v00 + c0 * z0;
+      box[q0 + ZSTEP] = v01 + c0 * z1;
+      box[q1] = v10 + c1 * z0;
+      box[q1 + ZSTEP] = v11 + c1 * z1;
+      box[q2] = v20 + c2 * z20;
+      box[q2 + ZSTEP] = v21 + c2 * z21;
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, bool COMP, bool MAC>
+__global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
+                                                     T* __restrict__ boxes) {
+  constexpr int TS = 8;
+  using Gm = Geo<3, TS>;
+  constexpr int PLANES = COMP ? 2 : 1;
+  constexpr int NROWS = TS * TS;
+  static_assert((3 * PLANES * Gm::BV * sizeof(T)) % 16 == 0, "16-byte sections");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t rstart[NROWS];
+  __shared__ uint32_t rpre[NROWS + 1];
+  __shared__ Job sjob;
+  const int lane = threadIdx.x;
+  const long long gt = blockIdx.x;
+  // boxes of component a: sums at a * PLANES * BV, errors (compensated) at + BV;
+  // then kSpreadBatch + 1 records
+  T* box = reinterpret_cast<T*>(smem_raw);
+  T* rec_s = box + 3 * PLANES * Gm::BV;
+  {
+    const int j = __shfl_sync(0xffffffffu, lane == 0 ? job_of_tile(J, gt) : 0, 0);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&job_at(J, j));
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sjob);
+    for (int w = lane; w < (int)(sizeof(Job) / 4); w += 32) dst[w] = src[w];
+    __syncwarp();
+  }
+  const Job& jb = sjob;
+  if (jb.G == nullptr) return;
+  int T0[3], TE[3];
+  tile_coords<3, TS>(jb.ntile, jb.n, gt - jb.tile_base, T0, TE);
+  // Cell rows of the tile: counts requested first, boxes zeroed while they arrive.
+  const int rows = TE[1] * TE[2];
+  uint32_t st[NROWS / 32], cn[NROWS / 32];
+#pragma unroll
+  for (int k = 0; k < NROWS / 32; ++k) {
+    const int r = lane + 32 * k;
+    st[k] = cn[k] = 0;
+    if (r < rows) {
+      const int y = T0[1] + r % TE[1];
+      const int z = T0[2] + r / TE[1];
+      const long long cell = jb.cell_base + T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
+      st[k] = B.count[cell];
+      cn[k] = B.count[cell + TE[0]];
+    }
+  }
+  {
+    constexpr int NV = (int)(3 * PLANES * Gm::BV * sizeof(T) / 16);
+    uint4* zz = reinterpret_cast<uint4*>(box);
+    for (int i = lane; i < NV; i += 32) zz[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  uint32_t M = 0;
+#pragma unroll
+  for (int k = 0; k < NROWS / 32; ++k) {
+    const uint32_t cnt = cn[k] - st[k];
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    rstart[lane + 32 * k] = st[k];
+    rpre[lane + 32 * k] = M + inc - cnt;
+    M += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+
+  const T* Xg = (const T*)jb.X;
+  const T* Gp = (const T*)jb.G;
+  // sorted point q of the tile -> its global point index
+  auto point_of = [&](uint32_t q) -> uint32_t {
+    int lo = 0;
+#pragma unroll
+    for (int step = NROWS / 2; step >= 1; step >>= 1)
+      if (lo + step < rows && rpre[lo + step] <= q) lo += step;
+    return B.perm[rstart[lo] + (q - rpre[lo])];
+  };
+  auto fetch = [&](uint32_t g, T xs[3], T gs[3]) {
+    const long long li = (long long)g - jb.pt_base;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) xs[b] = Xg[li * 3 + b];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) gs[b] = Gp[li * 3 + b];
+  };
+  T xs[3], gs[3] = {(T)0, (T)0, (T)0};
+  uint32_t pn = 0;                                 // point index of batch b + 1 (this lane)
+  if (lane < M) fetch(point_of(lane), xs, gs);
+  if (kSpreadBatch + lane < M) pn = point_of(kSpreadBatch + lane);
+  for (uint32_t base = 0; base < M; base += kSpreadBatch) {
+    if (base + lane < M) tile3_record<T, MAC>(jb, sh, B, xs, gs, T0, TE, rec_s + lane * kRec3);
+    if (base + kSpreadBatch + lane < M) fetch(pn, xs, gs);
+    if (base + 2 * kSpreadBatch + lane < M) pn = point_of(base + 2 * kSpreadBatch + lane);
+    __syncwarp();
+    tile3_add<T, COMP>(box, rec_s, (int)min((uint32_t)kSpreadBatch, M - base), lane);
+    __syncwarp();
+  }
+  // Boxes -> scratch [tile][comp][plane][BV]: the shared layout, one contiguous copy.
+  constexpr int NV = (int)(3 * PLANES * Gm::BV * sizeof(T) / 16);
+  const uint4* src = reinterpret_cast<const uint4*>(box);
+  uint4* dst = reinterpret_cast<uint4*>(boxes + gt * (long long)(3 * PLANES * Gm::BV));
+  for (int i = lane; i < NV; i += 32) dst[i] = src[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -390,6 +641,10 @@ __device__ __forceinline__ Cover3 cover_fast(int x, int n, int ntile) {
   if (xl < 2 && t >= 1) c.push(t - 1, xl + TS + 2);
   c.push(t, xl + 2);
   if (xl >= TS - 2 && t + 1 < ntile) c.push(t + 1, xl - TS + 2);
+  // The copy x + n: the last tile's box, and the one before it when the last
+  // tile holds a single cell (its box then ends exactly at node n).
+  const int vp = x + n - (ntile - 2) * TS + 2;
+  if (vp < TS + 4) c.push(ntile - 2, vp);
   const int vo = x + n - (ntile - 1) * TS + 2;
   if (vo < TS + 4) c.push(ntile - 1, vo);
   return c;
@@ -518,6 +773,59 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
     for (int v = 0; v < V; ++v) S[a][v] = E[a][v] = (T)0;
   // Covering boxes in increasing (z, y, x) unwrapped order; every component
   // sums them in that same order.
+  if constexpr (!CP && sizeof(T) == 4) {
+    if (cx.n <= 2 && cy.n <= 2 && cz.n <= 2 && nc <= 3) {
+      // At most 2 boxes per dimension (every node but a few at the periodic
+      // seam): the up to 8 entries of every component are loaded before any
+      // addition, so the loads are in flight together; the sums keep the order.
+      const T* bp[8];
+      bool ok[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int iz = k >> 2, iy = (k >> 1) & 1, ix = k & 1;
+        ok[k] = iz < cz.n && iy < cy.n && ix < cx.n;
+        const int trow = (int)jb.tile_base + jb.ntile[0] * (cy.t(iy) + jb.ntile[1] * cz.t(iz));
+        const int orow = (cz.o(iz) * Gm::BY + cy.o(iy)) * Gm::BX;
+        bp[k] = ok[k] ? boxes + (long long)(trow + cx.t(ix)) * nc * plane + (orow + cx.o(ix)) : boxes;
+      }
+      T val[3][8][V];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (a < nc && ok[k]) load_v<T, V>(bp[k] + a * plane, val[a][k]);
+          else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) val[a][k][v] = (T)0;
+          }
+        }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (ok[k]) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) S[a][v] += val[a][k][v];
+          }
+      T* f = (T*)jb.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a >= nc) break;
+        T* o = f + a * jb.ncell + lc;
+        T out[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] = S[a][v];
+        if (accumulate) {
+          T old[V];
+          load_v<T, V>(o, old);
+#pragma unroll
+          for (int v = 0; v < V; ++v) out[v] = old[v] + out[v];
+        }
+        store_v<T, V>(o, out);
+      }
+      return;
+    }
+  }
 #pragma unroll
   for (int iz = 0; iz < 3; ++iz) {
     if (iz >= cz.n) break;
@@ -850,29 +1158,55 @@ __global__ void __launch_bounds__(kThreads) k_advect(const __grid_constant__ Job
 
 template <typename K>
 void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // Always set: dynamic plus static shared memory may pass 48 KB while the dynamic part alone does not.
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T, int D, int TS>
 size_t spread_smem(bool comp) {
   using Gm = Geo<D, TS>;
-  return ((comp ? 2 : 1) * (size_t)Gm::BV + 4 * (size_t)kBatch * rec_words(D)) * sizeof(T);
+  return (size_t)kSpreadWarps * ((comp ? 2 : 1) * (size_t)Gm::BV + (size_t)kSpreadBatch * WRec<D>::words) * sizeof(T);
+}
+
+template <typename T, int D, int TS, bool COMP>
+void launch_spread_warp(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long nunits, cudaStream_t s) {
+  const size_t bytes = spread_smem<T, D, TS>(COMP);
+  cudaFuncSetAttribute(k_spread_warp<T, D, TS, COMP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  allow_smem(k_spread_warp<T, D, TS, COMP>, bytes);
+  const unsigned grid = (unsigned)((nunits + kSpreadWarps - 1) / kSpreadWarps);
+  k_spread_warp<T, D, TS, COMP><<<grid, 32 * kSpreadWarps, bytes, s>>>(J, sh, B, (T*)boxes, nunits);
+}
+
+template <typename T, bool COMP, bool MAC>
+void launch_spread_tile3(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, cudaStream_t s) {
+  using Gm = Geo<3, 8>;
+  const size_t bytes = ((size_t)3 * (COMP ? 2 : 1) * Gm::BV + (size_t)(kSpreadBatch + 1) * kRec3) * sizeof(T);
+  cudaFuncSetAttribute(k_spread_tile3<T, COMP, MAC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  allow_smem(k_spread_tile3<T, COMP, MAC>, bytes);
+  k_spread_tile3<T, COMP, MAC><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes);
 }
 
 template <typename T, int D, int TS>
 cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool comp,
                         bool accumulate, bool pairs, cudaStream_t s) {
   if (ntiles > 0) {
-    const size_t bytes = spread_smem<T, D, TS>(comp);
-    const unsigned grid = (unsigned)(ntiles * sh.ncomp);
-    if (comp) {
-      cudaFuncSetAttribute(k_spread_box<T, D, TS, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      allow_smem(k_spread_box<T, D, TS, true>, bytes);
-      k_spread_box<T, D, TS, true><<<grid, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
-    } else {
-      cudaFuncSetAttribute(k_spread_box<T, D, TS, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      allow_smem(k_spread_box<T, D, TS, false>, bytes);
-      k_spread_box<T, D, TS, false><<<grid, kBoxThreads, bytes, s>>>(J, sh, B, (T*)boxes);
+    bool done = false;
+    if constexpr (D == 3 && TS == 8) {
+      if (sh.ncomp == 3) {   // three components: one warp per tile for all of them
+        if (sh.mac) {
+          if (comp) launch_spread_tile3<T, true, true>(J, sh, B, boxes, ntiles, s);
+          else launch_spread_tile3<T, false, true>(J, sh, B, boxes, ntiles, s);
+        } else {
+          if (comp) launch_spread_tile3<T, true, false>(J, sh, B, boxes, ntiles, s);
+          else launch_spread_tile3<T, false, false>(J, sh, B, boxes, ntiles, s);
+        }
+        done = true;
+      }
+    }
+    if (!done) {
+      const long long nunits = ntiles * sh.ncomp;
+      if (comp) launch_spread_warp<T, D, TS, true>(J, sh, B, boxes, nunits, s);
+      else launch_spread_warp<T, D, TS, false>(J, sh, B, boxes, nunits, s);
     }
   }
   if (B.ncell_total > 0) {
@@ -896,9 +1230,9 @@ int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp) {
   (void)elem_bytes;
   (void)comp;
   (void)ncomp;
-  // One CTA per (tile, component): a 20^3 box of one component (two planes
-  // when compensated, FP64 at most 128 KB) and the staging records always fit.
-  return dim == 2 ? 32 : 16;
+  // One warp per tile: 12^3 boxes in 3-D, 36^2 in 2-D (two planes when
+  // compensated), plus the staging records.
+  return dim == 2 ? 32 : 8;
 }
 
 size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp) {
@@ -911,11 +1245,10 @@ cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* b
   const bool p = even_n0;
   if (dtype == 0) {
     if (sh.dim == 2) return spread_impl<float, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
-    if (tile == 16) return spread_impl<float, 3, 16>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
     return spread_impl<float, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
   }
   if (sh.dim == 2) return spread_impl<double, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
-  if (tile == 16) return spread_impl<double, 3, 16>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+  (void)tile;
   return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
 }
 

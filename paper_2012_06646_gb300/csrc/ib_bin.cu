@@ -5,7 +5,8 @@
 //   1. k_bin_count   per point: exact cell of xi = 0, key = c_x + n0 (c_y + n1 c_z)
 //                    (plus the job's cell base), atomic per-cell count; the
 //                    value returned by the atomic is the point's arrival rank.
-//   2. scan          exclusive prefix of the counts -> cell_start.
+//   2. scan          exclusive prefix of the counts -> cell_start (chunk
+//                    totals, then each chunk adds the totals before it).
 //   3. k_bin_scatter perm_tmp[cell_start[key] + rank] = (point, key) (any order
 //                    in a cell).
 //   4. k_bin_stable  per sorted position: perm[cell_start[key] + #(same-cell
@@ -132,15 +133,49 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t* __restrict
   if (threadIdx.x == 0) sums[nb] = carry;
 }
 
+// Exclusive offsets of the chunks.  With `direct` the block sums are still raw
+// chunk totals (k_scan_sums skipped, nb <= kDirectBlocks): each block adds up
+// the totals of the chunks before it itself.
+constexpr long long kDirectBlocks = 4 * kScanThreads;
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t v) {
+  __shared__ uint32_t part[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  uint32_t t = (lane < kScanThreads / 32) ? part[lane] : 0u;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __syncthreads();
+  return t;
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restrict__ a, long long m,
-                                                              const uint32_t* __restrict__ sums, long long nb) {
+                                                              const uint32_t* __restrict__ sums, long long nb,
+                                                              int direct) {
   const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
   uint32_t v[kScanItems], s = 0;
   load8(a, base, m, v);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) s += v[i];
+  uint32_t before;
+  if (direct) {
+    uint32_t p = 0;
+    for (long long j = threadIdx.x; j < blockIdx.x; j += kScanThreads) p += sums[j];
+    before = block_sum(p);
+    if (blockIdx.x == gridDim.x - 1) {
+      uint32_t q = 0;
+      for (long long j = threadIdx.x; j < nb; j += kScanThreads) q += sums[j];
+      q = block_sum(q);
+      if (threadIdx.x == 0) a[m] = q;
+    }
+  } else {
+    before = sums[blockIdx.x];
+  }
   uint32_t tot;
-  uint32_t off = sums[blockIdx.x] + block_exclusive(s, &tot);
+  uint32_t off = before + block_exclusive(s, &tot);
   uint32_t o[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
@@ -155,7 +190,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restric
     for (int i = 0; i < kScanItems; ++i)
       if (base + i < m) a[base + i] = o[i];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) a[m] = sums[nb];
+  if (!direct && blockIdx.x == 0 && threadIdx.x == 0) a[m] = sums[nb];
 }
 
 __global__ void __launch_bounds__(kThreads) k_bin_scatter(const Bins B) {
@@ -205,8 +240,9 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
   const long long m = B.ncell_total + 1;  // cells plus the sentinel; count[m] receives the total
   const long long nb = scan_blocks(m);
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.block_sums);
-  k_scan_sums<<<1, kScanThreads, 0, s>>>(B.block_sums, nb);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.block_sums, nb);
+  const int direct = nb <= kDirectBlocks ? 1 : 0;
+  if (!direct) k_scan_sums<<<1, kScanThreads, 0, s>>>(B.block_sums, nb);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.block_sums, nb, direct);
   if (n > 0) {
     k_bin_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);
     k_bin_stable<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);

@@ -1139,21 +1139,60 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad(const __grid_constant__ J
 // ---------------------------------------------------------------------------
 // Position update X <- X + dt U, wrapped into [0, L) (steps b and g of Section 2).
 // ---------------------------------------------------------------------------
+// Each thread moves P = 16 / sizeof(T) consecutive points (D P elements, a
+// whole number of 16-byte vectors) with vector loads and stores when X, U and
+// Xout are 16-byte aligned; the last partial group and unaligned arrays take
+// the scalar path.
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_advect(const __grid_constant__ Jobs J, const T* __restrict__ U, T dt,
-                                                     T* __restrict__ Xout) {
-  const long long e = (long long)blockIdx.x * kThreads + threadIdx.x;
-  const Job jb = J.one;
-  if (e >= jb.npts * D) return;
-  const int b = (int)(e % D);
-  const T L = (T)jb.Ld[b];
-  T x = ((const T*)jb.X)[e] + dt * U[e];
-  if (x >= L || x < (T)0) {
-    x -= L * floor(x / L);
-    if (x >= L) x -= L;
-    if (x < (T)0) x += L;
+                                                     T* __restrict__ Xout, int vec) {
+  constexpr int P = 16 / (int)sizeof(T);
+  constexpr int NE = P * D;
+  constexpr int NV = NE * (int)sizeof(T) / 16;
+  const long long n = J.one.npts;
+  const long long p0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * P;
+  if (p0 >= n) return;
+  const T* X = (const T*)J.one.X;
+  T L[D];
+#pragma unroll
+  for (int b = 0; b < D; ++b) L[b] = (T)J.one.Ld[b];
+  const long long e0 = p0 * D;
+  const bool full = vec && p0 + P <= n;
+  const int ne = full ? NE : (int)((n - p0) * D);
+  T xv[NE], uv[NE];
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      reinterpret_cast<uint4*>(xv)[k] = reinterpret_cast<const uint4*>(X + e0)[k];
+      reinterpret_cast<uint4*>(uv)[k] = reinterpret_cast<const uint4*>(U + e0)[k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NE; ++k)
+      if (k < ne) {
+        xv[k] = X[e0 + k];
+        uv[k] = U[e0 + k];
+      }
   }
-  Xout[e] = x;
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    const T Lb = L[k % D];
+    T x = xv[k] + dt * uv[k];
+    if (x >= Lb || x < (T)0) {
+      x -= Lb * floor(x / Lb);
+      if (x >= Lb) x -= Lb;
+      if (x < (T)0) x += Lb;
+    }
+    xv[k] = x;
+  }
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) reinterpret_cast<uint4*>(Xout + e0)[k] = reinterpret_cast<const uint4*>(xv)[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < NE; ++k)
+      if (k < ne) Xout[e0 + k] = xv[k];
+  }
 }
 
 template <typename K>
@@ -1298,15 +1337,17 @@ cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int d
 
 cudaError_t launch_advect(const Jobs& J, const Shape& sh, int dtype, const void* U, double dt, void* Xout,
                           cudaStream_t s) {
-  const long long n = J.one.npts * sh.dim;
+  const long long n = J.one.npts;
   if (n == 0) return cudaSuccess;
-  const unsigned grid = grid_for(n, kThreads);
+  const int vec = ((((uintptr_t)J.one.X) | ((uintptr_t)U) | ((uintptr_t)Xout)) % 16 == 0) ? 1 : 0;
   if (dtype == 0) {
-    if (sh.dim == 3) k_advect<float, 3><<<grid, kThreads, 0, s>>>(J, (const float*)U, (float)dt, (float*)Xout);
-    else k_advect<float, 2><<<grid, kThreads, 0, s>>>(J, (const float*)U, (float)dt, (float*)Xout);
+    const unsigned grid = grid_for((n + 3) / 4, kThreads);
+    if (sh.dim == 3) k_advect<float, 3><<<grid, kThreads, 0, s>>>(J, (const float*)U, (float)dt, (float*)Xout, vec);
+    else k_advect<float, 2><<<grid, kThreads, 0, s>>>(J, (const float*)U, (float)dt, (float*)Xout, vec);
   } else {
-    if (sh.dim == 3) k_advect<double, 3><<<grid, kThreads, 0, s>>>(J, (const double*)U, dt, (double*)Xout);
-    else k_advect<double, 2><<<grid, kThreads, 0, s>>>(J, (const double*)U, dt, (double*)Xout);
+    const unsigned grid = grid_for((n + 1) / 2, kThreads);
+    if (sh.dim == 3) k_advect<double, 3><<<grid, kThreads, 0, s>>>(J, (const double*)U, dt, (double*)Xout, vec);
+    else k_advect<double, 2><<<grid, kThreads, 0, s>>>(J, (const double*)U, dt, (double*)Xout, vec);
   }
   return cudaGetLastError();
 }

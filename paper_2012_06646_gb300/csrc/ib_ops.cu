@@ -897,7 +897,9 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
 // order) and sums its 4^d support from shared memory.  Points outside every
 // tile (invalid positions) are handled by k_interp_invalid.
 // ---------------------------------------------------------------------------
-constexpr int kInterpThreads = 256;
+constexpr int kInterpThreads = 128;   // 64 registers per thread: 8 tiles per SM
+constexpr int kInterpWarps = kInterpThreads / 32;
+static_assert(kInterpThreads >= 64, "a tile has up to 64 cell rows (3-D) or 32 (2-D), one per thread");
 
 template <typename T, int D, int TS>
 __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_constant__ Jobs J, const Shape sh,
@@ -905,9 +907,9 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   using Gm = Geo<D, TS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* box = reinterpret_cast<T*>(smem_raw);
-  __shared__ uint32_t rstart[256];
-  __shared__ uint32_t rpre[257];
-  __shared__ uint32_t wsum[8];
+  __shared__ uint32_t rstart[kInterpThreads];
+  __shared__ uint32_t rpre[kInterpThreads + 1];
+  __shared__ uint32_t wsum[kInterpWarps];
   __shared__ Job sjob;                  // one copy of the job per CTA (broadcast reads)
   const long long gt = blockIdx.x;
   if (threadIdx.x == 0) sjob = job_at(J, job_of_itile(J, gt));
@@ -920,9 +922,8 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   const int tid = threadIdx.x;
 
   // Grid values of the box: nodes T0 - 2 .. T0 + TS + 1 (unwrapped), all components,
-  // fetched with cp.async.  Wrapped row offsets come from two small tables; each
-  // thread keeps one x position (BXP, the row length rounded up to a power of
-  // two, divides the block size), so an element costs a few integer operations.
+  // fetched with cp.async, two entries per copy when n0 is even.  Wrapped row
+  // offsets come from two small tables.
   {
     constexpr int BXP = (Gm::BX <= 16) ? 16 : 64;
     constexpr int RSTEP = kInterpThreads / BXP;         // rows per block iteration
@@ -934,15 +935,33 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     __syncthreads();
     const T* u = (const T*)jb.u;
     const int nrows_box = nc * Gm::BZ * Gm::BY;
-    for (int bx0 = tid % BXP; bx0 < Gm::BX; bx0 += BXP) {
-      const int xw = wrapn(T0[0] - 2 + bx0, n0);
-      for (int row = tid / BXP; row < nrows_box; row += RSTEP) {
+    if ((n0 % 2) == 0 && ((uintptr_t)u % (2 * sizeof(T))) == 0) {
+      // Even n0 and an aligned grid: x pairs starting at an even node never
+      // straddle the periodic seam, so every row is fetched as BX/2 copies of
+      // two entries (T0 - 2 is even).
+      constexpr int NP = Gm::BX / 2;
+      for (int i = tid; i < nrows_box * NP; i += kInterpThreads) {
+        const int row = i / NP;
+        const int c = i - row * NP;
         const int a = row / (Gm::BZ * Gm::BY);
         const int rem = row - a * (Gm::BZ * Gm::BY);
         const int bz = rem / Gm::BY;
         const int by = rem - bz * Gm::BY;
+        const int xw = wrapn(T0[0] - 2 + 2 * c, n0);
         const T* src = u + (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
-        __pipeline_memcpy_async(box + row * Gm::BX + bx0, src, sizeof(T));
+        __pipeline_memcpy_async(box + row * Gm::BX + 2 * c, src, 2 * sizeof(T));
+      }
+    } else {
+      for (int bx0 = tid % BXP; bx0 < Gm::BX; bx0 += BXP) {
+        const int xw = wrapn(T0[0] - 2 + bx0, n0);
+        for (int row = tid / BXP; row < nrows_box; row += RSTEP) {
+          const int a = row / (Gm::BZ * Gm::BY);
+          const int rem = row - a * (Gm::BZ * Gm::BY);
+          const int bz = rem / Gm::BY;
+          const int by = rem - bz * Gm::BY;
+          const T* src = u + (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
+          __pipeline_memcpy_async(box + row * Gm::BX + bx0, src, sizeof(T));
+        }
       }
     }
     __pipeline_commit();
@@ -969,24 +988,24 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     if (lane == 31) wsum[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-      uint32_t t = (lane < 8) ? wsum[lane] : 0u;
+      uint32_t t = (lane < kInterpWarps) ? wsum[lane] : 0u;
 #pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
+      for (int o = 1; o < kInterpWarps; o <<= 1) {
         const uint32_t yv = __shfl_up_sync(0xffffffffu, t, o);
         if (lane >= o) t += yv;
       }
-      if (lane < 8) wsum[lane] = t;
+      if (lane < kInterpWarps) wsum[lane] = t;
     }
     __syncthreads();
     const uint32_t before = (warp > 0) ? wsum[warp - 1] : 0u;
     rstart[tid] = st;
     rpre[tid] = before + inc - cnt;
-    if (tid == 0) rpre[256] = wsum[7];
+    if (tid == 0) rpre[kInterpThreads] = wsum[kInterpWarps - 1];
   }
   __pipeline_wait_prior(0);
   __syncthreads();
 
-  const uint32_t P = rpre[256];
+  const uint32_t P = rpre[kInterpThreads];
   for (uint32_t q = tid; q < P; q += kInterpThreads) {
     int lo = 0, hi = nrows - 1;
     while (lo < hi) {

@@ -27,12 +27,9 @@ constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 static_assert(kScanChunk == kScanChunkCells, "scan chunk size shared with the scratch layout");
 
+// Key of one point (ncell_total for an invalid position, reported in B.err).
 template <typename T, int D>
-__global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B) {
-  const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (g >= B.npts_total) return;
-  const Job jb = job_at(J, job_of_point(J, g));
-  const T* X = (const T*)jb.X + (g - jb.pt_base) * D;
+__device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, const T* X) {
   uint32_t err = 0;
   long long key = 0, stride = 1;
 #pragma unroll
@@ -44,13 +41,59 @@ __global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ 
     key += (long long)cb * stride;
     stride *= n;
   }
-  uint32_t k;
   if (err) {
     atomicOr(B.err, err);
-    k = (uint32_t)B.ncell_total;
-  } else {
-    k = (uint32_t)(jb.cell_base + key);
+    return (uint32_t)B.ncell_total;
   }
+  return (uint32_t)(jb.cell_base + key);
+}
+
+// Four consecutive points per thread (single job, 16-byte aligned X, FP32):
+// three vector loads of positions, four independent counting atomics in
+// flight, vector stores of keys and ranks.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__ Jobs J, const Bins B) {
+  const long long g0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * 4;
+  const long long n = B.npts_total;
+  if (g0 >= n) return;
+  const Job& jb = J.one;
+  const float* X = (const float*)jb.X + g0 * D;
+  float x[4 * D];
+  const bool full = g0 + 4 <= n;
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) reinterpret_cast<float4*>(x)[k] = reinterpret_cast<const float4*>(X)[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4 * D; ++k)
+      if (g0 * D + k < n * D) x[k] = X[k];
+  }
+  uint32_t key[4], rank[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (full || g0 + i < n) key[i] = point_key<float, D>(jb, B, x + i * D);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (full || g0 + i < n) rank[i] = atomicAdd(&B.count[key[i]], 1u);
+  if (full) {
+    *reinterpret_cast<uint4*>(B.key + g0) = make_uint4(key[0], key[1], key[2], key[3]);
+    *reinterpret_cast<uint4*>(B.rank + g0) = make_uint4(rank[0], rank[1], rank[2], rank[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (g0 + i < n) {
+        B.key[g0 + i] = key[i];
+        B.rank[g0 + i] = rank[i];
+      }
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B) {
+  const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (g >= B.npts_total) return;
+  const Job& jb = job_at(J, job_of_point(J, g));
+  const uint32_t k = point_key<T, D>(jb, B, (const T*)jb.X + (g - jb.pt_base) * D);
   B.key[g] = k;
   B.rank[g] = atomicAdd(&B.count[k], 1u);
 }
@@ -229,7 +272,12 @@ long long scan_blocks(long long m) { return (m + kScanChunk - 1) / kScanChunk; }
 cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s) {
   const long long n = B.npts_total;
   if (n > 0) {
-    if (dtype == 0) {
+    // key and rank are 256-byte aligned sections of the arena
+    const bool vec = !J.table && ((uintptr_t)J.one.X % 16) == 0;
+    if (dtype == 0 && vec) {
+      if (sh.dim == 3) k_bin_count4<3><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B);
+      else k_bin_count4<2><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B);
+    } else if (dtype == 0) {
       if (sh.dim == 3) k_bin_count<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
       else k_bin_count<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
     } else {

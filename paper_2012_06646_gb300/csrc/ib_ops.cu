@@ -1006,17 +1006,39 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   __syncthreads();
 
   const uint32_t P = rpre[kInterpThreads];
-  for (uint32_t q = tid; q < P; q += kInterpThreads) {
+  // Sorted point q of the tile -> global point index.
+  auto point_of = [&](uint32_t q) -> uint32_t {
     int lo = 0, hi = nrows - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (rpre[mid] <= q) lo = mid; else hi = mid - 1;
     }
-    const uint32_t g = B.perm[rstart[lo] + (q - rpre[lo])];
+    return B.perm[rstart[lo] + (q - rpre[lo])];
+  };
+  const T* Xg = (const T*)jb.X;
+  // Software pipeline over this thread's points: the next point's index is
+  // requested at the top of an iteration and its coordinates after this
+  // point's weights, so neither load is waited for on the critical path.
+  uint32_t g = 0;
+  T xs[D];
+  if (tid < P) {
+    g = point_of(tid);
+#pragma unroll
+    for (int b = 0; b < D; ++b) xs[b] = Xg[((long long)g - jb.pt_base) * D + b];
+  }
+  for (uint32_t q = tid; q < P; q += kInterpThreads) {
+    const bool more = q + kInterpThreads < P;
+    const uint32_t gn = more ? point_of(q + kInterpThreads) : 0u;
     const long long li = (long long)g - jb.pt_base;
     PointBox<T, D> Pb;
     T* U = (T*)jb.U + li * nc;
-    if (!point_box<T, D>(jb, sh, (const T*)jb.X + li * D, T0, TE, Pb)) {
+    const bool ok = point_box<T, D>(jb, sh, xs, T0, TE, Pb);
+    if (more) {
+#pragma unroll
+      for (int b = 0; b < D; ++b) xs[b] = Xg[((long long)gn - jb.pt_base) * D + b];
+    }
+    g = gn;
+    if (!ok) {
       atomicOr(B.err, ERR_STALE);        // X changed after binning: no gather outside the box
       for (int a = 0; a < nc; ++a) U[a] = (T)NAN;
       continue;

@@ -453,8 +453,8 @@ def run_ours(args):
         except Exception as exc:
             serving = {"error": repr(exc)}
 
-    launches_per_step = 6 + 2 + 2 + 1     # bin: count, 3 scan, scatter, stable; spread: box, combine;
-    #                                        interp: tiles, invalid points; advect
+    launches_per_step = 5 + 2 + 1 + 1     # bin: count, 2 scan, scatter, stable; spread: tile boxes, combine;
+    #                                        interp: tiles (+ invalid points); advect
     line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -895,7 +895,7 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
 // tile plus a 2-node apron (every component) into shared memory with
 // asynchronous copies, then each thread takes one of the tile's points (cell
 // order) and sums its 4^d support from shared memory.  Points outside every
-// tile (invalid positions) are handled by k_interp_invalid.
+// tile (invalid positions) are handled by one extra block of the same launch.
 // ---------------------------------------------------------------------------
 constexpr int kInterpThreads = 128;   // 64 registers per thread: 8 tiles per SM
 constexpr int kInterpWarps = kInterpThreads / 32;
@@ -912,6 +912,18 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   __shared__ uint32_t wsum[kInterpWarps];
   __shared__ Job sjob;                  // one copy of the job per CTA (broadcast reads)
   const long long gt = blockIdx.x;
+  if (gt == gridDim.x - 1) {
+    // The last block: points with an invalid position, which sit after every
+    // valid point in the bins, get U = NaN (no point of a valid input).
+    for (long long p = B.count[B.ncell_total] + threadIdx.x; p < B.npts_total; p += kInterpThreads) {
+      const uint32_t g = B.perm[p];
+      const Job& jp = job_at(J, job_of_point(J, (long long)g));
+      if (jp.u == nullptr) continue;
+      T* U = (T*)jp.U + ((long long)g - jp.pt_base) * sh.ncomp;
+      for (int a = 0; a < sh.ncomp; ++a) U[a] = (T)NAN;
+    }
+    return;
+  }
   if (threadIdx.x == 0) sjob = job_at(J, job_of_itile(J, gt));
   __syncthreads();
   const Job& jb = sjob;
@@ -1075,20 +1087,6 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
       U[a] = acc * scale;
     }
   }
-}
-
-// Points with an invalid position (after every valid point in the bins): U = NaN.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_interp_invalid(const __grid_constant__ Jobs J, const Shape sh,
-                                                             const Bins B) {
-  const long long first = B.count[B.ncell_total];
-  const long long p = first + (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (p >= B.npts_total) return;
-  const uint32_t g = B.perm[p];
-  const Job jb = job_at(J, job_of_point(J, (long long)g));
-  if (jb.u == nullptr) return;
-  T* U = (T*)jb.U + ((long long)g - jb.pt_base) * sh.ncomp;
-  for (int a = 0; a < sh.ncomp; ++a) U[a] = (T)NAN;
 }
 
 // ---------------------------------------------------------------------------
@@ -1336,14 +1334,12 @@ template <typename T, int D, int TS>
 cudaError_t interp_impl(const Jobs& J, const Shape& sh, const Bins& B, long long ntiles, double scale,
                         cudaStream_t s) {
   using Gm = Geo<D, TS>;
-  if (ntiles > 0) {
+  // One block per tile, plus one for the points with invalid positions.
+  if (ntiles > 0 || B.npts_total > 0) {
     const size_t bytes = (size_t)sh.ncomp * Gm::BV * sizeof(T);
     allow_smem(k_interp_tile<T, D, TS>, bytes);
-    k_interp_tile<T, D, TS><<<(unsigned)ntiles, kInterpThreads, bytes, s>>>(J, sh, B, (T)scale);
+    k_interp_tile<T, D, TS><<<(unsigned)(ntiles + 1), kInterpThreads, bytes, s>>>(J, sh, B, (T)scale);
   }
-  // Invalid points sit after every valid one in the bins; at most npts of them.
-  if (B.npts_total > 0)
-    k_interp_invalid<T><<<grid_for(B.npts_total, kThreads), kThreads, 0, s>>>(J, sh, B);
   return cudaGetLastError();
 }
 

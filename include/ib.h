@@ -151,6 +151,35 @@ ib_status ib_advect(ib_plan plan, long long npts, const void* X, const void* U, 
  * if the stream reports an error). */
 ib_status ib_plan_check(ib_plan plan, void* stream);
 
+/* The paper's own parallel spreading algorithms, kept as comparators of
+ * ib_spread on the same data (f = S G, overwrite; the same result up to the
+ * order of the FP sums):
+ *   IB_PAPER_ALG4  Algorithm 4 ("par-spread"): per component, key each point
+ *                  by the cell it inhabits in that component's staggering,
+ *                  sort once, then for each of the s^d shifts in turn reduce
+ *                  the values of each inhabited cell (segmented reduce) and
+ *                  add them to the nodes cell + shift, one launch per shift;
+ *   IB_PAPER_ALG5  Algorithm 5 ("pa-par-spread"): beta shifts per pass, the
+ *                  reduced value of shift k of a pass added into buffer k of
+ *                  `buffer` (caller-owned device memory of beta * n0 n1 n2
+ *                  entries of the plan's dtype, overwritten), then f = sum of
+ *                  the beta buffers;
+ *   IB_PAPER_ALG6  Algorithm 6 ("otf-par-spread"): Algorithm 5 with the
+ *                  buffer allocated and freed by the call, stream-ordered
+ *                  (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * beta: 1 <= beta <= s^d (16 in 2-D, 64 in 3-D) for Algorithms 5 and 6,
+ * ignored by Algorithm 4; `buffer` is read only by Algorithm 5.  X (npts,
+ * dim), G (npts, ncomp) read; f [ncomp][grid] written.  The call re-bins X
+ * once per component staggering, so a later call needs fresh bins (it cannot
+ * pass IB_REUSE_BINS).  Errors: IB_ERR_INVALID_ARG (unknown algorithm, beta
+ * out of range, missing buffer), IB_ERR_CAPACITY, IB_ERR_OOM (Algorithm 6
+ * allocation), IB_ERR_CUDA. */
+#define IB_PAPER_ALG4 4
+#define IB_PAPER_ALG5 5
+#define IB_PAPER_ALG6 6
+ib_status ib_spread_paper(ib_plan plan, long long npts, const void* X, const void* G, void* f, int algorithm,
+                          int beta, void* buffer, void* stream);
+
 /* Device pointers to the bins of the last ib_bin on this plan (for
  * inspection and tests): perm[p] = index of the p-th point in cell order
  * (uint32, npts entries), cell_start[c] = first sorted position of cell c

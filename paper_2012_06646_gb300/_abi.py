@@ -40,6 +40,10 @@ IB_ADJOINT = 0x8
 
 IB_BATCH_HOST_IO = 0x1
 
+IB_PAPER_ALG4 = 4
+IB_PAPER_ALG5 = 5
+IB_PAPER_ALG6 = 6
+
 IB_NOALLOC_MAX_CELLS = 1 << 21
 IB_NOALLOC_MAX_POINTS = 1 << 20
 
@@ -84,6 +88,7 @@ SIGNATURES = {
     "ib_advect": (_st, [_vp, _ll, _vp, _vp, ctypes.c_double, _vp, _vp]),
     "ib_plan_check": (_st, [_vp, _vp]),
     "ib_plan_bins": (_st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    "ib_spread_paper": (_st, [_vp, _ll, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "ib_batch_footprint": (_st, [ctypes.POINTER(ib_batch_desc), ctypes.POINTER(ctypes.c_size_t)]),
     "ib_batch_job_footprint": (_st, [ctypes.POINTER(ib_batch_desc), ctypes.POINTER(ib_job),
                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_ll)]),

@@ -417,6 +417,69 @@ ib_status ib_advect(ib_plan p, long long npts, const void* X, const void* U, dou
   return IB_OK;
 }
 
+ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* G, void* f, int algorithm, int beta,
+                          void* buffer, void* stream) {
+  ib_status st = check_call(p, npts, X);
+  if (st != IB_OK) return st;
+  if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
+  const int S = p->desc.dim == 3 ? 64 : 16;        // s^d shifts of the 4-point support
+  if (algorithm == IB_PAPER_ALG4) {
+    beta = 1;
+  } else if (algorithm == IB_PAPER_ALG5 || algorithm == IB_PAPER_ALG6) {
+    if (beta < 1 || beta > S) return IB_ERR_INVALID_ARG;
+    if (algorithm == IB_PAPER_ALG5 && !buffer) return IB_ERR_INVALID_ARG;
+  } else {
+    return IB_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int dtype = p->desc.dtype;
+  const size_t eb = dtype == IB_F64 ? 8 : 4;
+  const long long ncell = p->job.ncell;
+  const size_t buf_bytes = (size_t)beta * (size_t)ncell * eb;
+  void* buf = buffer;
+  if (algorithm == IB_PAPER_ALG6 && cudaMallocAsync(&buf, buf_bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return IB_ERR_OOM;
+  }
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.one.G = G ? G : f;  // npts == 0: any non-null marker; no point is read
+  J.one.f = f;
+  J.njobs = 1;
+  const Bins B = call_bins(p, npts);
+  p->binned = false;    // the bins are keyed by a component's cells from here on
+  ib_status out = IB_OK;
+  for (int a = 0; a < p->desc.ncomp && out == IB_OK; ++a) {
+    // Keys: cells in component a's staggering (one staggering for every
+    // component on the cell-centred grid: one sort).
+    if (a == 0 || p->sh.mac) {
+      if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(ncell + 2), s) != cudaSuccess ||
+          launch_bin(J, p->sh, B, dtype, s, a) != cudaSuccess) {
+        out = IB_ERR_CUDA;
+        break;
+      }
+    }
+    char* fa = (char*)f + (size_t)a * (size_t)ncell * eb;
+    if (algorithm == IB_PAPER_ALG4) {
+      if (cudaMemsetAsync(fa, 0, (size_t)ncell * eb, s) != cudaSuccess) out = IB_ERR_CUDA;
+      for (int j = 0; j < S && out == IB_OK; ++j)   // one shift per launch: the synchronisation per shift
+        if (launch_paper_shifts(J, p->sh, B, dtype, a, j, 1, fa, 0, s) != cudaSuccess) out = IB_ERR_CUDA;
+    } else {
+      if (cudaMemsetAsync(buf, 0, buf_bytes, s) != cudaSuccess) out = IB_ERR_CUDA;
+      for (int j0 = 0; j0 < S && out == IB_OK; j0 += beta)
+        if (launch_paper_shifts(J, p->sh, B, dtype, a, j0, beta < S - j0 ? beta : S - j0, buf, ncell, s) !=
+            cudaSuccess)
+          out = IB_ERR_CUDA;
+      if (out == IB_OK && launch_paper_sum(J, dtype, a, beta, buf, s) != cudaSuccess) out = IB_ERR_CUDA;
+    }
+  }
+  if (algorithm == IB_PAPER_ALG6 && cudaFreeAsync(buf, s) != cudaSuccess && out == IB_OK) out = IB_ERR_CUDA;
+  return out;
+}
+
 ib_status ib_plan_check(ib_plan p, void* stream) {
   if (!p) return IB_ERR_INVALID_ARG;
   return check_error_word(p->bins.err, (cudaStream_t)stream);

@@ -27,9 +27,12 @@ constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 static_assert(kScanChunk == kScanChunkCells, "scan chunk size shared with the scratch layout");
 
-// Key of one point (ncell_total for an invalid position, reported in B.err).
+// Key of one point (ncell_total for an invalid position, reported in B.err):
+// its cell of xi = 0, or with key_comp >= 0 its cell in the staggering of
+// component key_comp.
 template <typename T, int D>
-__device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, const T* X) {
+__device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, const T* X, const Shape& sh,
+                                              int key_comp) {
   uint32_t err = 0;
   long long key = 0, stride = 1;
 #pragma unroll
@@ -37,7 +40,8 @@ __device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, cons
     Cell1<T> c;
     err |= point_cell<T>(X[b], jb, b, c);
     const int n = jb.n[b];
-    const int cb = ((unsigned)c.i0 < (unsigned)n) ? c.i0 : modn(c.i0, n);
+    const int ib = (key_comp >= 0 && half_stag(sh, key_comp, b)) ? c.i1 : c.i0;
+    const int cb = ((unsigned)ib < (unsigned)n) ? ib : modn(ib, n);
     key += (long long)cb * stride;
     stride *= n;
   }
@@ -52,7 +56,8 @@ __device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, cons
 // three vector loads of positions, four independent counting atomics in
 // flight, vector stores of keys and ranks.
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__ Jobs J, const Bins B) {
+__global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__ Jobs J, const Bins B, const Shape sh,
+                                                         int key_comp) {
   const long long g0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * 4;
   const long long n = B.npts_total;
   if (g0 >= n) return;
@@ -71,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__
   uint32_t key[4], rank[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
-    if (full || g0 + i < n) key[i] = point_key<float, D>(jb, B, x + i * D);
+    if (full || g0 + i < n) key[i] = point_key<float, D>(jb, B, x + i * D, sh, key_comp);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
     if (full || g0 + i < n) rank[i] = atomicAdd(&B.count[key[i]], 1u);
@@ -89,11 +94,12 @@ __global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B) {
+__global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B, const Shape sh,
+                                                        int key_comp) {
   const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (g >= B.npts_total) return;
   const Job& jb = job_at(J, job_of_point(J, g));
-  const uint32_t k = point_key<T, D>(jb, B, (const T*)jb.X + (g - jb.pt_base) * D);
+  const uint32_t k = point_key<T, D>(jb, B, (const T*)jb.X + (g - jb.pt_base) * D, sh, key_comp);
   B.key[g] = k;
   B.rank[g] = atomicAdd(&B.count[k], 1u);
 }
@@ -269,20 +275,20 @@ inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + thre
 
 long long scan_blocks(long long m) { return (m + kScanChunk - 1) / kScanChunk; }
 
-cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s) {
+cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s, int key_comp) {
   const long long n = B.npts_total;
   if (n > 0) {
     // key and rank are 256-byte aligned sections of the arena
     const bool vec = !J.table && ((uintptr_t)J.one.X % 16) == 0;
     if (dtype == 0 && vec) {
-      if (sh.dim == 3) k_bin_count4<3><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B);
-      else k_bin_count4<2><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B);
+      if (sh.dim == 3) k_bin_count4<3><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
+      else k_bin_count4<2><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
     } else if (dtype == 0) {
-      if (sh.dim == 3) k_bin_count<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
-      else k_bin_count<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
+      if (sh.dim == 3) k_bin_count<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
+      else k_bin_count<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
     } else {
-      if (sh.dim == 3) k_bin_count<double, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
-      else k_bin_count<double, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B);
+      if (sh.dim == 3) k_bin_count<double, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
+      else k_bin_count<double, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
     }
   }
   const long long m = B.ncell_total + 1;  // cells plus the sentinel; count[m] receives the total

@@ -20,8 +20,23 @@ constexpr long long kScanChunkCells = 8192;
 long long scan_blocks(long long m);
 
 // Binning (Algorithm 4 keys, sort and unique-key offsets): count, scan,
-// scatter and stable fix-up.  B.count must be zeroed by the caller.
-cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s);
+// scatter and stable fix-up.  B.count must be zeroed by the caller.  Keys are
+// cells of xi = 0, or with key_comp >= 0 cells in the staggering of that
+// component (the per-component keys of the paper's spreading algorithms).
+cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s, int key_comp = -1);
+
+// The paper's parallel spreading (Algorithm 4: one segmented reduce per
+// shift; Algorithms 5 and 6: beta shifts per pass into beta grid buffers) for
+// component a of a single job, on bins keyed by that component's cells:
+// shifts j0 .. j0 + nshift - 1 (colexicographic digits, x fastest); the
+// reduced value of shift j0 + k is added to out[k * out_stride + node] (out is
+// the component's grid, or a buffer of grids).  Distinct shifts of one launch
+// must go to distinct grids (out_stride >= ncell) or nshift must be 1.
+cudaError_t launch_paper_shifts(const Jobs& J, const Shape& sh, const Bins& B, int dtype, int a, int j0, int nshift,
+                                void* out, long long out_stride, cudaStream_t s);
+
+// f_a[node] = sum_{k < beta} buf[k * ncell + node], k increasing (Algorithm 5's final sum).
+cudaError_t launch_paper_sum(const Jobs& J, int dtype, int a, int beta, const void* buf, cudaStream_t s);
 
 // Spreading in two launches: per-tile boxes in shared memory written to
 // `boxes`, then the fixed-order combination of overlapping boxes into f.

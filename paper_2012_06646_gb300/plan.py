@@ -113,6 +113,21 @@ class Plan:
         check(self.lib.ib_spread(self.handle, n, _ptr(X), _ptr(G), _ptr(f), flags, _stream_ptr(stream)), "ib_spread")
         return f
 
+    def spread_paper(self, X, G, algorithm: int = 4, beta: int = 8, f=None, buffer=None, stream=None):
+        """The paper's spreading algorithm 4, 5 or 6 (comparators of `spread`): f = S G.
+
+        Algorithm 5 uses `buffer` (beta grids of the plan's dtype; allocated here if None)."""
+        n = self._points(X)
+        self._check(G, (n, self.ncomp), "G")
+        if f is None:
+            f = self._new(self.grid_shape())
+        self._check(f, self.grid_shape(), "f")
+        if algorithm == 5 and buffer is None:
+            buffer = torch.empty((beta,) + tuple(reversed(self.n)), dtype=self.dtype, device=self.device)
+        check(self.lib.ib_spread_paper(self.handle, n, _ptr(X), _ptr(G), _ptr(f), int(algorithm), int(beta),
+                                       _ptr(buffer), _stream_ptr(stream)), "ib_spread_paper")
+        return f
+
     def interpolate(self, X, u, U=None, reuse_bins=False, adjoint=False, stream=None):
         n = self._points(X)
         self._check(u, self.grid_shape(), "u")

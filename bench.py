@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=384, help="jobs of the served-batch measurement (0: skip)")
     ap.add_argument("--serve-loads", default="0.9,2.0",
                     help="offered loads as multiples of the one-job loop's capacity, comma separated")
+    ap.add_argument("--paper-reps", type=int, default=3,
+                    help="timed repetitions of the paper's spreading algorithms 4-6 on the workload (0: skip)")
     return ap.parse_args()
 
 
@@ -285,6 +287,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def paper_algorithms_bench(plan, X, G, f, stream, reps, beta=8):
+    """The paper's spreading algorithms 4, 5 and 6 (beta shifts per pass) next to
+    this library's binning + spreading, on the same points and forces: mean
+    milliseconds per call over `reps` timed calls after one warm-up call, L2
+    flushed before each.  Every variant includes its own key computation and sort."""
+    import torch
+    device = X.device
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    buf = torch.empty((beta,) + tuple(reversed(plan.n)), dtype=torch.float32, device=device)
+    variants = {
+        "ours_bin_and_spread": lambda: (plan.bin(X, stream=stream), plan.spread(X, G, f=f, reuse_bins=True,
+                                                                                stream=stream)),
+        "alg4": lambda: plan.spread_paper(X, G, algorithm=4, f=f, stream=stream),
+        f"alg5_beta{beta}": lambda: plan.spread_paper(X, G, algorithm=5, beta=beta, f=f, buffer=buf, stream=stream),
+        f"alg6_beta{beta}": lambda: plan.spread_paper(X, G, algorithm=6, beta=beta, f=f, stream=stream),
+    }
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, call in variants.items():
+            call()
+            times = []
+            for r in range(reps):
+                flush.fill_(r & 0xFF)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                call()
+                b.record(stream)
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+            out[name + "_ms"] = statistics.mean(times)
+    plan.check(stream)
+    base = out["ours_bin_and_spread_ms"]
+    out["speedup_over"] = {k[:-3]: v / base for k, v in out.items() if k != "ours_bin_and_spread_ms"}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -416,6 +454,14 @@ def run_ours(args):
                "h2d_bytes_per_step": int(Xd.numel() * 4 + Gd.numel() * 4),
                "d2h_bytes_per_step": int(Uh.numel() * 4 + fh.numel() * 4 + Xh.numel() * 4)}
 
+    paper = None
+    if args.paper_reps > 0 and rank == 0:
+        try:
+            paper = paper_algorithms_bench(plan, X, Gs[0], f, stream, args.paper_reps)
+            paper["workload"] = f"{N}^3 MAC grid, {npts} points, FP32, one spread (all three components)"
+        except Exception as exc:
+            paper = {"error": repr(exc)}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -466,7 +512,8 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "calls_ms": mean_ms,
-            "serving": serving}
+            "serving": serving,
+            "paper_algorithms": paper}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

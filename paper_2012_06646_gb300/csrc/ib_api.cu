@@ -451,13 +451,18 @@ ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* 
   J.njobs = 1;
   const Bins B = call_bins(p, npts);
   p->binned = false;    // the bins are keyed by a component's cells from here on
+  // The list of inhabited cells and its length reuse binning scratch that is
+  // dead once the bins are built: perm_tmp (2 npts entries >= the number of
+  // inhabited cells) and key.
+  uint32_t* cells = (uint32_t*)B.perm_tmp;
+  uint32_t* q = B.key;
   ib_status out = IB_OK;
   for (int a = 0; a < p->desc.ncomp && out == IB_OK; ++a) {
     // Keys: cells in component a's staggering (one staggering for every
     // component on the cell-centred grid: one sort).
     if (a == 0 || p->sh.mac) {
       if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(ncell + 2), s) != cudaSuccess ||
-          launch_bin(J, p->sh, B, dtype, s, a) != cudaSuccess) {
+          launch_bin(J, p->sh, B, dtype, s, a) != cudaSuccess || launch_paper_cells(B, cells, q, s) != cudaSuccess) {
         out = IB_ERR_CUDA;
         break;
       }
@@ -466,11 +471,11 @@ ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* 
     if (algorithm == IB_PAPER_ALG4) {
       if (cudaMemsetAsync(fa, 0, (size_t)ncell * eb, s) != cudaSuccess) out = IB_ERR_CUDA;
       for (int j = 0; j < S && out == IB_OK; ++j)   // one shift per launch: the synchronisation per shift
-        if (launch_paper_shifts(J, p->sh, B, dtype, a, j, 1, fa, 0, s) != cudaSuccess) out = IB_ERR_CUDA;
+        if (launch_paper_shifts(J, p->sh, B, dtype, a, j, 1, fa, 0, cells, q, s) != cudaSuccess) out = IB_ERR_CUDA;
     } else {
       if (cudaMemsetAsync(buf, 0, buf_bytes, s) != cudaSuccess) out = IB_ERR_CUDA;
       for (int j0 = 0; j0 < S && out == IB_OK; j0 += beta)
-        if (launch_paper_shifts(J, p->sh, B, dtype, a, j0, beta < S - j0 ? beta : S - j0, buf, ncell, s) !=
+        if (launch_paper_shifts(J, p->sh, B, dtype, a, j0, beta < S - j0 ? beta : S - j0, buf, ncell, cells, q, s) !=
             cudaSuccess)
           out = IB_ERR_CUDA;
       if (out == IB_OK && launch_paper_sum(J, dtype, a, beta, buf, s) != cudaSuccess) out = IB_ERR_CUDA;

@@ -27,13 +27,18 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
 
 // The paper's parallel spreading (Algorithm 4: one segmented reduce per
 // shift; Algorithms 5 and 6: beta shifts per pass into beta grid buffers) for
-// component a of a single job, on bins keyed by that component's cells:
+// component a of a single job, on bins keyed by that component's cells and
+// its list of inhabited cells:
 // shifts j0 .. j0 + nshift - 1 (colexicographic digits, x fastest); the
 // reduced value of shift j0 + k is added to out[k * out_stride + node] (out is
 // the component's grid, or a buffer of grids).  Distinct shifts of one launch
 // must go to distinct grids (out_stride >= ncell) or nshift must be 1.
 cudaError_t launch_paper_shifts(const Jobs& J, const Shape& sh, const Bins& B, int dtype, int a, int j0, int nshift,
-                                void* out, long long out_stride, cudaStream_t s);
+                                void* out, long long out_stride, const uint32_t* cells, const uint32_t* q,
+                                cudaStream_t s);
+
+// The inhabited cells of the bins ("count unique" of Algorithm 4): cells[0 .. *q).
+cudaError_t launch_paper_cells(const Bins& B, uint32_t* cells, uint32_t* q, cudaStream_t s);
 
 // f_a[node] = sum_{k < beta} buf[k * ncell + node], k increasing (Algorithm 5's final sum).
 cudaError_t launch_paper_sum(const Jobs& J, int dtype, int a, int beta, const void* buf, cudaStream_t s);

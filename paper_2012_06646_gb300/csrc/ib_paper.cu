@@ -15,11 +15,11 @@
 // buffers, no contention within a launch), then sum the buffers; Algorithm 6
 // allocates the buffers itself.
 //
-// The GPU form: one thread per cell (the segments of the sorted points are the
-// cells' ranges in the bins, so the key-value sort and unique count are the
-// binning of ib_bin.cu keyed by the component's cells); the thread walks its
-// cell's points in sorted order, which is the segmented reduce with a fixed
-// order, and writes its node.  Results are therefore run-to-run reproducible.
+// The GPU form: the key-value sort is the binning of ib_bin.cu keyed by the
+// component's cells, the unique count a compaction of the inhabited cells, and
+// one thread per inhabited cell walks the cell's points in sorted order (the
+// segmented reduce, with a fixed order) and writes its node.  Results are
+// therefore run-to-run reproducible.
 #include "ib_internal.h"
 
 namespace ibgb {
@@ -29,22 +29,40 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxPass = 16;   // shifts handled by one launch (a pass of beta > 16 takes several launches)
 
-template <typename T, int D>
+// "Count unique": the inhabited cells of the bins, appended to `cells` (any
+// order: every cell reaches its own node for a given shift, so the order of
+// the list does not change any sum), their number in *q.
+__global__ void __launch_bounds__(kThreads) k_paper_cells(const Bins B, uint32_t* __restrict__ cells,
+                                                          uint32_t* __restrict__ q) {
+  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const bool inhabited = c < B.ncell_total && B.count[c + 1] > B.count[c];
+  const unsigned m = __ballot_sync(0xffffffffu, inhabited);
+  if (m == 0) return;
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd(q, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);   // every lane is here (no divergence above)
+  if (inhabited) cells[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)c;
+}
+
+// One thread per inhabited cell (q of them, at most npts).
+template <typename T, int D, int NS>
 __global__ void __launch_bounds__(kThreads) k_paper_shifts(const __grid_constant__ Jobs J, const Shape sh,
                                                            const Bins B, int a, int j0, int nshift, T* __restrict__ out,
-                                                           long long out_stride) {
-  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (c >= B.ncell_total) return;
+                                                           long long out_stride, const uint32_t* __restrict__ cells,
+                                                           const uint32_t* __restrict__ q) {
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= *q) return;
+  const long long c = cells[i];
   const uint32_t s = B.count[c], e = B.count[c + 1];
-  if (s == e) return;                                   // not an inhabited cell
   const Job& jb = J.one;
   const T* X = (const T*)jb.X;
   const T* G = (const T*)jb.G;
   const int nc = sh.ncomp;
   const T hmd = (T)jb.hmd;
-  T V[kMaxPass];
+  T V[NS];
 #pragma unroll
-  for (int k = 0; k < kMaxPass; ++k) V[k] = (T)0;
+  for (int k = 0; k < NS; ++k) V[k] = (T)0;
   // Segmented reduce: the cell's points in sorted order.
   for (uint32_t q = s; q < e; ++q) {
     const long long p = B.perm[q];
@@ -58,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_paper_shifts(const __grid_constant
     }
     const T g = hmd * G[p * nc + a];
 #pragma unroll
-    for (int k = 0; k < kMaxPass; ++k) {
+    for (int k = 0; k < NS; ++k) {
       if (k >= nshift) break;
       const int j = j0 + k;                             // shift digits, x fastest (Algorithm 1)
       T wt = w[0][j & 3] * w[1][(j >> 2) & 3];
@@ -72,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k_paper_shifts(const __grid_constant
   const int cy = (int)((c / n0) % n1);
   const int cz = (D == 3) ? (int)(c / ((long long)n0 * n1)) : 0;
 #pragma unroll
-  for (int k = 0; k < kMaxPass; ++k) {
+  for (int k = 0; k < NS; ++k) {
     if (k >= nshift) break;
     const int j = j0 + k;
     long long node = wrapn(cx + (j & 3) - 1, n0) + (long long)n0 * wrapn(cy + ((j >> 2) & 3) - 1, n1);
@@ -97,20 +115,40 @@ inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + thre
 
 }  // namespace
 
+cudaError_t launch_paper_cells(const Bins& B, uint32_t* cells, uint32_t* q, cudaStream_t s) {
+  if (cudaMemsetAsync(q, 0, sizeof(uint32_t), s) != cudaSuccess) return cudaErrorUnknown;
+  const unsigned g = grid_for(B.ncell_total, kThreads);
+  if (g > 0) k_paper_cells<<<g, kThreads, 0, s>>>(B, cells, q);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_paper_shifts(const Jobs& J, const Shape& sh, const Bins& B, int dtype, int a, int j0, int nshift,
-                                void* out, long long out_stride, cudaStream_t s) {
+                                void* out, long long out_stride, const uint32_t* cells, const uint32_t* q,
+                                cudaStream_t s) {
+  // q <= min(ncell, npts) threads do work; the grid covers the bound.
+  const long long bound = B.npts_total < B.ncell_total ? B.npts_total : B.ncell_total;
+  const unsigned g = grid_for(bound, kThreads);
+  if (g == 0) return cudaSuccess;
   for (int k0 = 0; k0 < nshift; k0 += kMaxPass) {
     const int ns = nshift - k0 < kMaxPass ? nshift - k0 : kMaxPass;
-    const unsigned g = grid_for(B.ncell_total, kThreads);
-    if (g == 0) break;
     if (dtype == 0) {
       float* o = (float*)out + (long long)k0 * out_stride;
-      if (sh.dim == 3) k_paper_shifts<float, 3><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride);
-      else k_paper_shifts<float, 2><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride);
+      if (ns == 1) {
+        if (sh.dim == 3) k_paper_shifts<float, 3, 1><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, 1, o, out_stride, cells, q);
+        else k_paper_shifts<float, 2, 1><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, 1, o, out_stride, cells, q);
+      } else {
+        if (sh.dim == 3) k_paper_shifts<float, 3, kMaxPass><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride, cells, q);
+        else k_paper_shifts<float, 2, kMaxPass><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride, cells, q);
+      }
     } else {
       double* o = (double*)out + (long long)k0 * out_stride;
-      if (sh.dim == 3) k_paper_shifts<double, 3><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride);
-      else k_paper_shifts<double, 2><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride);
+      if (ns == 1) {
+        if (sh.dim == 3) k_paper_shifts<double, 3, 1><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, 1, o, out_stride, cells, q);
+        else k_paper_shifts<double, 2, 1><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, 1, o, out_stride, cells, q);
+      } else {
+        if (sh.dim == 3) k_paper_shifts<double, 3, kMaxPass><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride, cells, q);
+        else k_paper_shifts<double, 2, kMaxPass><<<g, kThreads, 0, s>>>(J, sh, B, a, j0 + k0, ns, o, out_stride, cells, q);
+      }
     }
   }
   return cudaGetLastError();

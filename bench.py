@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=384, help="jobs of the served-batch measurement (0: skip)")
     ap.add_argument("--serve-loads", default="0.9,2.0",
                     help="offered loads as multiples of the one-job loop's capacity, comma separated")
+    ap.add_argument("--membrane-reps", type=int, default=10,
+                    help="timed repetitions of the clustered red-cell membrane workload (0: skip)")
     ap.add_argument("--paper-reps", type=int, default=3,
                     help="timed repetitions of the paper's spreading algorithms 4-6 on the workload (0: skip)")
     return ap.parse_args()
@@ -323,6 +325,75 @@ def paper_algorithms_bench(plan, X, G, f, stream, reps, beta=8):
     return out
 
 
+def touched_nodes_mac(X: np.ndarray, N: int) -> int:
+    """Distinct grid nodes (summed over the three MAC components) inside the 4^3
+    support of at least one point: the nodes a spread writes or an interpolation
+    reads when only the touched part of the grid counts."""
+    total = 0
+    u = X.astype(np.float64) * N
+    t = np.arange(4) - 1
+    for a in range(3):
+        base = np.floor(u - np.where(np.arange(3) == a, 0.0, 0.5)).astype(np.int64)   # cell of this staggering
+        ix = (base[:, None, 0] + t[None, :]) % N
+        iy = (base[:, None, 1] + t[None, :]) % N
+        iz = (base[:, None, 2] + t[None, :]) % N
+        idx = (ix[:, :, None, None] + N * (iy[:, None, :, None] + N * iz[:, None, None, :])).ravel()
+        total += int(np.unique(idx).size)
+    return total
+
+
+def membrane_bench(device, stream, reps: int, peak: float, seed: int = 0, N: int = 128):
+    """The clustered-membrane workload: randomly oriented, non-overlapping red cells
+    (2562 points each) packed into the 128^3 MAC box, smooth membrane forces.
+    Times binning + spreading (TwoSum node sums, and plain) and interpolation,
+    CUDA events on the stream, L2 flushed before each timed call."""
+    import torch
+    import ib_inputs
+    from paper_2012_06646_gb300.plan import Plan
+    mem = ib_inputs.pack_membranes(seed)
+    X = torch.from_numpy(mem.X).to(device)
+    G = torch.from_numpy(ib_inputs.membrane_forces(seed, mem)).to(device)
+    u = torch.from_numpy(ib_inputs.normal_array(seed + 1, (3, N, N, N))).to(device)
+    n = X.shape[0]
+    plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", max_points=n, compensated=True, device=device)
+    f = torch.empty(plan.grid_shape(), dtype=torch.float32, device=device)
+    U = torch.empty((n, 3), dtype=torch.float32, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    calls = {
+        "bin_and_spread_compensated": lambda: plan.spread(X, G, f=f, compensated=True, stream=stream),
+        "bin_and_spread": lambda: plan.spread(X, G, f=f, stream=stream),
+        "interp": lambda: plan.interpolate(X, u, U=U, reuse_bins=True, stream=stream),
+    }
+    ms = {}
+    with torch.cuda.stream(stream):
+        for name, call in calls.items():
+            call()
+            t = []
+            for r in range(reps):
+                flush.fill_(r & 0xFF)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                call()
+                b.record(stream)
+                b.synchronize()
+                t.append(a.elapsed_time(b))
+            ms[name] = statistics.mean(t)
+    plan.check(stream)
+    pair = ms["bin_and_spread_compensated"] + ms["interp"]
+    grid_bytes = 2 * (n * 24 + 3 * N ** 3 * 4)
+    touched = touched_nodes_mac(mem.X, N)
+    touched_bytes = 2 * (n * 24 + touched * 4)
+    return {"workload": f"{len(mem.centres)} red cells x 2562 points ({n} points, volume fraction "
+                        f"{mem.volume_fraction:.3f}), {N}^3 MAC grid, FP32, TwoSum node sums in spreading",
+            "calls_ms": ms, "pts_per_s": n / (pair / 1e3),
+            "roofline_full_grid": {"achieved_gbs": grid_bytes / (pair / 1e3) / 1e9, "peak": peak,
+                                   "frac": grid_bytes / (pair / 1e3) / 1e9 / peak, "bytes": grid_bytes},
+            "roofline_touched_nodes": {"achieved_gbs": touched_bytes / (pair / 1e3) / 1e9, "peak": peak,
+                                       "frac": touched_bytes / (pair / 1e3) / 1e9 / peak, "bytes": touched_bytes,
+                                       "touched_nodes": touched},
+            "note": "spread + interpolate pair (compensated spread, binning included)"}
+
+
 def run_ours(args):
     import torch
 
@@ -454,6 +525,13 @@ def run_ours(args):
                "h2d_bytes_per_step": int(Xd.numel() * 4 + Gd.numel() * 4),
                "d2h_bytes_per_step": int(Uh.numel() * 4 + fh.numel() * 4 + Xh.numel() * 4)}
 
+    membranes = None
+    if args.membrane_reps > 0 and rank == 0:
+        try:
+            membranes = membrane_bench(device, stream, args.membrane_reps, load_peaks()[0])
+        except Exception as exc:
+            membranes = {"error": repr(exc)}
+
     paper = None
     if args.paper_reps > 0 and rank == 0:
         try:
@@ -513,6 +591,7 @@ def run_ours(args):
             "clocks": clocks,
             "calls_ms": mean_ms,
             "serving": serving,
+            "membranes": membranes,
             "paper_algorithms": paper}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -728,7 +728,9 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
                                                              const T* __restrict__ boxes, long long ncell_total,
                                                              int accumulate) {
   using Gm = Geo<D, TS>;
-  const int c = (blockIdx.x * kThreads + threadIdx.x) * V;   // global cell ids stay below 2^31
+  // Blocks walk the grid from its end: the tile kernel writes the boxes in
+  // tile order, so the last-written boxes (the ones still in L2) are read first.
+  const int c = ((gridDim.x - 1 - blockIdx.x) * kThreads + threadIdx.x) * V;   // global cell ids stay below 2^31
   if (c >= ncell_total) return;
   const int jj = job_of_cell(J, c);
   const Job jb = job_at(J, jj);

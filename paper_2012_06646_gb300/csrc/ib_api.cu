@@ -102,10 +102,11 @@ bool valid_shape(int dim, int grid, int kernel, int dtype, int ncomp) {
 
 // Arena layout shared by plans and batches.
 struct Layout {
-  size_t count, key, rank, perm_tmp, perm, block_sums, err, boxes, table, io, total;
+  size_t count, key, rank, perm_tmp, perm, block_sums, err, tflags, boxes, table, io, total;
 };
 
-Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t table_bytes, size_t io_bytes = 0) {
+Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t table_bytes, size_t io_bytes = 0,
+                   long long ntiles = 0) {
   Layout L;
   size_t off = 0;
   L.count = off;      off += align_up(sizeof(uint32_t) * (size_t)(ncell + 2));
@@ -115,6 +116,7 @@ Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t t
   L.perm = off;       off += align_up(sizeof(uint32_t) * (size_t)npts);
   L.block_sums = off; off += align_up(sizeof(uint32_t) * (size_t)(scan_blocks(ncell + 1) + 1));
   L.err = off;        off += align_up(sizeof(uint32_t));
+  L.tflags = off;     off += align_up(sizeof(uint32_t) * (size_t)ntiles);
   L.boxes = off;      off += align_up(boxes_bytes);
   L.table = off;      off += align_up(table_bytes);
   L.io = off;         off += align_up(io_bytes);
@@ -131,6 +133,7 @@ Bins carve(char* base, const Layout& L) {
   B.perm = (uint32_t*)(base + L.perm);
   B.block_sums = (uint32_t*)(base + L.block_sums);
   B.err = (uint32_t*)(base + L.err);
+  B.tflags = L.boxes > L.tflags ? (uint32_t*)(base + L.tflags) : nullptr;
   B.ncell_total = 0;
   B.npts_total = 0;
   return B;
@@ -206,7 +209,7 @@ bool plan_sizes(const ib_plan_desc* d, Job* jb, int* tp, int* tc, long long* ntp
   if (tc) *tc = tile_comp;
   if (ntp) *ntp = ntp_;
   if (ntc) *ntc = ntc_;
-  if (L) *L = make_layout(j.ncell, d->max_points, boxes, 0);
+  if (L) *L = make_layout(j.ncell, d->max_points, boxes, 0, 0, ntp_ > ntc_ ? ntp_ : ntc_);
   return true;
 }
 
@@ -514,7 +517,7 @@ static bool batch_sizes(const ib_batch_desc* d, int* tile, Layout* L) {
                                 (size_t)d->max_cells * (size_t)d->ncomp) + 3 * 256
                         : 0;
   if (tile) *tile = t;
-  if (L) *L = make_layout(d->max_cells, d->max_points, boxes, sizeof(Job) * (size_t)d->max_jobs, io);
+  if (L) *L = make_layout(d->max_cells, d->max_points, boxes, sizeof(Job) * (size_t)d->max_jobs, io, d->max_tiles);
   return true;
 }
 

@@ -71,6 +71,7 @@ struct Bins {
   uint32_t* perm;        // [npts_total]: points in cell order, index order inside a cell (stable)
   uint32_t* block_sums;  // scan scratch
   uint32_t* err;         // device error word
+  uint32_t* tflags;      // [tiles]: 1 if the spreading tile holds points (its boxes were written), or null
   long long ncell_total;
   long long npts_total;
 };
@@ -179,11 +180,15 @@ __device__ __forceinline__ uint32_t cell_short(float X, int S, int E, Cell1<floa
 // FP32 position with a short scale, the common case: X S = p + e exactly
 // (TwoProduct with one FMA), so u = X scale = (p + e) 2^E exactly.  floor(u)
 // is floor(p), lowered by one when p is an integer and e < 0 (|e| is below
-// half an ulp of p, so it cannot cross any other integer); the same holds for
-// u - 1/2 = (p - 1/2) + e, with p - 1/2 exact while |p| < 2^22.  Offsets are
-// formed as (p - floor) + e and ((floor + 1) - p) - e, so both r and 1 - r
-// keep their relative accuracy.  Outside |p| in [2^-100, 2^22) (or for a
-// non-finite X) the integer path decides.
+// half an ulp of p, so it cannot cross any other integer).  The fraction
+// u - floor(u) is D + e = 1 - (C - e) with D = p - floor and C = (floor + 1) - p:
+// D is exact for p >= 0 (the fraction of a float) and C for p < 0 (Sterbenz,
+// or 0 - p), and the exact one is a multiple of ulp(p) > 2|e|.  So the cell of
+// xi = 1/2 (floor(u - 1/2) = floor(u) - [fraction < 1/2]) is decided exactly
+// from the exact part, and every offset is formed from it with e added last:
+// r and 1 - r for both staggerings keep their relative accuracy whenever they
+// are small (a value p - 1/2 formed in FP32 would not: it rounds for p < 1/4).
+// Outside |p| in [2^-100, 2^22) (or for a non-finite X) the integer path decides.
 __device__ __forceinline__ uint32_t cell_twoprod(float X, const Job& jb, int b, Cell1<float>& c) {
   const float p0 = X * jb.sSf[b];
   const float e0 = fmaf(X, jb.sSf[b], -p0);
@@ -193,15 +198,19 @@ __device__ __forceinline__ uint32_t cell_twoprod(float X, const Job& jb, int b, 
   if (!(ap < 4194304.f) || !(ap >= 7.8886e-31f)) return cell_short(X, jb.sS[b], jb.sE[b], c);
   float f0 = floorf(p);
   if (p == f0 && e < 0.f) f0 -= 1.f;
-  const float v = p - 0.5f;
-  float f1 = floorf(v);
-  if (v == f1 && e < 0.f) f1 -= 1.f;
+  const float D = p - f0;
+  const float C = (f0 + 1.f) - p;
+  const bool pos = p >= 0.f;
+  // fraction below 1/2: the xi = 1/2 cell is one lower
+  const bool lower = pos ? (D < 0.5f || (D == 0.5f && e < 0.f)) : (C > 0.5f || (C == 0.5f && e < 0.f));
   c.i0 = (int)f0;
-  c.i1 = (int)f1;
-  c.r0 = (p - f0) + e;
-  c.c0 = ((f0 + 1.f) - p) - e;
-  c.r1 = (v - f1) + e;
-  c.c1 = ((f1 + 1.f) - v) - e;
+  c.i1 = (int)f0 - (lower ? 1 : 0);
+  c.r0 = D + e;
+  c.c0 = C - e;
+  const float rA = pos ? (lower ? D + 0.5f : D - 0.5f) : (lower ? 1.5f - C : 0.5f - C);
+  const float cA = pos ? (lower ? 0.5f - D : 1.5f - D) : (lower ? C - 0.5f : C + 0.5f);
+  c.r1 = rA + e;
+  c.c1 = cA - e;
   return 0;
 }
 

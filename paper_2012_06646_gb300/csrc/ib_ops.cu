@@ -177,7 +177,7 @@ __device__ __forceinline__ bool point_comp(const Job& jb, const Shape& sh, const
 
 template <typename T, int D, int TS, bool COMP, int W = kSpreadWarps>
 __global__ void __launch_bounds__(32 * W) k_spread_warp(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
-                                                         T* __restrict__ boxes, long long nunits) {
+                                                         T* __restrict__ boxes, long long nunits, int skip_empty) {
   using Gm = Geo<D, TS>;
   constexpr int REC = WRec<D>::words;
   constexpr int PLANES = COMP ? 2 : 1;
@@ -241,6 +241,10 @@ __global__ void __launch_bounds__(32 * W) k_spread_warp(const __grid_constant__ 
     M += __shfl_sync(0xffffffffu, inc, 31);
   }
   __syncwarp();
+  if (skip_empty) {                                // sparse call: an empty tile writes no boxes
+    if (lane == 0) B.tflags[gt] = M > 0 ? 1u : 0u;
+    if (M == 0) return;
+  }
 
   const T* Xg = (const T*)jb.X;
   const T* Gp = (const T*)jb.G;
@@ -483,7 +487,7 @@ __device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane
 
 template <typename T, bool COMP, bool MAC>
 __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
-                                                     T* __restrict__ boxes) {
+                                                     T* __restrict__ boxes, int skip_empty) {
   constexpr int TS = 8;
   using Gm = Geo<3, TS>;
   constexpr int PLANES = COMP ? 2 : 1;
@@ -545,6 +549,10 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
     M += __shfl_sync(0xffffffffu, inc, 31);
   }
   __syncwarp();
+  if (skip_empty) {                                // sparse call: an empty tile writes no boxes
+    if (lane == 0) B.tflags[gt] = M > 0 ? 1u : 0u;
+    if (M == 0) return;
+  }
 
   const T* Xg = (const T*)jb.X;
   const T* Gp = (const T*)jb.G;
@@ -650,9 +658,10 @@ __device__ __forceinline__ Cover3 cover_fast(int x, int n, int ntile) {
   return c;
 }
 
-template <typename T, int D, int TS, bool CP>
+template <typename T, int D, int TS, bool CP, bool CHECK>
 __device__ __noinline__ void combine_general(const Jobs& J, int j, const Shape& sh, const T* __restrict__ boxes,
-                                             const int* x, long long lc, int accumulate) {
+                                             const uint32_t* __restrict__ tflags, const int* x, long long lc,
+                                             int accumulate) {
   using Gm = Geo<D, TS>;
   const Job& jb = job_at(J, j);
   int tl[3][kMaxCover], of[3][kMaxCover], nco[3];
@@ -671,6 +680,7 @@ __device__ __noinline__ void combine_general(const Jobs& J, int j, const Shape& 
       for (int iy = 0; iy < nco[1]; ++iy)
         for (int ix = 0; ix < nco[0]; ++ix) {
           const long long tile = jb.tile_base + tl[0][ix] + (long long)jb.ntile[0] * (tl[1][iy] + (long long)jb.ntile[1] * tl[2][iz]);
+          if (CHECK && !tflags[tile]) continue;  // empty tile: its boxes are zero and were not written
           const long long idx = (tile * nc + a) * plane + (of[2][iz] * Gm::BY + of[1][iy]) * Gm::BX + of[0][ix];
           if (CP) {
             const T sv = boxes[idx];
@@ -723,9 +733,12 @@ __device__ __forceinline__ void store_v(T* p, const T* v) {
   }
 }
 
-template <typename T, int D, int TS, bool CP, int V>
+// CHECK: some tiles may be empty (a sparse call); their boxes were not written
+// and count as zero.
+template <typename T, int D, int TS, bool CP, int V, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_constant__ Jobs J, const Shape sh,
-                                                             const T* __restrict__ boxes, long long ncell_total,
+                                                             const T* __restrict__ boxes,
+                                                             const uint32_t* __restrict__ tflags, long long ncell_total,
                                                              int accumulate) {
   using Gm = Geo<D, TS>;
   // Blocks walk the grid from its end: the tile kernel writes the boxes in
@@ -753,7 +766,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       int xv[3] = {x[0] + v, x[1], x[2]};
-      combine_general<T, D, TS, CP>(J, jj, sh, boxes, xv, lc + v, accumulate);
+      combine_general<T, D, TS, CP, CHECK>(J, jj, sh, boxes, tflags, xv, lc + v, accumulate);
     }
     return;
   }
@@ -788,6 +801,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
         ok[k] = iz < cz.n && iy < cy.n && ix < cx.n;
         const int trow = (int)jb.tile_base + jb.ntile[0] * (cy.t(iy) + jb.ntile[1] * cz.t(iz));
         const int orow = (cz.o(iz) * Gm::BY + cy.o(iy)) * Gm::BX;
+        if (CHECK) ok[k] = ok[k] && tflags[trow + cx.t(ix)] != 0u;   // empty tile: zero boxes, not written
         bp[k] = ok[k] ? boxes + (long long)(trow + cx.t(ix)) * nc * plane + (orow + cx.o(ix)) : boxes;
       }
       T val[3][8][V];
@@ -839,6 +853,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 #pragma unroll
       for (int ix = 0; ix < 3; ++ix) {
         if (ix >= cx.n) break;
+        if (CHECK && !tflags[trow + cx.t(ix)]) continue;   // empty tile: zero boxes, not written
         const T* bp = boxes + (long long)(trow + cx.t(ix)) * nc * plane + (orow + cx.o(ix));
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -1249,56 +1264,71 @@ size_t spread_smem(bool comp) {
 }
 
 template <typename T, int D, int TS, bool COMP>
-void launch_spread_warp(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long nunits, cudaStream_t s) {
+void launch_spread_warp(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long nunits, int skip_empty,
+                        cudaStream_t s) {
   const size_t bytes = spread_smem<T, D, TS>(COMP);
   cudaFuncSetAttribute(k_spread_warp<T, D, TS, COMP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   allow_smem(k_spread_warp<T, D, TS, COMP>, bytes);
   const unsigned grid = (unsigned)((nunits + kSpreadWarps - 1) / kSpreadWarps);
-  k_spread_warp<T, D, TS, COMP><<<grid, 32 * kSpreadWarps, bytes, s>>>(J, sh, B, (T*)boxes, nunits);
+  k_spread_warp<T, D, TS, COMP><<<grid, 32 * kSpreadWarps, bytes, s>>>(J, sh, B, (T*)boxes, nunits, skip_empty);
 }
 
 template <typename T, bool COMP, bool MAC>
-void launch_spread_tile3(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, cudaStream_t s) {
+void launch_spread_tile3(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, int skip_empty,
+                         cudaStream_t s) {
   using Gm = Geo<3, 8>;
   const size_t bytes = ((size_t)3 * (COMP ? 2 : 1) * Gm::BV + (size_t)(kSpreadBatch + 1) * kRec3) * sizeof(T);
   cudaFuncSetAttribute(k_spread_tile3<T, COMP, MAC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   allow_smem(k_spread_tile3<T, COMP, MAC>, bytes);
-  k_spread_tile3<T, COMP, MAC><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes);
+  k_spread_tile3<T, COMP, MAC><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes, skip_empty);
+}
+
+template <typename T, int D, int TS, bool CP, int V>
+void launch_combine(const Jobs& J, const Shape& sh, const Bins& B, const void* boxes, int acc, bool sparse,
+                    cudaStream_t s) {
+  const unsigned g = grid_for((B.ncell_total + V - 1) / V, kThreads);
+  if (sparse)
+    k_spread_combine<T, D, TS, CP, V, true><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total, acc);
+  else
+    k_spread_combine<T, D, TS, CP, V, false><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total, acc);
 }
 
 template <typename T, int D, int TS>
 cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool comp,
                         bool accumulate, bool pairs, cudaStream_t s) {
+  // A sparse call (fewer than 8 points per tile on average, e.g. a few membranes
+  // in a large box) skips the boxes of empty tiles; a dense one writes every box
+  // and combines without looking at tile flags.
+  const bool sparse = B.tflags != nullptr && B.npts_total < 8 * ntiles;
+  const int skip = sparse ? 1 : 0;
   if (ntiles > 0) {
     bool done = false;
     if constexpr (D == 3 && TS == 8) {
       if (sh.ncomp == 3) {   // three components: one warp per tile for all of them
         if (sh.mac) {
-          if (comp) launch_spread_tile3<T, true, true>(J, sh, B, boxes, ntiles, s);
-          else launch_spread_tile3<T, false, true>(J, sh, B, boxes, ntiles, s);
+          if (comp) launch_spread_tile3<T, true, true>(J, sh, B, boxes, ntiles, skip, s);
+          else launch_spread_tile3<T, false, true>(J, sh, B, boxes, ntiles, skip, s);
         } else {
-          if (comp) launch_spread_tile3<T, true, false>(J, sh, B, boxes, ntiles, s);
-          else launch_spread_tile3<T, false, false>(J, sh, B, boxes, ntiles, s);
+          if (comp) launch_spread_tile3<T, true, false>(J, sh, B, boxes, ntiles, skip, s);
+          else launch_spread_tile3<T, false, false>(J, sh, B, boxes, ntiles, skip, s);
         }
         done = true;
       }
     }
     if (!done) {
       const long long nunits = ntiles * sh.ncomp;
-      if (comp) launch_spread_warp<T, D, TS, true>(J, sh, B, boxes, nunits, s);
-      else launch_spread_warp<T, D, TS, false>(J, sh, B, boxes, nunits, s);
+      if (comp) launch_spread_warp<T, D, TS, true>(J, sh, B, boxes, nunits, skip, s);
+      else launch_spread_warp<T, D, TS, false>(J, sh, B, boxes, nunits, skip, s);
     }
   }
   if (B.ncell_total > 0) {
     const int acc = accumulate ? 1 : 0;
     if (pairs) {
-      const unsigned g = grid_for((B.ncell_total + 1) / 2, kThreads);
-      if (comp) k_spread_combine<T, D, TS, true, 2><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
-      else k_spread_combine<T, D, TS, false, 2><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
+      if (comp) launch_combine<T, D, TS, true, 2>(J, sh, B, boxes, acc, sparse, s);
+      else launch_combine<T, D, TS, false, 2>(J, sh, B, boxes, acc, sparse, s);
     } else {
-      const unsigned g = grid_for(B.ncell_total, kThreads);
-      if (comp) k_spread_combine<T, D, TS, true, 1><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
-      else k_spread_combine<T, D, TS, false, 1><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.ncell_total, acc);
+      if (comp) launch_combine<T, D, TS, true, 1>(J, sh, B, boxes, acc, sparse, s);
+      else launch_combine<T, D, TS, false, 1>(J, sh, B, boxes, acc, sparse, s);
     }
   }
   return cudaGetLastError();

@@ -97,3 +97,66 @@ def test_many_invalid_positions(P, orc):
     assert np.isnan(Uh[bad]).all()
     U_ref, Uabs = orc.interp(g, X[~bad], u)
     assert_interp_close(Uh[~bad], U_ref, Uabs)
+
+
+SPARSE = [
+    # dim, n, mac, ncomp, dtype, compensated
+    (3, (48, 40, 32), True, 3, np.float32, False),
+    (3, (48, 40, 32), True, 3, np.float32, True),
+    (3, (40, 40, 40), False, 2, np.float32, False),
+    (3, (24, 32, 40), True, 3, np.float64, False),
+    (2, (96, 64), True, 2, np.float32, True),
+]
+
+
+@pytest.mark.parametrize("case", SPARSE, ids=[f"{c[0]}d-{'x'.join(map(str, c[1]))}-{'mac' if c[2] else 'cc'}-c{c[3]}"
+                                              f"-{np.dtype(c[4]).name}{'-comp' if c[5] else ''}" for c in SPARSE])
+def test_sparse_points_skip_empty_tiles(P, orc, case):
+    """Fewer than 8 points per tile: empty tiles write no boxes and the combination
+    skips them; points sit in a corner of the box and across the periodic seam."""
+    dim, n, mac, ncomp, dtype, comp = case
+    L = (1.0,) * dim
+    rng_pts = ib_inputs.uniform_points(77, 60, L, dim, dtype=np.float64)
+    X = (0.15 * rng_pts - 0.05).astype(dtype)          # a corner cluster, some points at negative coordinates
+    X = np.concatenate([X, ib_inputs.uniform_points(78, 5, L, dim, dtype=dtype)])
+    G = ib_inputs.normal_array(79, (len(X), ncomp), dtype=dtype)
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    plan = P(dim, n, L, grid="mac" if mac else "cc", dtype=tdt, ncomp=ncomp, max_points=len(X), compensated=comp)
+    f = host(plan.spread(dev(X), dev(G), compensated=comp))
+    g = orc.Grid(dim=dim, n=n, L=L, mac=mac, ncomp=ncomp)
+    f_ref, fabs = orc.spread(g, X, G)
+    from _gpu import FLOOR32, FLOOR64
+    rel, floor = (1e-5, FLOOR32) if dtype == np.float32 else (1e-12, FLOOR64)
+    assert_spread_close(f, f_ref, fabs, rel, floor)
+    # a dense call on the same plan afterwards writes every box again
+    Xd = ib_inputs.uniform_points(80, 20 * np.prod(n) // 64, L, dim, dtype=dtype)
+    Gd = ib_inputs.normal_array(81, (len(Xd), ncomp), dtype=dtype)
+    plan2 = P(dim, n, L, grid="mac" if mac else "cc", dtype=tdt, ncomp=ncomp, max_points=len(Xd), compensated=comp)
+    fd = host(plan2.spread(dev(Xd), dev(Gd), compensated=comp))
+    f_ref2, fabs2 = orc.spread(g, Xd, Gd)
+    assert_spread_close(fd, f_ref2, fabs2, rel, floor)
+
+
+@pytest.mark.parametrize("mac", [True, False], ids=["mac", "cc"])
+def test_offsets_near_half_cells_origin_and_negative(P, orc, mac):
+    """Positions whose half-staggered offsets are small or whose cell map runs
+    through negative or sub-quarter-cell products: half-cell positions and their
+    float neighbours, tiny and negative coordinates; each point alone in the box,
+    so every node holds a single contribution and its relative error shows."""
+    n = (16, 16, 16)
+    h = 1.0 / 16
+    base = []
+    for k in (0, 1, 5):
+        for frac in (0.5, 0.25, 0.75, 1e-3, 0.999):
+            x = np.float32((k + frac) * h)
+            base += [x, np.nextafter(x, np.float32(0)), np.nextafter(x, np.float32(1))]
+    base += [np.float32(v) for v in (1e-7, 3e-9, -1e-7, -0.3 * h, -0.5 * h, -0.7 * h, -1.5 * h, -2.5 * h)]
+    vals = np.array(base, np.float32)
+    for i, x in enumerate(vals):        # one point per call: nodes are never shared
+        X = np.array([[x, vals[(i + 7) % len(vals)], vals[(i + 13) % len(vals)]]], np.float32)
+        G = np.array([[1.0, -2.0, 0.5]], np.float32)
+        plan = P(3, n, (1.0, 1.0, 1.0), grid="mac" if mac else "cc", max_points=1)
+        f = host(plan.spread(dev(X), dev(G)))
+        g = orc.Grid(dim=3, n=n, L=(1.0, 1.0, 1.0), mac=mac)
+        f_ref, fabs = orc.spread(g, X, G)
+        assert_spread_close(f, f_ref, fabs, what=f"spread of X = {X[0].tolist()}")

@@ -8,8 +8,11 @@ Lagrangian points processed per second by that spread + interpolate pair.
 
 Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
 the launching stream; L2 is flushed (256 MB write) between timed steps,
-outside the events.  Per-call events give the per-kernel durations used for
-the roofline.  `e2e` repeats the step through the same C ABI with host
+outside the events.  The timed step is one CUDA graph replay of the same
+calls (captured once per force buffer, so the forces change every step;
+--no-graph times the separate calls instead).  A first pass of W + K steps as
+separate calls gives the per-call durations used for the breakdown and the
+roofline.  `e2e` repeats the step through the same C ABI with host
 buffers: X and G copied in from pinned memory and U, f and the new X copied
 back, inside the timed region.
 
@@ -58,6 +61,8 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=384, help="jobs of the served-batch measurement (0: skip)")
     ap.add_argument("--serve-loads", default="0.9,2.0",
                     help="offered loads as multiples of the one-job loop's capacity, comma separated")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time the step as separate calls instead of one CUDA graph replay")
     ap.add_argument("--membrane-reps", type=int, default=10,
                     help="timed repetitions of the clustered red-cell membrane workload (0: skip)")
     ap.add_argument("--paper-reps", type=int, default=3,
@@ -436,8 +441,7 @@ def run_ours(args):
     sampler = ClockSampler(gpu_id)
     sampler.start()
 
-    def one_step(s, e=None):
-        G = Gs[s % len(Gs)]
+    def raw_step(G, e=None):
         if e is not None:
             e[0].record(stream)
         plan.bin(X, stream=stream)
@@ -453,6 +457,38 @@ def run_ours(args):
         if e is not None:
             e[4].record(stream)
 
+    # ---- the step as separate calls: per-call times (roofline, breakdown) ----
+    plain_ms = []
+    with torch.cuda.stream(stream):
+        for s in range(nsteps):
+            flush.fill_(s & 0xFF)                    # L2 flush, outside the timed events
+            e = [ev() for _ in range(5)]
+            raw_step(Gs[s % len(Gs)], e)
+            if s >= args.warmup:
+                e[4].synchronize()
+                plain_ms.append(e[0].elapsed_time(e[4]))
+                for i, k in enumerate(names):
+                    per_call[k].append(e[i].elapsed_time(e[i + 1]))
+    torch.cuda.synchronize()
+
+    # ---- the step as one CUDA graph (the same launches, captured once per force
+    # buffer so the forces still change every step) ----
+    graphs = []
+    if not args.no_graph:
+        with torch.cuda.stream(stream):
+            for G in Gs:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    raw_step(G)
+                graphs.append(g)
+        torch.cuda.synchronize()
+
+    def one_step(s):
+        if graphs:
+            graphs[s % len(graphs)].replay()
+        else:
+            raw_step(Gs[s % len(Gs)])
+
     t_begin = t_end = time.time()
     extra_steps = 0
     with torch.cuda.stream(stream):
@@ -464,13 +500,13 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 t_begin = time.time()
             flush.fill_(s & 0xFF)                    # L2 flush, outside the timed events
-            e = [ev() for _ in range(5)]
-            one_step(s, e)
+            a, b = ev(), ev()
+            a.record(stream)
+            one_step(s)
+            b.record(stream)
             if timed:
-                e[4].synchronize()
-                step_ms.append(e[0].elapsed_time(e[4]))
-                for i, k in enumerate(names):
-                    per_call[k].append(e[i].elapsed_time(e[i + 1]))
+                b.synchronize()
+                step_ms.append(a.elapsed_time(b))
         torch.cuda.synchronize()
         # nvidia-smi samples every 50 ms: a timed region shorter than that is
         # sampled over a window extended by untimed repeats of the same step.
@@ -590,6 +626,8 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "calls_ms": mean_ms,
+            "step_ms_as_separate_calls": statistics.mean(plain_ms) if plain_ms else None,
+            "step_as_cuda_graph": bool(graphs),
             "serving": serving,
             "membranes": membranes,
             "paper_algorithms": paper}

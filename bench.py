@@ -67,6 +67,8 @@ def parse():
                     help="timed repetitions of the clustered red-cell membrane workload (0: skip)")
     ap.add_argument("--paper-reps", type=int, default=3,
                     help="timed repetitions of the paper's spreading algorithms 4-6 on the workload (0: skip)")
+    ap.add_argument("--ib-step-reps", type=int, default=10,
+                    help="timed repetitions of the full IB timestep (a)-(g) with the Stokes solve (0: skip)")
     return ap.parse_args()
 
 
@@ -399,6 +401,61 @@ def membrane_bench(device, stream, reps: int, peak: float, seed: int = 0, N: int
             "note": "spread + interpolate pair (compensated spread, binning included)"}
 
 
+def ib_step_bench(device, stream, X0, ud, G, reps: int, peak: float, N: int, dt: float,
+                  rho: float = 1.0, mu: float = 1.0e-2):
+    """The full IB timestep (Section 2, steps (a)-(g)) on the bench workload:
+    bin + interpolate, advect, bin + spread the given forces (step (c), the
+    elastic model, is outside the library: the forces are a fixed buffer),
+    the periodic Stokes solve, interpolate, advect.  CUDA events on the
+    stream, L2 flushed before each timed step; the Stokes solve is also timed
+    alone, against its algorithmic bytes (read f and u_old, write u)."""
+    import torch
+    from paper_2012_06646_gb300.step import IBStep
+    npts = X0.shape[0]
+    stepper = IBStep(3, (N, N, N), (1.0, 1.0, 1.0), rho, mu, dt, max_points=npts, device=device)
+    X = X0.clone()
+    Xo = torch.empty_like(X)
+    u_a = ud.clone()
+    u_b = torch.empty_like(ud)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    step_ms, solve_ms = [], []
+    with torch.cuda.stream(stream):
+        for r in range(reps + 2):
+            flush.fill_(r & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stepper.step(X, u_a, lambda Xs: G, X_out=Xo, u_out=u_b, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if r >= 2:
+                step_ms.append(a.elapsed_time(b))
+            X, Xo = Xo, X
+            u_a, u_b = u_b, u_a
+        f = torch.empty_like(ud).normal_()
+        for r in range(reps + 2):
+            flush.fill_(r & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stepper.fluid.solve(f, u_a, rho / dt, mu, u=u_b, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if r >= 2:
+                solve_ms.append(a.elapsed_time(b))
+    stepper.plan_n.check(stream)
+    stepper.plan_s.check(stream)
+    stepper.close()
+    solve_bytes = 3 * 3 * N ** 3 * 4
+    sm = statistics.mean(solve_ms)
+    return {"workload": f"{N}^3 MAC grid, {npts} points, FP32; per step (a) bin + interpolate, (b) advect, "
+                        "(d) bin + spread (forces given), (e) Stokes solve (rho 1, mu 0.01, k = bench dt), "
+                        "(f) interpolate, (g) advect",
+            "step_ms": statistics.mean(step_ms), "pts_per_s": npts / (statistics.mean(step_ms) / 1e3),
+            "stokes_solve_ms": sm,
+            "stokes_roofline": {"bound": "hbm", "achieved_gbs": solve_bytes / (sm / 1e3) / 1e9, "peak": peak,
+                                "frac": solve_bytes / (sm / 1e3) / 1e9 / peak, "algorithmic_bytes": solve_bytes,
+                                "note": "f, u_old read and u written once; the transforms' own passes not counted"}}
+
+
 def run_ours(args):
     import torch
 
@@ -576,6 +633,14 @@ def run_ours(args):
         except Exception as exc:
             paper = {"error": repr(exc)}
 
+    ibstep = None
+    if args.ib_step_reps > 0 and rank == 0:
+        try:
+            ibstep = ib_step_bench(device, stream, torch.from_numpy(X0).to(device), ud, Gs[0], args.ib_step_reps,
+                                   load_peaks()[0], N, dt)
+        except Exception as exc:
+            ibstep = {"error": repr(exc)}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -630,7 +695,8 @@ def run_ours(args):
             "step_as_cuda_graph": bool(graphs),
             "serving": serving,
             "membranes": membranes,
-            "paper_algorithms": paper}
+            "paper_algorithms": paper,
+            "ib_step": ibstep}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -297,6 +297,46 @@ ib_status ib_batch_check(ib_batch batch, void* stream);
 ib_status ib_interpolate_noalloc(const ib_plan_desc* desc, long long npts, const void* X, const void* u, void* U,
                                  void* stream);
 
+/* ---------------------------------------------------------------------------
+ * The Eulerian step (e) of the IB timestep (Section 2, the step list (a)-(g))
+ * on the periodic MAC grid, in its Stokes limit: the convective term of the
+ * Navier-Stokes momentum equation is dropped, the viscous term is taken
+ * backward Euler and incompressibility is enforced by an exact discrete
+ * projection (on a periodic grid the projection of the paper's fluid solver
+ * is exact).  Solves, for u and a cell-centred pressure p,
+ *     (rho/k) u + G p - mu L u = (rho/k) u_old + f,     D u = 0,
+ * with D the face-to-cell-centre divergence (forward differences), G = -D^T
+ * the cell-centre-to-face gradient and L = sum_b of the 3-point second
+ * difference along b, every component on its own staggered grid (component a
+ * at x - h e_a / 2 for the cell centres x, as the spreading of a MAC plan).
+ * The mean of u is (rho/k) mean(u_old) + mean(f), divided by rho/k (0 when
+ * rho/k = 0: the steady Stokes problem, whose mean is undetermined).  The
+ * solve is cuFFT real-to-complex transforms and one kernel of per-mode
+ * arithmetic.  Paper counterpart: the fluid solver the paper uses (a
+ * first-order IMEX Runge-Kutta step with projection) is outside the paper's
+ * parallel algorithms; this is the periodic Stokes form of it.
+ * ------------------------------------------------------------------------- */
+typedef struct ib_stokes_s* ib_stokes;
+
+/* Plans the transforms for the grid `desc` (dim, n, L, dtype; grid must be
+ * IB_GRID_MAC with ncomp == dim, every n_b >= 2 and n0 n1 n2 <= 2^31;
+ * kernel, max_points and flags are not used)
+ * and allocates the scratch: the right-hand side and the complex modes, about
+ * 2 ncomp n0 n1 n2 entries of the dtype.  Errors: IB_ERR_INVALID_ARG,
+ * IB_ERR_OOM, IB_ERR_CUDA (a cuFFT plan failed). */
+ib_status ib_stokes_create(const ib_plan_desc* desc, ib_stokes* out);
+
+/* Enqueues one solve on `stream`.  f, u_old (may be NULL: zero) read and u
+ * written, each [ncomp][n2][n1][n0] device arrays of the dtype owned by the
+ * caller; u may alias u_old but not f.  rho_over_k >= 0 (density over time
+ * step), mu >= 0 (viscosity), not both 0, finite, else IB_ERR_INVALID_ARG.
+ * Solves on one stream at a time per object (they share its scratch). */
+ib_status ib_stokes_solve(ib_stokes solver, const void* f, const void* u_old, void* u, double rho_over_k,
+                          double mu, void* stream);
+
+/* Synchronises the device, releases the plans and scratch; NULL is a no-op. */
+ib_status ib_stokes_destroy(ib_stokes solver);
+
 /* Human-readable name of a status code (static storage). */
 const char* ib_status_string(ib_status status);
 

@@ -18,7 +18,7 @@ def load():
 
 
 def __getattr__(name):
-    if name in ("Plan", "Batch"):
+    if name in ("Plan", "Batch", "Stokes"):
         from . import plan
         return getattr(plan, name)
     raise AttributeError(name)

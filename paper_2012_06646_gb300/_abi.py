@@ -98,6 +98,9 @@ SIGNATURES = {
     "ib_batch_check": (_st, [_vp, _vp]),
     "ib_batch_run_host": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_host_job), _vp]),
     "ib_interpolate_noalloc": (_st, [ctypes.POINTER(ib_plan_desc), _ll, _vp, _vp, _vp, _vp]),
+    "ib_stokes_create": (_st, [ctypes.POINTER(ib_plan_desc), ctypes.POINTER(_vp)]),
+    "ib_stokes_solve": (_st, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
+    "ib_stokes_destroy": (_st, [_vp]),
     "ib_status_string": (ctypes.c_char_p, [_st]),
     "ib_version": (ctypes.c_char_p, []),
 }

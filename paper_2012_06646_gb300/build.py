@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libibgb.so")
-SOURCES = ["ib_bin.cu", "ib_ops.cu", "ib_paper.cu", "ib_api.cu"]
+SOURCES = ["ib_bin.cu", "ib_ops.cu", "ib_paper.cu", "ib_fluid.cu", "ib_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -64,7 +64,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = SO + f".tmp{os.getpid()}"
-    res = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs], capture_output=True, text=True)
+    # cuFFT (the Stokes solve) is linked dynamically, found through the
+    # toolkit's library directory when the loader path lacks it.
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    res = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcufft", "-Xlinker", f"-rpath={cudalib}"],
+                         capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{res.stdout}\n{res.stderr}")
     os.replace(tmp, SO)

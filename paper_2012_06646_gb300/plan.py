@@ -200,6 +200,67 @@ class Plan:
             pass
 
 
+class Stokes:
+    """An `ib_stokes`: the periodic MAC-grid Stokes solve of the IB step (e).
+
+    `solve(f, u_old, rho_over_k, mu)` returns u with (rho/k) u + G p - mu L u = (rho/k) u_old + f
+    and D u = 0; fields have the Plan grid shape (dim, n2, n1, n0) / (dim, n1, n0).
+    """
+
+    def __init__(self, dim: int, n, L, dtype=torch.float32, device=None):
+        self.lib = _abi.load()
+        self.dim = int(dim)
+        self.n = tuple(int(v) for v in n)[: self.dim]
+        self.L = tuple(float(v) for v in L)[: self.dim]
+        self.dtype = dtype
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        d = _abi.ib_plan_desc()
+        d.dim = self.dim
+        for b in range(3):
+            d.n[b] = self.n[b] if b < self.dim else 1
+            d.L[b] = self.L[b] if b < self.dim else 1.0
+        d.grid = _abi.IB_GRID_MAC
+        d.kernel = _abi.IB_KERNEL_PESKIN4
+        d.dtype = _DTYPES[dtype]
+        d.ncomp = self.dim
+        self.desc = d
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.ib_stokes_create(ctypes.byref(d), ctypes.byref(h)), "ib_stokes_create")
+        self.handle = h
+
+    def grid_shape(self):
+        return (self.dim,) + tuple(reversed(self.n))
+
+    def _check(self, t, name):
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous tensor of the solver's dtype on its device")
+        if tuple(t.shape) != self.grid_shape():
+            raise ValueError(f"{name} must have shape {self.grid_shape()}, got {tuple(t.shape)}")
+
+    def solve(self, f, u_old=None, rho_over_k: float = 1.0, mu: float = 1.0, u=None, stream=None):
+        self._check(f, "f")
+        if u_old is not None:
+            self._check(u_old, "u_old")
+        if u is None:
+            u = torch.empty(self.grid_shape(), dtype=self.dtype, device=self.device)
+        self._check(u, "u")
+        check(self.lib.ib_stokes_solve(self.handle, _ptr(f), _ptr(u_old), _ptr(u), float(rho_over_k), float(mu),
+                                       _stream_ptr(stream)), "ib_stokes_solve")
+        return u
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.ib_stokes_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """An `ib_batch`: one wave of independent spread + interpolate jobs per `run` call."""
 

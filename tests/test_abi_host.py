@@ -71,6 +71,21 @@ def test_footprint_and_validation_on_host(abi):
     assert b"sm_103a" in lib.ib_version()
 
 
+def test_stokes_validation_on_host(abi):
+    """ib_stokes_create rejects what it cannot solve before any CUDA or cuFFT call."""
+    lib = abi.load()
+    h = ctypes.c_void_p(7)
+    bad = [dict(grid=abi.IB_GRID_CELL_CENTERED), dict(ncomp=2), dict(dim=4), dict(n=(1, 8, 8)), dict(n=(8, 8, 0)),
+           dict(L=(1.0, 0.0, 1.0)), dict(L=(1.0, float("inf"), 1.0)), dict(dtype=3), dict(n=(2048, 2048, 1024))]
+    for kw in bad:
+        assert lib.ib_stokes_create(ctypes.byref(_desc(abi, **kw)), ctypes.byref(h)) == abi.IB_ERR_INVALID_ARG, kw
+        assert h.value is None
+        h = ctypes.c_void_p(7)
+    assert lib.ib_stokes_create(None, ctypes.byref(h)) == abi.IB_ERR_INVALID_ARG
+    assert lib.ib_stokes_solve(None, None, None, None, 1.0, 1.0, None) == abi.IB_ERR_INVALID_ARG
+    assert lib.ib_stokes_destroy(None) == abi.IB_OK
+
+
 def test_batch_footprints_on_host(abi):
     lib = abi.load()
     d = abi.ib_batch_desc(dim=3, grid=abi.IB_GRID_MAC, kernel=0, dtype=0, ncomp=3, max_jobs=64,

@@ -171,8 +171,9 @@ def test_nonfinite_and_out_of_range_positions_are_reported(P, orc):
     u = ib_inputs.normal_array(4, plan.grid_shape())
     Xbad = X.copy()
     Xbad[5, 1] = np.nan
-    f = plan.spread(dev(Xbad), dev(G))
-    U = plan.interpolate(dev(Xbad), dev(u), reuse_bins=True)
+    Xbad_d = dev(Xbad)                 # one device array: reuse_bins requires the X that was binned
+    f = plan.spread(Xbad_d, dev(G))
+    U = plan.interpolate(Xbad_d, dev(u), reuse_bins=True)
     with pytest.raises(IBError) as e:
         plan.check()
     assert e.value.status == IB_ERR_NONFINITE

@@ -55,7 +55,7 @@ class Grid:
     n: tuple
     L: tuple
     mac: bool = True
-    kernel: int = 0          # 0 = standard 4-point, 1 = cosine
+    kernel: int = 0          # 0 = standard 4-point, 1 = cosine, 2 = 3-point, 3 = 6-point B-spline
     ncomp: int | None = None
 
     @property
@@ -95,6 +95,8 @@ def lib():
         L.or_phi.argtypes = [ctypes.c_int, ctypes.c_double]
         L.or_dphi.restype = ctypes.c_double
         L.or_dphi.argtypes = [ctypes.c_int, ctypes.c_double]
+        L.or_width.restype = ctypes.c_int
+        L.or_width.argtypes = [ctypes.c_int]
         L.or_cell.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_longlong), dp]
         L.or_cell_keys.argtypes = [ctypes.POINTER(_Grid), ctypes.c_longlong, dp, ctypes.POINTER(ctypes.c_ulonglong)]
@@ -120,6 +122,11 @@ def _f64(a) -> np.ndarray:
 def phi(kernel: int, r) -> np.ndarray:
     r = np.atleast_1d(np.asarray(r, dtype=np.float64))
     return np.array([lib().or_phi(kernel, float(x)) for x in r.ravel()]).reshape(r.shape)
+
+
+def width(kernel: int) -> int:
+    """Support width s of the kernel (Section 3.1)."""
+    return int(lib().or_width(int(kernel)))
 
 
 def dphi(kernel: int, r) -> np.ndarray:

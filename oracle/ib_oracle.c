@@ -23,7 +23,52 @@ void or_set_mutation(int m) { g_mutation = m; }
  *   outer branch: multiply and divide by (5 - 2|r| + sqrt(...)); the
  *     numerator (5 - 2|r|)^2 - (-7 + 12|r| - 4r^2) equals 8 (2 - |r|)^2;
  *   cosine: 1 + cos(2 y) = 2 cos(y)^2 with y = pi r / 4. */
+/* Kernels of other support widths (the methods of the paper do not depend on
+ * phi, Section 2; s[phi] of Section 3.1 is 3 and 6 for these):
+ * 3-point (Roma, Peskin and Berger 1999), s = 3:
+ *   (1 + sqrt(1 - 3 r^2)) / 3                   on |r| <= 1/2,
+ *   (5 - 3|r| - sqrt(1 - 3 (1 - |r|)^2)) / 6    on 1/2 <= |r| <= 3/2, else 0;
+ *   the outer branch is evaluated as (3 - 2|r|)^2 / (2 (5 - 3|r| + sqrt(...))),
+ *   the same value without the cancellation near |r| = 3/2 (the numerator
+ *   (5 - 3|r|)^2 - (1 - 3 (1 - |r|)^2) equals 3 (3 - 2|r|)^2).
+ * 6-point B-spline (the centred quintic B-spline, six-fold convolution of the
+ * unit box), s = 6, as its piecewise polynomial on |r| in [0,1), [1,2), [2,3):
+ *   (66 - 60 r^2 + 30 r^4 - 10 |r|^5) / 120,
+ *   (1 + 5c + 10c^2 + 10c^3 + 5c^4 - 5c^5) / 120 with c = 2 - |r|,
+ *   (3 - |r|)^5 / 120, else 0;
+ *   the middle piece is written in c = 2 - |r| so that it has no cancellation
+ *   as |r| -> 2 (the same polynomial as the power form in |r|). */
+static double phi_roma3(double r) {
+  double a = fabs(r);
+  if (a >= 1.5) return 0.0;
+  if (a <= 0.5) return (1.0 + sqrt(1.0 - 3.0 * a * a)) / 3.0;
+  double q = sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a));
+  return (3.0 - 2.0 * a) * (3.0 - 2.0 * a) / (2.0 * (5.0 - 3.0 * a + q));
+}
+
+static double phi_bspline6(double r) {
+  double a = fabs(r);
+  if (a >= 3.0) return 0.0;
+  if (a >= 2.0) {
+    double c = 3.0 - a;
+    return c * c * c * c * c / 120.0;
+  }
+  if (a >= 1.0) {
+    double c = 2.0 - a;
+    return (1.0 + 5.0 * c + 10.0 * c * c + 10.0 * c * c * c + 5.0 * c * c * c * c - 5.0 * c * c * c * c * c) / 120.0;
+  }
+  return (66.0 - 60.0 * a * a + 30.0 * a * a * a * a - 10.0 * a * a * a * a * a) / 120.0;
+}
+
+int or_width(int kernel) {
+  if (kernel == 2) return 3;
+  if (kernel == 3) return 6;
+  return 4;
+}
+
 double or_phi(int kernel, double r) {
+  if (kernel == 2) return phi_roma3(r);
+  if (kernel == 3) return phi_bspline6(r);
   double a = fabs(r);
   if (a >= 2.0) return 0.0;
   if (kernel == 1) {
@@ -37,6 +82,7 @@ double or_phi(int kernel, double r) {
 
 /* d phi / d r of the same formulas (both kernels are C^1 on the real line). */
 double or_dphi(int kernel, double r) {
+  if (kernel >= 2) return NAN;   /* position gradients are defined for the 4-point kernels only */
   double a = fabs(r);
   double sgn = (r < 0.0) ? -1.0 : 1.0;
   if (a >= 2.0) return 0.0;
@@ -80,6 +126,7 @@ static int check_grid(const or_grid* g) {
     if (g->n[b] < 1 || !(g->L[b] > 0.0)) return 1;
   if (g->ncomp < 1) return 1;
   if (g->grid == 1 && g->ncomp != g->dim) return 1;
+  if (g->kernel < 0 || g->kernel > 3) return 1;
   return 0;
 }
 
@@ -135,12 +182,34 @@ static void point_cell(const or_grid* g, const double* Xj, int comp, cellrec* c)
   }
 }
 
+/* Nodes i + t examined around the cell i = floor(u) of a point, per
+ * dimension: every node whose weight phi(t - r) can be nonzero for some
+ * r in [0, 1), i.e. |t - r| < s/2.  Even s: t in [1 - s/2, s/2] (s nodes,
+ * {-1, 0, 1, 2} for s = 4); odd s: t in [(1 - s)/2, (1 + s)/2] (s + 1 nodes,
+ * one of which has weight 0 for any given r). */
+static int window_lo(int kernel) {
+  int s = or_width(kernel);
+  return (s % 2 == 0) ? 1 - s / 2 : (1 - s) / 2;
+}
+
+static int window_n(int kernel) {
+  int s = or_width(kernel);
+  return (s % 2 == 0) ? s : s + 1;
+}
+
+static int nshift_of(const or_grid* g) {
+  int w = window_n(g->kernel), m = 1;
+  for (int b = 0; b < g->dim; ++b) m *= w;
+  return m;
+}
+
 /* Shift number s (0-based) in colexicographic order, x fastest (Algorithm 1 with
- * the digits of s read base 4), mapped to t in {-1, 0, 1, 2}. */
-static void shift_of(int s, int dim, int* t) {
-  for (int b = 0; b < dim; ++b) {
-    t[b] = (s % 4) - 1;
-    s /= 4;
+ * the digits of s read base w, the window size), mapped to t = digit + window_lo. */
+static void shift_of(const or_grid* g, int s, int* t) {
+  int w = window_n(g->kernel), lo = window_lo(g->kernel);
+  for (int b = 0; b < g->dim; ++b) {
+    t[b] = (s % w) + lo;
+    s /= w;
   }
 }
 
@@ -165,7 +234,7 @@ static double inv_cell_volume(const or_grid* g) {
 int or_spread(const or_grid* g, long long n, const double* X, const double* G, double* f, double* fabs_out) {
   if (check_grid(g)) return 1;
   long long ncell = ncell_of(g);
-  int nshift = (g->dim == 3) ? 64 : 16;
+  int nshift = nshift_of(g);
   double hmd = (g_mutation == 1) ? 1.0 : inv_cell_volume(g);
   memset(f, 0, sizeof(double) * (size_t)(ncell * g->ncomp));
   if (fabs_out) memset(fabs_out, 0, sizeof(double) * (size_t)(ncell * g->ncomp));
@@ -175,7 +244,7 @@ int or_spread(const or_grid* g, long long n, const double* X, const double* G, d
       point_cell(g, X + j * g->dim, a, &c);
       for (int s = 0; s < nshift; ++s) {       /* loop over shifts */
         int t[3];
-        shift_of(s, g->dim, t);
+        shift_of(g, s, t);
         double w = 1.0;
         for (int b = 0; b < g->dim; ++b) w *= or_phi(g->kernel, karg(t[b], c.r[b]));
         long long k = node_index(g, &c, t);
@@ -191,7 +260,7 @@ int or_spread(const or_grid* g, long long n, const double* X, const double* G, d
 int or_interp(const or_grid* g, long long n, const double* X, const double* u, double* U, double* Uabs) {
   if (check_grid(g)) return 1;
   long long ncell = ncell_of(g);
-  int nshift = (g->dim == 3) ? 64 : 16;
+  int nshift = nshift_of(g);
   for (long long j = 0; j < n; ++j) {          /* one independent row of S* per point (Algorithm 3) */
     for (int a = 0; a < g->ncomp; ++a) {
       cellrec c;
@@ -199,7 +268,7 @@ int or_interp(const or_grid* g, long long n, const double* X, const double* u, d
       double acc = 0.0, aabs = 0.0;
       for (int s = 0; s < nshift; ++s) {
         int t[3];
-        shift_of(s, g->dim, t);
+        shift_of(g, s, t);
         double w = 1.0;
         for (int b = 0; b < g->dim; ++b) w *= or_phi(g->kernel, karg(t[b], c.r[b]));
         double term = w * u[a * ncell + node_index(g, &c, t)];
@@ -217,7 +286,7 @@ int or_pos_grad(const or_grid* g, long long n, const double* X, const double* fi
                 double* D, double* Dabs) {
   if (check_grid(g)) return 1;
   long long ncell = ncell_of(g);
-  int nshift = (g->dim == 3) ? 64 : 16;
+  int nshift = nshift_of(g);
   for (long long j = 0; j < n; ++j) {
     for (int b = 0; b < g->dim; ++b) {
       double acc = 0.0, aabs = 0.0;
@@ -229,7 +298,7 @@ int or_pos_grad(const or_grid* g, long long n, const double* X, const double* fi
         point_cell(g, X + j * g->dim, a, &c);
         for (int s = 0; s < nshift; ++s) {
           int t[3];
-          shift_of(s, g->dim, t);
+          shift_of(g, s, t);
           double w = chain * or_dphi(g->kernel, karg(t[b], c.r[b]));
           for (int e = 0; e < g->dim; ++e)
             if (e != b) w *= or_phi(g->kernel, karg(t[e], c.r[e]));

@@ -19,7 +19,11 @@
  *   - Cell of a point X for staggering xi: i = floor(X/h - xi), offset
  *     r = X/h - xi - i in [0, 1), with X/h evaluated as X * (N/L) in FP64.
  *   - Support nodes are i + t for t in {-1, 0, 1, 2} per dimension, weight
- *     prod_b phi(t_b - r_b) (Eq. delta-defs with the lower-corner cell of Fig. 1a).
+ *     prod_b phi(t_b - r_b) (Eq. delta-defs with the lower-corner cell of Fig. 1a),
+ *     for the 4-point kernels.  For a kernel of support width s the nodes
+ *     examined are every i + t with |t - r| < s/2 possible (the definition of
+ *     delta_h: phi vanishes outside), t in [1 - s/2, s/2] for even s and
+ *     [(1 - s)/2, (1 + s)/2] for odd s.
  *   - Periodic box: node indices wrap modulo N in every dimension.
  *   - MAC grid (Section 2): component a has xi_a = 0 and xi_b = 1/2 for b != a.
  *     Cell-centred grid: xi_b = 1/2 for every component.
@@ -44,13 +48,18 @@ typedef struct {
   int n[3];      /* grid points per dimension (n[2] ignored when dim == 2) */
   double L[3];   /* box side per dimension */
   int grid;      /* 0 = cell-centred, 1 = MAC (requires ncomp == dim) */
-  int kernel;    /* 0 = standard 4-point (Peskin 2002), 1 = cosine 4-point */
+  int kernel;    /* 0 = standard 4-point (Peskin 2002), 1 = cosine 4-point,
+                    2 = 3-point (Roma, Peskin, Berger 1999), 3 = 6-point quintic B-spline */
   int ncomp;     /* components of the spread / interpolated field */
 } or_grid;
 
-/* 1-D kernel phi(r) and its derivative (Section 2; kernels of Peskin 2002). */
+/* 1-D kernel phi(r) and its derivative (Section 2; kernels of Peskin 2002 and
+ * the 3- and 6-point kernels above; the derivative is NaN for those two). */
 double or_phi(int kernel, double r);
 double or_dphi(int kernel, double r);
+
+/* Support width s[phi] of Section 3.1: 4, 4, 3, 6 for kernels 0 .. 3. */
+int or_width(int kernel);
 
 /* Cell map of Fig. 1 / Section 3.1: u = X*scale - xi, i = floor(u), r = u - i. */
 void or_cell(double X, double scale, double xi, long long* i, double* r);

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from conftest import read_golden
-from _dense import dense_S, phi_cos, phi_std
+from _dense import dense_S, phi_bspline6, phi_cos, phi_roma3, phi_std
 
 import ib_inputs
 
@@ -63,6 +63,52 @@ def test_cosine_kernel_identities(orc):
     assert np.max(np.abs((w ** 2).sum(0) - 0.375)) < 1e-14
     first = np.max(np.abs(((t[:, None] - R_GRID[None, :]) * w).sum(0)))
     assert 0.02 < first < 0.022
+
+
+def test_other_width_kernels_closed_forms(orc):
+    """3-point kernel (Roma, Peskin, Berger 1999) and the centred quintic B-spline at exact points."""
+    roma = {0.0: 2 / 3, 0.5: 0.5, -0.5: 0.5, 1.0: 1 / 6, -1.0: 1 / 6, 1.5: 0.0, 2.0: 0.0,
+            0.25: (1 + math.sqrt(1 - 3 / 16)) / 3}
+    for r, v in roma.items():
+        assert orc.phi(2, r)[0] == pytest.approx(v, abs=1e-15), r
+    bsp = {0.0: 11 / 20, 0.5: 841 / 1920, -0.5: 841 / 1920, 1.0: 13 / 60, -1.0: 13 / 60, 1.5: 237 / 3840,
+           2.0: 1 / 120, -2.0: 1 / 120, 2.5: 1 / 3840, 3.0: 0.0, -3.5: 0.0}
+    for r, v in bsp.items():
+        assert orc.phi(3, r)[0] == pytest.approx(v, abs=1e-15), r
+    assert [orc.width(k) for k in range(4)] == [4, 4, 3, 6]
+
+
+def _moments_w(orc, kernel, lo, hi):
+    t = np.arange(lo, hi + 1, dtype=np.float64)
+    w = np.stack([orc.phi(kernel, tt - R_GRID) for tt in t])
+    return t, w
+
+
+def test_roma3_identities(orc):
+    """Partition of unity, zero first moment and sum of squares 1/2 for every offset."""
+    t, w = _moments_w(orc, 2, -2, 3)
+    d = t[:, None] - R_GRID[None, :]
+    assert np.max(np.abs(w.sum(0) - 1.0)) < 1e-14
+    assert np.max(np.abs((d * w).sum(0))) < 1e-14
+    assert np.max(np.abs((w ** 2).sum(0) - 0.5)) < 1e-14
+    assert np.all((w > 0).sum(0) <= 3)                       # at most s = 3 nonzero weights
+
+
+def test_bspline6_identities(orc):
+    """Partition of unity; moments 0, 1/2, 0 of orders 1-3 (the variance of a sum of six unit boxes)."""
+    t, w = _moments_w(orc, 3, -3, 4)
+    d = t[:, None] - R_GRID[None, :]
+    assert np.max(np.abs(w.sum(0) - 1.0)) < 1e-14
+    assert np.max(np.abs((d * w).sum(0))) < 1e-14
+    assert np.max(np.abs((d * d * w).sum(0) - 0.5)) < 1e-13
+    assert np.max(np.abs((d ** 3 * w).sum(0))) < 1e-13
+    assert np.all((w > 0).sum(0) <= 6)
+
+
+def test_other_width_kernels_match_independent_copies(orc):
+    r = np.linspace(-3.4, 3.4, 1361)
+    assert np.max(np.abs(orc.phi(2, r) - phi_roma3(r))) < 1e-15
+    assert np.max(np.abs(orc.phi(3, r) - phi_bspline6(r))) < 1e-15
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -155,6 +201,12 @@ CASES = [
     (3, (4, 5, 6), (1.0, 1.1, 0.9), True, 0, 3),
     (3, (5, 4, 4), (2.0, 1.0, 1.0), False, 1, 2),
     (3, (2, 3, 4), (1.0, 1.0, 1.0), True, 0, 3),
+    (2, (7, 5), (1.0, 0.9), True, 2, 2),
+    (2, (6, 9), (1.1, 1.0), False, 3, 2),
+    (2, (1, 3), (1.0, 1.0), False, 2, 1),
+    (3, (5, 4, 6), (1.0, 0.8, 1.2), True, 2, 3),
+    (3, (7, 6, 5), (1.0, 1.0, 0.9), True, 3, 3),
+    (3, (2, 3, 4), (1.0, 1.0, 1.0), False, 3, 1),
 ]
 
 
@@ -179,7 +231,7 @@ def test_spread_and_interp_equal_dense_operator(orc, dim, n, L, mac, kernel, nco
 
 # ------------------------------------------------------------ invariants --
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("mac", [True, False])
 def test_conservation_of_force(orc, kernel, mac):
     """sum_k f_a[k] h^d = sum_j G_{j,a}, from partition of unity."""
@@ -192,7 +244,7 @@ def test_conservation_of_force(orc, kernel, mac):
     assert np.max(np.abs(tot - G.sum(0))) <= 1e-13 * np.abs(G).sum()
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_interpolates_constants(orc, kernel):
     g = orc.Grid(dim=3, n=(8, 8, 8), L=(1.0, 1.0, 1.0), mac=True, kernel=kernel)
     X = ib_inputs.uniform_points(21, 200, g.L, 3, dtype=np.float64)
@@ -201,11 +253,13 @@ def test_interpolates_constants(orc, kernel):
     assert np.max(np.abs(U - np.array([1.5, -2.0, 0.25]))) < 1e-14
 
 
+@pytest.mark.parametrize("kernel", [0, 2, 3])
 @pytest.mark.parametrize("mac", [True, False])
-def test_interpolates_linears_exactly_standard_kernel(orc, mac):
-    """Zero first moment makes the standard kernel exact on alpha + beta . x (away from the periodic seam)."""
+def test_interpolates_linears_exactly(orc, mac, kernel):
+    """Zero first moment makes the standard, 3-point and B-spline kernels exact on alpha + beta . x
+    (away from the periodic seam)."""
     n, L = (16, 12, 20), (1.0, 0.75, 1.25)
-    g = orc.Grid(dim=3, n=n, L=L, mac=mac, kernel=0)
+    g = orc.Grid(dim=3, n=n, L=L, mac=mac, kernel=kernel)
     h = np.array(L) / np.array(n)
     X = 3 * h + ib_inputs.uniform_points(22, 300, np.array(L) - 6 * h, 3, dtype=np.float64)
     alpha, beta = np.array([0.3, -1.1, 2.0]), np.array([[1.0, -2.0, 0.5], [0.2, 0.7, -1.3], [-0.4, 0.1, 0.9]])
@@ -220,7 +274,7 @@ def test_interpolates_linears_exactly_standard_kernel(orc, mac):
     assert np.max(np.abs(U - want)) < 1e-13
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_adjointness(orc, kernel):
     """<S G, u>_h = h^d sum_k f_k u_k equals <G, S* u>_L = sum_j G_j U_j (spec: 1e-12)."""
     g = orc.Grid(dim=3, n=(12, 10, 8), L=(1.2, 1.0, 0.8), mac=True, kernel=kernel)
@@ -290,7 +344,7 @@ def _pins_pass(orc):
         test_conservation_of_force(orc, 0, True)
         test_spread_and_interp_equal_dense_operator(orc, *CASES[5])
         test_spread_and_interp_equal_dense_operator(orc, *CASES[1])
-        test_interpolates_linears_exactly_standard_kernel(orc, True)
+        test_interpolates_linears_exactly(orc, True, 0)
         test_position_gradients_match_central_differences(orc, 0)
     except AssertionError:
         return False
@@ -318,3 +372,17 @@ def test_kernel_tail_keeps_relative_accuracy(orc, kernel):
         lead = e * e / 2.0 if kernel == 0 else (math.pi * e / 4.0) ** 2 / 2.0
         v = orc.phi(kernel, a)[0]
         assert abs(v / lead - 1.0) < 10 * eps + 1e-12, (eps, v, lead)
+
+
+def test_other_width_kernel_tails_keep_relative_accuracy(orc):
+    """3-point: near |r| = 3/2 the weight is (3 - 2a)^2 / (2 (5 - 3a + q)) -> 2 e^2 (e = 3/2 - a);
+    B-spline: near |r| = 3 it is e^5 / 120 and near 2 the middle piece tends to 1/120 smoothly."""
+    for eps in (1e-3, 1e-6, 1e-9):
+        a = 1.5 - eps
+        e = 1.5 - a
+        v = orc.phi(2, a)[0]
+        assert abs(v / (2 * e * e) - 1.0) < 10 * eps + 1e-12, (eps, v)
+        a = 3.0 - eps
+        e = 3.0 - a
+        assert abs(orc.phi(3, a)[0] / (e ** 5 / 120) - 1.0) < 1e-12
+        assert abs(orc.phi(3, 2.0 - eps)[0] / phi_bspline6(np.array([2.0 - eps]))[0] - 1.0) < 1e-12

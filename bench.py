@@ -67,6 +67,8 @@ def parse():
                     help="timed repetitions of the clustered red-cell membrane workload (0: skip)")
     ap.add_argument("--paper-reps", type=int, default=3,
                     help="timed repetitions of the paper's spreading algorithms 4-6 on the workload (0: skip)")
+    ap.add_argument("--kernel-reps", type=int, default=10,
+                    help="timed repetitions of spread + interpolate with each other kernel (0: skip)")
     ap.add_argument("--ib-step-reps", type=int, default=10,
                     help="timed repetitions of the full IB timestep (a)-(g) with the Stokes solve (0: skip)")
     return ap.parse_args()
@@ -401,6 +403,42 @@ def membrane_bench(device, stream, reps: int, peak: float, seed: int = 0, N: int
             "note": "spread + interpolate pair (compensated spread, binning included)"}
 
 
+def kernels_bench(device, stream, X, G, u, reps: int, N: int):
+    """Bin + spread + interpolate on the bench workload with every kernel of
+    the library (support widths 4, 4, 3, 6): CUDA events on the stream, L2
+    flushed before each timed repetition."""
+    import torch
+    from paper_2012_06646_gb300.plan import Plan
+    npts = X.shape[0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    out = {}
+    for name, width in (("peskin4", 4), ("cosine4", 4), ("roma3", 3), ("bspline6", 6)):
+        plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", kernel=name, max_points=npts, device=device)
+        f = torch.empty(plan.grid_shape(), dtype=torch.float32, device=device)
+        U = torch.empty((npts, 3), dtype=torch.float32, device=device)
+        ms = {"spread": [], "interp": []}
+        with torch.cuda.stream(stream):
+            for r in range(reps + 2):
+                flush.fill_(r & 0xFF)
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                plan.spread(X, G, f=f, stream=stream)
+                e[1].record(stream)
+                plan.interpolate(X, u, U=U, reuse_bins=True, stream=stream)
+                e[2].record(stream)
+                e[2].synchronize()
+                if r >= 2:
+                    ms["spread"].append(e[0].elapsed_time(e[1]))
+                    ms["interp"].append(e[1].elapsed_time(e[2]))
+        plan.check(stream)
+        plan.close()
+        sp, it = statistics.mean(ms["spread"]), statistics.mean(ms["interp"])
+        out[name] = {"support": width, "bin_and_spread_ms": sp, "interp_ms": it,
+                     "pts_per_s": npts / ((sp + it) / 1e3)}
+    return {"workload": f"{N}^3 MAC grid, {npts} uniform points, FP32, spread (binning included) + interpolate",
+            "kernels": out}
+
+
 def ib_step_bench(device, stream, X0, ud, G, reps: int, peak: float, N: int, dt: float,
                   rho: float = 1.0, mu: float = 1.0e-2):
     """The full IB timestep (Section 2, steps (a)-(g)) on the bench workload:
@@ -633,6 +671,13 @@ def run_ours(args):
         except Exception as exc:
             paper = {"error": repr(exc)}
 
+    kern = None
+    if args.kernel_reps > 0 and rank == 0:
+        try:
+            kern = kernels_bench(device, stream, X, Gs[0], ud, args.kernel_reps, N)
+        except Exception as exc:
+            kern = {"error": repr(exc)}
+
     ibstep = None
     if args.ib_step_reps > 0 and rank == 0:
         try:
@@ -696,6 +741,7 @@ def run_ours(args):
             "serving": serving,
             "membranes": membranes,
             "paper_algorithms": paper,
+            "kernel_widths": kern,
             "ib_step": ibstep}
     print(json.dumps(line), flush=True)
     if world > 1:

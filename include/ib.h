@@ -67,7 +67,19 @@ typedef enum {
                                  the points concerned spread nothing and interpolate to NaN */
 } ib_status;
 
-enum { IB_KERNEL_PESKIN4 = 0, IB_KERNEL_COSINE4 = 1 };   /* standard 4-point / cosine 4-point phi (Section 2) */
+/* One-dimensional kernel phi of delta_h (Section 2; the methods do not depend
+ * on phi).  Support width s (Section 3.1): 4, 4, 3, 6.
+ *   IB_KERNEL_PESKIN4   standard 4-point kernel (Peskin 2002)
+ *   IB_KERNEL_COSINE4   cosine 4-point kernel (Peskin 2002), the paper's choice
+ *   IB_KERNEL_ROMA3     3-point kernel (Roma, Peskin, Berger 1999), odd s: the
+ *                       cell of a point is centred on its nearest node (Fig. 1b)
+ *   IB_KERNEL_BSPLINE6  6-point kernel: the centred quintic B-spline
+ * The 3- and 6-point kernels are available to ib_bin, ib_spread (not
+ * IB_COMPENSATED), ib_interpolate and ib_advect; ib_pos_grad and
+ * ib_spread_paper return IB_ERR_NOT_IMPLEMENTED for them, and batches, the
+ * no-alloc interpolation and IB_PLAN_COMPENSATED plans reject them
+ * (IB_ERR_INVALID_ARG). */
+enum { IB_KERNEL_PESKIN4 = 0, IB_KERNEL_COSINE4 = 1, IB_KERNEL_ROMA3 = 2, IB_KERNEL_BSPLINE6 = 3 };
 enum { IB_GRID_CELL_CENTERED = 0, IB_GRID_MAC = 1 };
 enum { IB_F32 = 0, IB_F64 = 1 };
 
@@ -90,7 +102,7 @@ typedef struct {
   int n[3];               /* grid points per dimension, each >= 1 (n[2] ignored in 2-D) */
   double L[3];            /* box side per dimension, > 0 */
   int grid;               /* IB_GRID_MAC (requires ncomp == dim) or IB_GRID_CELL_CENTERED */
-  int kernel;             /* IB_KERNEL_PESKIN4 or IB_KERNEL_COSINE4 */
+  int kernel;             /* IB_KERNEL_PESKIN4, _COSINE4, _ROMA3 or _BSPLINE6 */
   int dtype;              /* IB_F32 or IB_F64: element type of X, G, f, u, U */
   int ncomp;              /* components per field, 1..4 */
   long long max_points;   /* largest npts any call on this plan will pass, 0 <= max_points < 2^31 */

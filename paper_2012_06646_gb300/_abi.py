@@ -27,6 +27,8 @@ IB_ERR_BINS_STALE = 10
 
 IB_KERNEL_PESKIN4 = 0
 IB_KERNEL_COSINE4 = 1
+IB_KERNEL_ROMA3 = 2
+IB_KERNEL_BSPLINE6 = 3
 IB_GRID_CELL_CENTERED = 0
 IB_GRID_MAC = 1
 IB_F32 = 0

@@ -93,7 +93,9 @@ void set_tiles(Job& jb, int dim, int tile) {
 bool valid_shape(int dim, int grid, int kernel, int dtype, int ncomp) {
   if (dim != 2 && dim != 3) return false;
   if (grid != IB_GRID_MAC && grid != IB_GRID_CELL_CENTERED) return false;
-  if (kernel != IB_KERNEL_PESKIN4 && kernel != IB_KERNEL_COSINE4) return false;
+  if (kernel != IB_KERNEL_PESKIN4 && kernel != IB_KERNEL_COSINE4 && kernel != IB_KERNEL_ROMA3 &&
+      kernel != IB_KERNEL_BSPLINE6)
+    return false;
   if (dtype != IB_F32 && dtype != IB_F64) return false;
   if (ncomp < 1 || ncomp > 4) return false;
   if (grid == IB_GRID_MAC && ncomp != dim) return false;
@@ -190,6 +192,8 @@ bool plan_sizes(const ib_plan_desc* d, Job* jb, int* tp, int* tc, long long* ntp
   if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
   if (d->max_points < 0 || d->max_points > kMaxPointsTotal) return false;
   if (d->flags & ~IB_PLAN_COMPENSATED) return false;
+  const int width = kernel_width(d->kernel);
+  if (width != 4 && (d->flags & IB_PLAN_COMPENSATED)) return false;   // compensated sums: 4-point kernels
   const int tile_plain = spread_tile_side(d->dim, entry_bytes(d->dtype, false), false, d->ncomp);
   const int tile_comp = spread_tile_side(d->dim, entry_bytes(d->dtype, false), true, d->ncomp);
   Job j;
@@ -199,7 +203,7 @@ bool plan_sizes(const ib_plan_desc* d, Job* jb, int* tp, int* tc, long long* ntp
   set_tiles(j, d->dim, tile_comp);
   const long long ntc_ = j.ntiles;
   set_tiles(j, d->dim, tile_plain);
-  size_t boxes = (size_t)ntp_ * box_bytes(d->dim, tile_plain, entry_bytes(d->dtype, false), d->ncomp);
+  size_t boxes = (size_t)ntp_ * box_bytes(d->dim, tile_plain, entry_bytes(d->dtype, false), d->ncomp, width);
   if (d->flags & IB_PLAN_COMPENSATED) {
     const size_t bc = (size_t)ntc_ * box_bytes(d->dim, tile_comp, entry_bytes(d->dtype, true), d->ncomp);
     if (bc > boxes) boxes = bc;
@@ -352,6 +356,12 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   J.one.f = f;
   if (flags & IB_ADJOINT) J.one.hmd = 1.0;
   J.njobs = 1;
+  if (kernel_width(p->desc.kernel) != 4) {
+    if (launch_spread_width(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, p->desc.dtype,
+                            (flags & IB_ACCUMULATE) != 0, s) != cudaSuccess)
+      return IB_ERR_CUDA;
+    return IB_OK;
+  }
   if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp,
                     (flags & IB_ACCUMULATE) != 0, pair_aligned(p->job.n[0], f, p->desc.dtype), s) != cudaSuccess)
     return IB_ERR_CUDA;
@@ -376,6 +386,11 @@ ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u
   J.one.U = U;
   J.njobs = 1;
   const double scale = (flags & IB_ADJOINT) ? p->job.hmd : 1.0;
+  if (kernel_width(p->desc.kernel) != 4) {
+    if (launch_interp_width(J, p->sh, call_bins(p, npts), J.one.nitiles, p->desc.dtype, scale, s) != cudaSuccess)
+      return IB_ERR_CUDA;
+    return IB_OK;
+  }
   if (launch_interp(J, p->sh, call_bins(p, npts), J.one.nitiles, p->desc.dtype, scale, s) != cudaSuccess)
     return IB_ERR_CUDA;
   return IB_OK;
@@ -388,6 +403,7 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
   if (npts > 0 && (!field || !v || !D)) return IB_ERR_INVALID_ARG;
   if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
   if (!isfinite(scale)) return IB_ERR_INVALID_ARG;
+  if (kernel_width(p->desc.kernel) != 4) return IB_ERR_NOT_IMPLEMENTED;
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare(p, npts, X, flags, s);
   if (st != IB_OK) return st;
@@ -425,6 +441,7 @@ ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* 
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
+  if (kernel_width(p->desc.kernel) != 4) return IB_ERR_NOT_IMPLEMENTED;
   const int S = p->desc.dim == 3 ? 64 : 16;        // s^d shifts of the 4-point support
   if (algorithm == IB_PAPER_ALG4) {
     beta = 1;
@@ -506,6 +523,7 @@ ib_status ib_plan_bins(ib_plan p, const void** perm, const void** cell_start, lo
 
 static bool batch_sizes(const ib_batch_desc* d, int* tile, Layout* L) {
   if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
+  if (kernel_width(d->kernel) != 4) return false;     // served waves: 4-point kernels
   if ((d->flags & ~IB_BATCH_HOST_IO) || d->max_jobs < 1 || d->max_points < 0 || d->max_points > kMaxPointsTotal)
     return false;
   if (d->max_cells < 1 || d->max_cells > kMaxCellsTotal || d->max_tiles < 0) return false;
@@ -754,6 +772,7 @@ void* g_noalloc_addr[kMaxDevices] = {};
 extern "C" ib_status ib_interpolate_noalloc(const ib_plan_desc* desc, long long npts, const void* X, const void* u,
                                             void* U, void* stream) {
   if (!desc || !valid_shape(desc->dim, desc->grid, desc->kernel, desc->dtype, desc->ncomp)) return IB_ERR_INVALID_ARG;
+  if (kernel_width(desc->kernel) != 4) return IB_ERR_INVALID_ARG;
   if (desc->flags != 0 || npts < 0 || (npts > 0 && (!X || !u || !U))) return IB_ERR_INVALID_ARG;
   Job jb;
   if (!fill_job(jb, desc->dim, desc->n, desc->L, spread_tile_side(desc->dim, entry_bytes(desc->dtype, false), false,

@@ -59,7 +59,7 @@ struct Shape {
   int dim;               // 2 or 3
   int ncomp;             // components per field
   int mac;               // 1: MAC staggering, 0: cell-centred
-  int kernel;            // 0: standard 4-point, 1: cosine 4-point
+  int kernel;            // 0: standard 4-point, 1: cosine 4-point, 2: 3-point, 3: 6-point B-spline
 };
 
 // Scratch arena views (global arrays over all jobs of a wave).

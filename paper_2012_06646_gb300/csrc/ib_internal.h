@@ -12,8 +12,21 @@ namespace ibgb {
 // every component and the staging records fit in shared memory, else 8; 32 in 2-D.
 int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp);
 
-// Bytes of one spreading box (all components) for a tile side.
-size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp);
+// Bytes of one spreading box (all components) for a tile side and a kernel
+// support width s (box side tile + s).
+size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp, int width = 4);
+
+// Support width s of a kernel (Section 3.1): 4 for the 4-point kernels, 3 for
+// the 3-point kernel, 6 for the 6-point B-spline.
+int kernel_width(int kernel);
+
+// Spreading and interpolation for kernels of width s != 4 (ib_width.cu), a
+// single job: tile boxes of side TS + s, then the fixed-order combination;
+// interpolation by tiles with the box of grid values in shared memory.
+cudaError_t launch_spread_width(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles,
+                                int dtype, bool accumulate, cudaStream_t s);
+cudaError_t launch_interp_width(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, int dtype,
+                                double scale, cudaStream_t s);
 
 // Cells per block of the cell-count scan, and the number of blocks for m entries.
 constexpr long long kScanChunkCells = 8192;

@@ -1345,8 +1345,8 @@ int spread_tile_side(int dim, int elem_bytes, bool comp, int ncomp) {
   return dim == 2 ? 32 : 8;
 }
 
-size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp) {
-  const size_t side = (size_t)tile + 4;
+size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp, int width) {
+  const size_t side = (size_t)tile + (size_t)width;
   return (dim == 3 ? side * side * side : side * side) * (size_t)entry_bytes * ncomp;
 }
 

@@ -1,0 +1,509 @@
+// ib_width.cu -- spreading and interpolation for kernels whose support width
+// s (Section 3.1) is not 4: the 3-point kernel of Roma, Peskin and Berger
+// (s = 3) and the 6-point quintic B-spline (s = 6).  The methods of the paper
+// do not depend on phi (Section 2); only the cell map and the box sizes do.
+//
+// Cell map for width s (Section 3.1, Fig. 1): the cell of a point is the
+// region of points with the same s^d support nodes.  With u = X N/L - xi it is
+// bounded by grid nodes for even s (node index i = floor(u), offset
+// rho = u - i in [0, 1)) and centred on the nearest node for odd s
+// (i = floor(u + 1/2), rho = u - i in [-1/2, 1/2)).  The support nodes are
+// i + t for t in [tlo, tlo + s) with tlo = 1 - s/2 (even) or (1 - s)/2 (odd),
+// weight phi(t - rho) per dimension.  For odd s, u + 1/2 = X N/L - (xi - 1/2)
+// is the even map with the staggerings 0 and 1/2 exchanged (cell one higher
+// for xi = 0), so the exact two-product offsets of the 4-point path serve
+// both: the fraction of u + 1/2 is r and 1 - r of the other staggering.
+//
+// The points are binned exactly as for the 4-point kernels (by the xi = 0
+// cell), and a tile of cells T0 .. T0 + TS - 1 owns a box of side TS + s
+// starting at node T0 + lo, lo = tlo - 1 (even s) or tlo (odd s): the nodes
+// its points can reach in any staggering.  One warp per (tile, component)
+// adds its points' s^d contributions in a fixed order (the order of the
+// bins), a second kernel sums the boxes covering each node in a fixed order,
+// so results are bit-reproducible as on the 4-point path.  Interpolation
+// stages a tile's box of grid values in shared memory and gives each point
+// one thread.
+#include <math.h>
+
+#include "ib_internal.h"
+
+namespace ibgb {
+namespace {
+
+constexpr int kWWarps = 2;     // (tile, component) units per CTA, one warp each
+constexpr int kWBatch = 32;    // points per staging batch
+constexpr int kWCover = 8;     // covering boxes per node and dimension (at most 1 + ceil(s / n) <= 7)
+constexpr int kWInterpThreads = 128;
+constexpr int kThreads = 256;
+
+template <int D, int S, int TS>
+struct WGeo {
+  static constexpr bool odd = (S & 1) != 0;
+  static constexpr int tlo = odd ? -(S - 1) / 2 : 1 - S / 2;
+  static constexpr int lo = odd ? tlo : tlo - 1;            // box origin relative to the tile's first cell
+  static constexpr int BS = TS + S;                         // box side
+  static constexpr int BV = (D == 3) ? BS * BS * BS : BS * BS;
+  static constexpr int NODES = (D == 3) ? S * S * S : S * S;
+  static constexpr int PER = (NODES + 31) / 32;             // support nodes per lane
+  static constexpr int REC = S * S + ((D == 3) ? S : 0);    // wx wy h^-d G products, then wz
+  static constexpr int NROWS = (D == 3) ? TS * TS : TS;     // cell rows (x runs) of a full tile
+};
+
+inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <int D, int TS>
+__device__ __forceinline__ void wtile_coords(const int* ntile, const int* n, long long lt, int T0[3], int TE[3]) {
+  const int l = (int)lt;
+  const int c0 = l % ntile[0];
+  const int r = l / ntile[0];
+  const int c1 = r % ntile[1];
+  const int c2 = r / ntile[1];
+  T0[0] = c0 * TS;
+  T0[1] = c1 * TS;
+  T0[2] = (D == 3) ? c2 * TS : 0;
+  TE[0] = min(TS, n[0] - T0[0]);
+  TE[1] = min(TS, n[1] - T0[1]);
+  TE[2] = (D == 3) ? min(TS, n[2] - T0[2]) : 1;
+}
+
+__device__ __forceinline__ int wfloor_div(int a, int b) {
+  int q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+// Weights w[k] = phi(tlo + k - rho) from the fraction r (of u for even s, of
+// u + 1/2 for odd s) and c = 1 - r, each without cancellation:
+//   3-point (rho = r - 1/2, q = sqrt(1 - 3 rho^2) = sqrt(1/4 + 3 r c)):
+//     2 c^2 / (1/2 + 3c + q),  (1 + q) / 3,  2 r^2 / (1/2 + 3r + q);
+//   6-point B-spline (rho = r): c^5/120, m(c), p(r), p(c), m(r), r^5/120 with
+//     p(x) = (66 - 60 x^2 + 30 x^4 - 10 x^5) / 120 (the piece on [0, 1)) and
+//     m(x) = (1 + 5x + 10x^2 + 10x^3 + 5x^4 - 5x^5) / 120 (the piece on [1, 2)
+//     in the distance x = 2 - |arg| to its far end).
+template <typename T, int S>
+__device__ __forceinline__ void wweights(T r, T c, T w[S]) {
+  if constexpr (S == 3) {
+    const T q = sqrt(fma((T)3 * r, c, (T)0.25));
+    w[0] = (T)2 * c * c / ((T)0.5 + (T)3 * c + q);
+    w[1] = ((T)1 + q) * (T)(1.0 / 3.0);
+    w[2] = (T)2 * r * r / ((T)0.5 + (T)3 * r + q);
+  } else {
+    constexpr T k = (T)(1.0 / 120.0);
+    const T r2 = r * r, c2 = c * c;
+    w[0] = c2 * c2 * c * k;
+    w[1] = ((T)1 + c * ((T)5 + c * ((T)10 + c * ((T)10 + c * ((T)5 - (T)5 * c))))) * k;
+    w[2] = ((T)66 + r2 * ((T)-60 + r2 * ((T)30 - (T)10 * r))) * k;
+    w[3] = ((T)66 + c2 * ((T)-60 + c2 * ((T)30 - (T)10 * c))) * k;
+    w[4] = ((T)1 + r * ((T)5 + r * ((T)10 + r * ((T)10 + r * ((T)5 - (T)5 * r))))) * k;
+    w[5] = r2 * r2 * r * k;
+  }
+}
+
+// One dimension of a point for component a: box offset of its first support
+// node and its s weights.  Returns false when the point's xi = 0 cell is not
+// in the tile (X changed after binning).
+template <typename T, int D, int S, int TS>
+__device__ __forceinline__ bool wpoint_dim(const Job& jb, const Shape& sh, T x, int b, int a, const int T0[3],
+                                           const int TE[3], int& o, T w[S]) {
+  using W = WGeo<D, S, TS>;
+  Cell1<T> cl;
+  const uint32_t e = point_cell<T>(x, jb, b, cl);
+  const int n = jb.n[b];
+  const int cphys = ((unsigned)cl.i0 < (unsigned)n) ? cl.i0 : modn(cl.i0, n);
+  const bool inside = e == 0 && (unsigned)(cphys - T0[b]) < (unsigned)TE[b] && (cl.i1 - cl.i0) >= -1 &&
+                      (cl.i1 - cl.i0) <= 0;
+  const bool h = half_stag(sh, a, b);
+  int di;
+  T r, c;
+  if (W::odd == h) {          // even s with xi = 0, or odd s with xi = 1/2: floor(X N/L)
+    di = 0;
+    r = cl.r0;
+    c = cl.c0;
+  } else if (!W::odd) {       // even s, xi = 1/2: floor(X N/L - 1/2)
+    di = cl.i1 - cl.i0;
+    r = cl.r1;
+    c = cl.c1;
+  } else {                    // odd s, xi = 0: floor(X N/L + 1/2) = floor(X N/L - 1/2) + 1
+    di = cl.i1 + 1 - cl.i0;
+    r = cl.r1;
+    c = cl.c1;
+  }
+  o = cphys - T0[b] + di + (W::tlo - W::lo);
+  wweights<T, S>(r, c, w);
+  return inside;
+}
+
+// ---------------------------------------------------------------------------
+// Spreading into tile boxes: one warp per (tile, component), the two stages
+// of the 4-point path.  Stage 1 (lanes = points): a point's record holds the
+// s^2 products wx[tx] wy[ty] h^-d G and the s weights wz, plus its box offset.
+// Stage 2 (warp = point): lane l owns support nodes l, l + 32, ... of the s^d
+// (distinct nodes, so plain read-modify-writes are race-free); the lane's
+// loads come before its stores, and __syncwarp orders consecutive points.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int S, int TS>
+__global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant__ Jobs J, const Shape sh,
+                                                            const Bins B, T* __restrict__ boxes, long long nunits) {
+  using W = WGeo<D, S, TS>;
+  static_assert(W::NROWS % 32 == 0, "rows: a multiple of 32");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t rstart_s[kWWarps][W::NROWS];
+  __shared__ uint32_t rpre_s[kWWarps][W::NROWS];
+  __shared__ int roff_s[kWWarps][kWBatch];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long unit = (long long)blockIdx.x * kWWarps + warp;
+  if (unit >= nunits) return;                      // the whole warp leaves; no block barrier follows
+  T* box = reinterpret_cast<T*>(smem_raw) + warp * (W::BV + kWBatch * W::REC);
+  T* rec_s = box + W::BV;
+  uint32_t* rstart = rstart_s[warp];
+  uint32_t* rpre = rpre_s[warp];
+  int* roff = roff_s[warp];
+  const Job& jb = J.one;
+  const int nc = sh.ncomp;
+  const long long gt = unit / nc;
+  const int a = (int)(unit - gt * nc);
+  int T0[3], TE[3];
+  wtile_coords<D, TS>(jb.ntile, jb.n, gt, T0, TE);
+  for (int i = lane; i < W::BV; i += 32) box[i] = (T)0;
+
+  const int rows = (D == 3) ? TE[1] * TE[2] : TE[1];
+  uint32_t M = 0;
+#pragma unroll
+  for (int k = 0; k < W::NROWS / 32; ++k) {
+    const int r = lane + 32 * k;
+    uint32_t st = 0, cnt = 0;
+    if (r < rows) {
+      const int y = T0[1] + ((D == 3) ? r % TE[1] : r);
+      const int z = (D == 3) ? T0[2] + r / TE[1] : 0;
+      const long long cell = T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
+      st = B.count[cell];
+      cnt = B.count[cell + TE[0]] - st;
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    rstart[r] = st;
+    rpre[r] = M + inc - cnt;
+    M += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+
+  const T* Xg = (const T*)jb.X;
+  const T* Gp = (const T*)jb.G;
+  const T hmd = (T)jb.hmd;
+  auto load_point = [&](uint32_t q, T xs[D], T& gs) {
+    int lo = 0;
+#pragma unroll
+    for (int step = W::NROWS / 2; step >= 1; step >>= 1)
+      if (lo + step < rows && rpre[lo + step] <= q) lo += step;
+    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])];
+#pragma unroll
+    for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
+    gs = Gp[li * nc + a];
+  };
+
+  int loff[W::PER], lxy[W::PER], lz[W::PER];
+  bool lon[W::PER];
+#pragma unroll
+  for (int k = 0; k < W::PER; ++k) {
+    const int q = lane + 32 * k;
+    lon[k] = q < W::NODES;
+    const int tx = q % S, ty = (q / S) % S, tz = (D == 3) ? q / (S * S) : 0;
+    loff[k] = tx + W::BS * (ty + W::BS * tz);
+    lxy[k] = tx + S * ty;
+    lz[k] = S * S + tz;
+  }
+
+  T xs[D], gs = (T)0;
+  if (lane < M) load_point(lane, xs, gs);
+  for (uint32_t base = 0; base < M; base += kWBatch) {
+    if (base + lane < M) {
+      int o[3] = {0, 0, 0};
+      T w[3][S];
+      bool inside = true;
+#pragma unroll
+      for (int b = 0; b < D; ++b) inside = wpoint_dim<T, D, S, TS>(jb, sh, xs[b], b, a, T0, TE, o[b], w[b]) && inside;
+      T ga = hmd * gs;
+      if (!inside) {                 // X changed after binning: contribute nothing, report
+        atomicOr(B.err, ERR_STALE);
+        ga = (T)0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          o[b] = 0;
+#pragma unroll
+          for (int t = 0; t < S; ++t) w[b][t] = (T)0;
+        }
+      }
+      T* rec = rec_s + lane * W::REC;
+#pragma unroll
+      for (int ty = 0; ty < S; ++ty)
+#pragma unroll
+        for (int tx = 0; tx < S; ++tx) rec[tx + S * ty] = (w[0][tx] * ga) * w[1][ty];
+      if (D == 3) {
+#pragma unroll
+        for (int tz = 0; tz < S; ++tz) rec[S * S + tz] = w[D - 1][tz];
+      }
+      roff[lane] = o[0] + W::BS * (o[1] + W::BS * o[2]);
+    }
+    const uint32_t nq = base + kWBatch + lane;     // next batch's point data, fetched during the additions
+    if (nq < M) load_point(nq, xs, gs);
+    __syncwarp();
+    const int cnt = (int)min((uint32_t)kWBatch, M - base);
+    for (int i = 0; i < cnt; ++i) {
+      const T* rp = rec_s + i * W::REC;
+      const int off = roff[i];
+      T v[W::PER], add[W::PER];
+#pragma unroll
+      for (int k = 0; k < W::PER; ++k) {
+        if (lon[k]) {
+          add[k] = (D == 3) ? rp[lxy[k]] * rp[lz[k]] : rp[lxy[k]];
+          v[k] = box[off + loff[k]];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < W::PER; ++k)
+        if (lon[k]) box[off + loff[k]] = v[k] + add[k];
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  T* dst = boxes + unit * (long long)W::BV;        // scratch [tile][comp][BV]
+  for (int i = lane; i < W::BV; i += 32) dst[i] = box[i];
+}
+
+// Boxes covering node x of a dimension with n nodes and ntile tiles: every
+// unwrapped copy v = x + k n inside some tile's used box range (offsets
+// 0 .. TE + s - 1 from the box origin), in increasing v, then tile.
+template <int S, int TS>
+__device__ __forceinline__ int wcover(int x, int n, int ntile, int* tl, int* of) {
+  using W = WGeo<3, S, TS>;
+  int cnt = 0;
+  int v = x;
+  while (v - n >= W::lo) v -= n;
+  const int last = (ntile - 1) * TS;
+  const int vend = last + W::lo + (n - last) + S;
+  for (; v < vend; v += n) {
+    const int t0 = max(0, wfloor_div(v - W::lo - W::BS + 1, TS));
+    const int t1 = min(ntile - 1, wfloor_div(v - W::lo, TS));
+    for (int t = t0; t <= t1; ++t) {
+      const int o = v - t * TS - W::lo;
+      const int te = min(TS, n - t * TS);
+      if (o >= 0 && o < te + S && cnt < kWCover) {
+        tl[cnt] = t;
+        of[cnt] = o;
+        ++cnt;
+      }
+    }
+  }
+  return cnt;
+}
+
+template <typename T, int D, int S, int TS>
+__global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ Jobs J, const Shape sh,
+                                                         const T* __restrict__ boxes, int accumulate) {
+  using W = WGeo<D, S, TS>;
+  const Job& jb = J.one;
+  const long long lc = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (lc >= jb.ncell) return;
+  int x[3];
+  x[0] = (int)(lc % jb.n[0]);
+  const long long q = lc / jb.n[0];
+  x[1] = (int)(q % jb.n[1]);
+  x[2] = (D == 3) ? (int)(q / jb.n[1]) : 0;
+  int tl[3][kWCover], of[3][kWCover], nco[3];
+#pragma unroll
+  for (int b = 0; b < D; ++b) nco[b] = wcover<S, TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
+  if (D == 2) {
+    nco[2] = 1;
+    tl[2][0] = 0;
+    of[2][0] = 0;
+  }
+  const int nc = sh.ncomp;
+  T* f = (T*)jb.f;
+  for (int a = 0; a < nc; ++a) {
+    T s = 0;
+    for (int iz = 0; iz < nco[2]; ++iz)
+      for (int iy = 0; iy < nco[1]; ++iy) {
+        const long long trow = tl[1][iy] + (long long)jb.ntile[1] * tl[2][iz];
+        const int orow = (of[2][iz] * W::BS + of[1][iy]) * W::BS;
+        for (int ix = 0; ix < nco[0]; ++ix) {
+          const long long tile = tl[0][ix] + (long long)jb.ntile[0] * trow;
+          s += boxes[(tile * nc + a) * W::BV + orow + of[0][ix]];
+        }
+      }
+    const long long o = a * jb.ncell + lc;
+    f[o] = accumulate ? f[o] + s : s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Interpolation: one CTA per tile (plus a last block for the points with
+// invalid positions, which get NaN); the tile's box of grid values (all
+// components) is staged in shared memory, then each thread takes points of
+// the tile (cell order) and sums their s^d support per component.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int S, int TS>
+__global__ void __launch_bounds__(kWInterpThreads) k_interp_w(const __grid_constant__ Jobs J, const Shape sh,
+                                                               const Bins B, const T scale) {
+  using W = WGeo<D, S, TS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* box = reinterpret_cast<T*>(smem_raw);
+  __shared__ uint32_t rstart[W::NROWS];
+  __shared__ uint32_t rpre[W::NROWS + 1];
+  const Job& jb = J.one;
+  const int nc = sh.ncomp;
+  const int tid = threadIdx.x;
+  if (blockIdx.x == gridDim.x - 1) {
+    for (long long p = B.count[B.ncell_total] + tid; p < B.npts_total; p += kWInterpThreads) {
+      T* U = (T*)jb.U + (long long)B.perm[p] * nc;
+      for (int a = 0; a < nc; ++a) U[a] = (T)NAN;
+    }
+    return;
+  }
+  int T0[3], TE[3];
+  wtile_coords<D, TS>(jb.itile, jb.n, blockIdx.x, T0, TE);
+  const T* u = (const T*)jb.u;
+  for (int i = tid; i < nc * W::BV; i += kWInterpThreads) {
+    const int a = i / W::BV;
+    const int rem = i - a * W::BV;
+    const int bx = rem % W::BS;
+    const int by = (rem / W::BS) % W::BS;
+    const int bz = (D == 3) ? rem / (W::BS * W::BS) : 0;
+    long long node = modn(T0[0] + W::lo + bx, jb.n[0]) +
+                     (long long)jb.n[0] * modn(T0[1] + W::lo + by, jb.n[1]);
+    if (D == 3) node += (long long)jb.n[0] * jb.n[1] * modn(T0[2] + W::lo + bz, jb.n[2]);
+    box[i] = u[a * jb.ncell + node];
+  }
+  const int rows = (D == 3) ? TE[1] * TE[2] : TE[1];
+  if (tid < rows) {
+    const int y = T0[1] + ((D == 3) ? tid % TE[1] : tid);
+    const int z = (D == 3) ? T0[2] + tid / TE[1] : 0;
+    const long long cell = T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
+    rstart[tid] = B.count[cell];
+    rpre[tid] = B.count[cell + TE[0]] - rstart[tid];     // count, made a prefix below
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (int r = 0; r < rows; ++r) {
+      const uint32_t c = rpre[r];
+      rpre[r] = run;
+      run += c;
+    }
+    rpre[rows] = run;
+  }
+  __syncthreads();
+  const uint32_t P = rpre[rows];
+  const T* Xg = (const T*)jb.X;
+  for (uint32_t q = tid; q < P; q += kWInterpThreads) {
+    int lo = 0, hi = rows - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rpre[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])];
+    T xs[D];
+#pragma unroll
+    for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
+    T* U = (T*)jb.U + li * nc;
+    for (int a = 0; a < nc; ++a) {
+      int o[3] = {0, 0, 0};
+      T w[3][S];
+      bool inside = true;
+#pragma unroll
+      for (int b = 0; b < D; ++b) inside = wpoint_dim<T, D, S, TS>(jb, sh, xs[b], b, a, T0, TE, o[b], w[b]) && inside;
+      if (!inside) {
+        atomicOr(B.err, ERR_STALE);      // X changed after binning: no gather outside the box
+        U[a] = (T)NAN;
+        continue;
+      }
+      const T* bp = box + a * W::BV + (o[2] * W::BS + o[1]) * W::BS + o[0];
+      T acc = 0;
+#pragma unroll
+      for (int tz = 0; tz < ((D == 3) ? S : 1); ++tz) {
+        T accy = 0;
+#pragma unroll
+        for (int ty = 0; ty < S; ++ty) {
+          const T* row = bp + (tz * W::BS + ty) * W::BS;
+          T accx = w[0][0] * row[0];
+#pragma unroll
+          for (int tx = 1; tx < S; ++tx) accx += w[0][tx] * row[tx];
+          accy += w[1][ty] * accx;
+        }
+        acc += ((D == 3) ? w[D - 1][tz] : (T)1) * accy;
+      }
+      U[a] = acc * scale;
+    }
+  }
+}
+
+template <typename K>
+void allow_smem_w(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int D, int S, int TS>
+cudaError_t spread_w(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool accumulate,
+                     cudaStream_t s) {
+  using W = WGeo<D, S, TS>;
+  const long long nunits = ntiles * sh.ncomp;
+  if (nunits > 0) {
+    const size_t bytes = (size_t)kWWarps * (W::BV + kWBatch * W::REC) * sizeof(T);
+    allow_smem_w(k_spread_w<T, D, S, TS>, bytes);
+    k_spread_w<T, D, S, TS><<<grid_for(nunits, kWWarps), 32 * kWWarps, bytes, s>>>(J, sh, B, (T*)boxes, nunits);
+  }
+  if (J.one.ncell > 0)
+    k_combine_w<T, D, S, TS><<<grid_for(J.one.ncell, kThreads), kThreads, 0, s>>>(J, sh, (const T*)boxes,
+                                                                                   accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, int S, int TS>
+cudaError_t interp_w(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, double scale, cudaStream_t s) {
+  using W = WGeo<D, S, TS>;
+  const size_t bytes = (size_t)sh.ncomp * W::BV * sizeof(T);
+  allow_smem_w(k_interp_w<T, D, S, TS>, bytes);
+  k_interp_w<T, D, S, TS><<<(unsigned)(nitiles + 1), kWInterpThreads, bytes, s>>>(J, sh, B, (T)scale);
+  return cudaGetLastError();
+}
+
+template <typename T, int S>
+cudaError_t spread_w_dim(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool acc,
+                         cudaStream_t s) {
+  if (sh.dim == 3) return spread_w<T, 3, S, 8>(J, sh, B, boxes, ntiles, acc, s);
+  return spread_w<T, 2, S, 32>(J, sh, B, boxes, ntiles, acc, s);
+}
+
+template <typename T, int S>
+cudaError_t interp_w_dim(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, double scale,
+                         cudaStream_t s) {
+  if (sh.dim == 3) return interp_w<T, 3, S, 8>(J, sh, B, nitiles, scale, s);
+  return interp_w<T, 2, S, 32>(J, sh, B, nitiles, scale, s);
+}
+
+}  // namespace
+
+int kernel_width(int kernel) { return kernel == 2 ? 3 : (kernel == 3 ? 6 : 4); }
+
+cudaError_t launch_spread_width(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles,
+                                int dtype, bool accumulate, cudaStream_t s) {
+  const int S = kernel_width(sh.kernel);
+  if (dtype == 0) return S == 3 ? spread_w_dim<float, 3>(J, sh, B, boxes, ntiles, accumulate, s)
+                                : spread_w_dim<float, 6>(J, sh, B, boxes, ntiles, accumulate, s);
+  return S == 3 ? spread_w_dim<double, 3>(J, sh, B, boxes, ntiles, accumulate, s)
+                : spread_w_dim<double, 6>(J, sh, B, boxes, ntiles, accumulate, s);
+}
+
+cudaError_t launch_interp_width(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, int dtype,
+                                double scale, cudaStream_t s) {
+  const int S = kernel_width(sh.kernel);
+  if (dtype == 0) return S == 3 ? interp_w_dim<float, 3>(J, sh, B, nitiles, scale, s)
+                                : interp_w_dim<float, 6>(J, sh, B, nitiles, scale, s);
+  return S == 3 ? interp_w_dim<double, 3>(J, sh, B, nitiles, scale, s)
+                : interp_w_dim<double, 6>(J, sh, B, nitiles, scale, s);
+}
+
+}  // namespace ibgb

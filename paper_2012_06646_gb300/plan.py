@@ -49,7 +49,8 @@ class Plan:
         self.n = tuple(int(v) for v in n)[: self.dim]
         self.L = tuple(float(v) for v in L)[: self.dim]
         self.mac = grid == "mac"
-        self.kernel = {"peskin4": _abi.IB_KERNEL_PESKIN4, "cosine4": _abi.IB_KERNEL_COSINE4}[kernel]
+        self.kernel = {"peskin4": _abi.IB_KERNEL_PESKIN4, "cosine4": _abi.IB_KERNEL_COSINE4,
+                       "roma3": _abi.IB_KERNEL_ROMA3, "bspline6": _abi.IB_KERNEL_BSPLINE6}[kernel]
         self.dtype = dtype
         self.ncomp = int(ncomp) if ncomp is not None else self.dim
         self.max_points = int(max_points)

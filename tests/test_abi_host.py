@@ -71,6 +71,31 @@ def test_footprint_and_validation_on_host(abi):
     assert b"sm_103a" in lib.ib_version()
 
 
+def test_kernel_widths_on_host(abi):
+    """3- and 6-point kernels: plans size their boxes for the width; compensated plans and batches reject them."""
+    lib = abi.load()
+    size = ctypes.c_size_t()
+    sizes = {}
+    for k in (abi.IB_KERNEL_PESKIN4, abi.IB_KERNEL_ROMA3, abi.IB_KERNEL_BSPLINE6):
+        assert lib.ib_plan_footprint(ctypes.byref(_desc(abi, kernel=k)), ctypes.byref(size)) == abi.IB_OK
+        sizes[k] = size.value
+    boxes = {k: 4096 * 3 * (8 + w) ** 3 * 4 for k, w in ((0, 4), (2, 3), (3, 6))}
+    assert sizes[2] - sizes[0] == pytest.approx(boxes[2] - boxes[0], abs=4096)
+    assert sizes[3] - sizes[0] == pytest.approx(boxes[3] - boxes[0], abs=4096)
+    h = ctypes.c_void_p()
+    for k in (abi.IB_KERNEL_ROMA3, abi.IB_KERNEL_BSPLINE6):
+        d = _desc(abi, kernel=k, flags=abi.IB_PLAN_COMPENSATED)
+        assert lib.ib_plan_footprint(ctypes.byref(d), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG
+        assert lib.ib_plan_create(ctypes.byref(d), ctypes.byref(h)) == abi.IB_ERR_INVALID_ARG
+        b = abi.ib_batch_desc()
+        b.dim, b.grid, b.kernel, b.dtype, b.ncomp = 3, abi.IB_GRID_MAC, k, abi.IB_F32, 3
+        b.max_jobs, b.max_points, b.max_cells, b.max_tiles = 4, 1000, 1 << 16, 256
+        assert lib.ib_batch_footprint(ctypes.byref(b), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG
+        assert lib.ib_interpolate_noalloc(ctypes.byref(_desc(abi, kernel=k)), 0, None, None, None, None) == \
+            abi.IB_ERR_INVALID_ARG
+    assert lib.ib_plan_footprint(ctypes.byref(_desc(abi, kernel=4)), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG
+
+
 def test_stokes_validation_on_host(abi):
     """ib_stokes_create rejects what it cannot solve before any CUDA or cuFFT call."""
     lib = abi.load()

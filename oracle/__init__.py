@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
 
 class _Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3),
-                ("grid", ctypes.c_int), ("kernel", ctypes.c_int), ("ncomp", ctypes.c_int)]
+                ("grid", ctypes.c_int), ("kernel", ctypes.c_int), ("ncomp", ctypes.c_int), ("bounded", ctypes.c_int)]
 
 
 @dataclass(frozen=True)
@@ -57,6 +57,7 @@ class Grid:
     mac: bool = True
     kernel: int = 0          # 0 = standard 4-point, 1 = cosine, 2 = 3-point, 3 = 6-point B-spline
     ncomp: int | None = None
+    bounded: tuple = ()      # per dimension: True for a non-periodic dimension
 
     @property
     def comps(self) -> int:
@@ -79,6 +80,7 @@ class Grid:
         g.grid = 1 if self.mac else 0
         g.kernel = int(self.kernel)
         g.ncomp = int(self.comps)
+        g.bounded = sum(1 << b for b, v in enumerate(self.bounded) if v)
         return g
 
 

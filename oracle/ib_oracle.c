@@ -127,6 +127,7 @@ static int check_grid(const or_grid* g) {
   if (g->ncomp < 1) return 1;
   if (g->grid == 1 && g->ncomp != g->dim) return 1;
   if (g->kernel < 0 || g->kernel > 3) return 1;
+  if (g->bounded & ~((1 << g->dim) - 1)) return 1;
   return 0;
 }
 
@@ -216,13 +217,31 @@ static void shift_of(const or_grid* g, int s, int* t) {
 /* Argument of phi for shift t and offset r: the displacement t - r of Eq. delta-defs. */
 static double karg(int t, double r) { return (g_mutation == 2) ? (double)t + r : (double)t - r; }
 
+/* Grid index of node i + t (periodic wrap), or -1 when it lies outside the
+ * domain in a bounded dimension (the empty marker of the grid indexing function). */
 static long long node_index(const or_grid* g, const cellrec* c, const int* t) {
   long long k = 0, stride = 1;
   for (int b = 0; b < g->dim; ++b) {
-    k += wrap(c->i[b] + t[b], g->n[b]) * stride;
+    long long i = c->i[b] + t[b];
+    if ((g->bounded >> b) & 1) {
+      if (i < 0 || i >= g->n[b]) return -1;
+    } else {
+      i = wrap(i, g->n[b]);
+    }
+    k += i * stride;
     stride *= g->n[b];
   }
   return k;
+}
+
+/* A point takes part only if it lies in [0, L_b] in every bounded dimension. */
+static int point_in_domain(const or_grid* g, const double* Xj) {
+  for (int b = 0; b < g->dim; ++b) {
+    if (!((g->bounded >> b) & 1)) continue;
+    volatile double u = Xj[b] * ((double)g->n[b] / g->L[b]);
+    if (!(u >= 0.0 && u <= (double)g->n[b])) return 0;
+  }
+  return 1;
 }
 
 static double inv_cell_volume(const or_grid* g) {
@@ -239,6 +258,7 @@ int or_spread(const or_grid* g, long long n, const double* X, const double* G, d
   memset(f, 0, sizeof(double) * (size_t)(ncell * g->ncomp));
   if (fabs_out) memset(fabs_out, 0, sizeof(double) * (size_t)(ncell * g->ncomp));
   for (long long j = 0; j < n; ++j) {          /* loop over IB points (Algorithm 2) */
+    if (!point_in_domain(g, X + j * g->dim)) continue;
     for (int a = 0; a < g->ncomp; ++a) {
       cellrec c;
       point_cell(g, X + j * g->dim, a, &c);
@@ -248,6 +268,7 @@ int or_spread(const or_grid* g, long long n, const double* X, const double* G, d
         double w = 1.0;
         for (int b = 0; b < g->dim; ++b) w *= or_phi(g->kernel, karg(t[b], c.r[b]));
         long long k = node_index(g, &c, t);
+        if (k < 0) continue;
         double contrib = hmd * w * G[j * g->ncomp + a];
         f[a * ncell + k] += contrib;
         if (fabs_out) fabs_out[a * ncell + k] += fabs(contrib);
@@ -262,6 +283,13 @@ int or_interp(const or_grid* g, long long n, const double* X, const double* u, d
   long long ncell = ncell_of(g);
   int nshift = nshift_of(g);
   for (long long j = 0; j < n; ++j) {          /* one independent row of S* per point (Algorithm 3) */
+    if (!point_in_domain(g, X + j * g->dim)) {
+      for (int a = 0; a < g->ncomp; ++a) {
+        U[j * g->ncomp + a] = NAN;
+        if (Uabs) Uabs[j * g->ncomp + a] = 0.0;
+      }
+      continue;
+    }
     for (int a = 0; a < g->ncomp; ++a) {
       cellrec c;
       point_cell(g, X + j * g->dim, a, &c);
@@ -271,7 +299,9 @@ int or_interp(const or_grid* g, long long n, const double* X, const double* u, d
         shift_of(g, s, t);
         double w = 1.0;
         for (int b = 0; b < g->dim; ++b) w *= or_phi(g->kernel, karg(t[b], c.r[b]));
-        double term = w * u[a * ncell + node_index(g, &c, t)];
+        long long k = node_index(g, &c, t);
+        if (k < 0) continue;
+        double term = w * u[a * ncell + k];
         acc += term;
         aabs += fabs(term);
       }
@@ -284,7 +314,7 @@ int or_interp(const or_grid* g, long long n, const double* X, const double* u, d
 
 int or_pos_grad(const or_grid* g, long long n, const double* X, const double* field, const double* v,
                 double* D, double* Dabs) {
-  if (check_grid(g)) return 1;
+  if (check_grid(g) || g->bounded) return 1;   /* gradients: periodic grids only */
   long long ncell = ncell_of(g);
   int nshift = nshift_of(g);
   for (long long j = 0; j < n; ++j) {

@@ -24,7 +24,11 @@
  *     examined are every i + t with |t - r| < s/2 possible (the definition of
  *     delta_h: phi vanishes outside), t in [1 - s/2, s/2] for even s and
  *     [(1 - s)/2, (1 + s)/2] for odd s.
- *   - Periodic box: node indices wrap modulo N in every dimension.
+ *   - Periodic box: node indices wrap modulo N in every dimension, except the
+ *     bounded dimensions (Section 3.1: # returns the empty marker outside the
+ *     domain): there a node index outside 0 .. N - 1 has no grid point and
+ *     takes no part, and a point must lie in [0, L] (u = X N/L in [0, N]);
+ *     a point outside spreads nothing and interpolates to NaN.
  *   - MAC grid (Section 2): component a has xi_a = 0 and xi_b = 1/2 for b != a.
  *     Cell-centred grid: xi_b = 1/2 for every component.
  *   - Spreading (Eq. disc-spread):  f_a[k] = sum_j h^-d prod_b phi(.) G_{j,a}
@@ -51,6 +55,7 @@ typedef struct {
   int kernel;    /* 0 = standard 4-point (Peskin 2002), 1 = cosine 4-point,
                     2 = 3-point (Roma, Peskin, Berger 1999), 3 = 6-point quintic B-spline */
   int ncomp;     /* components of the spread / interpolated field */
+  int bounded;   /* bit b set: dimension b is non-periodic (nodes outside 0 .. n_b - 1 do not exist) */
 } or_grid;
 
 /* 1-D kernel phi(r) and its derivative (Section 2; kernels of Peskin 2002 and
@@ -86,7 +91,7 @@ int or_spread(const or_grid* g, long long n, const double* X, const double* G, d
  * NULL, receives sum_k |weight * u| per point and component. */
 int or_interp(const or_grid* g, long long n, const double* X, const double* u, double* U, double* Uabs);
 
-/* Position derivative of the interpolation sum contracted with v:
+/* Position derivative of the interpolation sum contracted with v (periodic grids):
  *   D_{j,b} = sum_a v_{j,a} sum_k (d/dX_b) [prod_c phi(t_c - r_c)] field_a[k],
  * (d/dX_b) r_b = N_b / L_b.  For interpolation, dLoss/dX = D(field = u, v = dLoss/dU);
  * for spreading, dLoss/dX = h^-d D(field = dLoss/df, v = G).  D is (n, dim). */

@@ -55,7 +55,8 @@ def node_positions(n, L, xi):
     return np.stack([m.ravel() for m in reversed(mesh)], axis=1)
 
 
-def dense_S(n, L, xi, kernel, X):
+def dense_S(n, L, xi, kernel, X, bounded=()):
+    """bounded[b] True: dimension b is not periodic (no images along it)."""
     d = len(n)
     h = np.array([L[b] / n[b] for b in range(d)])
     phi = PHI[kernel]
@@ -63,7 +64,7 @@ def dense_S(n, L, xi, kernel, X):
     S = np.zeros((len(xk), len(X)))
     lo = int(np.floor(np.min(X / np.array(L[:d])))) - 3 if len(X) else -3
     hi = int(np.ceil(np.max(X / np.array(L[:d])))) + 3 if len(X) else 3
-    span = [range(-hi, -lo + 1)] * d
+    span = [range(0, 1) if (b < len(bounded) and bounded[b]) else range(-hi, -lo + 1) for b in range(d)]
     for img in itertools.product(*span):
         shift = np.array(img) * np.array(L[:d])
         diff = (xk[:, None, :] - (X[None, :, :] + shift)) / h

@@ -412,8 +412,11 @@ def kernels_bench(device, stream, X, G, u, reps: int, N: int):
     npts = X.shape[0]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     out = {}
-    for name, width in (("peskin4", 4), ("cosine4", 4), ("roma3", 3), ("bspline6", 6)):
-        plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", kernel=name, max_points=npts, device=device)
+    cases = (("peskin4", 4, False), ("cosine4", 4, False), ("roma3", 3, False), ("bspline6", 6, False),
+             ("peskin4", 4, True))
+    for name, width, walls in cases:
+        plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", kernel=name, max_points=npts, device=device,
+                    bounded=(False, False, walls))
         f = torch.empty(plan.grid_shape(), dtype=torch.float32, device=device)
         U = torch.empty((npts, 3), dtype=torch.float32, device=device)
         ms = {"spread": [], "interp": []}
@@ -433,9 +436,10 @@ def kernels_bench(device, stream, X, G, u, reps: int, N: int):
         plan.check(stream)
         plan.close()
         sp, it = statistics.mean(ms["spread"]), statistics.mean(ms["interp"])
-        out[name] = {"support": width, "bin_and_spread_ms": sp, "interp_ms": it,
-                     "pts_per_s": npts / ((sp + it) / 1e3)}
-    return {"workload": f"{N}^3 MAC grid, {npts} uniform points, FP32, spread (binning included) + interpolate",
+        out[name + ("_walls_z" if walls else "")] = {"support": width, "bin_and_spread_ms": sp, "interp_ms": it,
+                                                    "pts_per_s": npts / ((sp + it) / 1e3)}
+    return {"workload": f"{N}^3 MAC grid, {npts} uniform points, FP32, spread (binning included) + interpolate; "
+                        "'_walls_z': non-periodic in z (walls at z = 0 and z = L)",
             "kernels": out}
 
 

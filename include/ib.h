@@ -85,6 +85,22 @@ enum { IB_F32 = 0, IB_F64 = 1 };
 
 /* Plan creation flags (ib_plan_desc.flags). */
 #define IB_PLAN_COMPENSATED 0x1u   /* size the scratch for IB_COMPENSATED spreading (twice the box scratch) */
+/* Non-periodic ("bounded") dimensions (Section 3.1: the grid indexing
+ * function # returns the empty marker for grid points outside the domain).
+ * In a bounded dimension b every component keeps its n_b nodes
+ * x = h (i + xi), i = 0 .. n_b - 1; spreading drops the contributions to
+ * nodes outside that range and interpolation takes nothing from them.
+ * Positions must lie in [0, L_b] (else IB_ERR_RANGE: the point spreads
+ * nothing and interpolates to NaN), and ib_advect does not wrap them.  The
+ * plan works on the grid extended by 8 ghost nodes per bounded dimension (the
+ * de facto cells of the extended grid of Section 3.1, with the same spacing)
+ * and copies the domain's nodes out of it (spreading) or into it with zero
+ * ghosts (interpolation).  ib_pos_grad and ib_spread_paper return
+ * IB_ERR_NOT_IMPLEMENTED on such plans; ib_plan_bins describes the cells of
+ * the extended grid. */
+#define IB_PLAN_BOUNDED_X 0x2u
+#define IB_PLAN_BOUNDED_Y 0x4u
+#define IB_PLAN_BOUNDED_Z 0x8u   /* 3-D plans only */
 
 /* Per-call flags. */
 #define IB_ACCUMULATE   0x1u   /* spread: f += S G (the paper's l_k <- l_k + w L_i), instead of f = S G */
@@ -106,7 +122,7 @@ typedef struct {
   int dtype;              /* IB_F32 or IB_F64: element type of X, G, f, u, U */
   int ncomp;              /* components per field, 1..4 */
   long long max_points;   /* largest npts any call on this plan will pass, 0 <= max_points < 2^31 */
-  unsigned flags;         /* 0 or IB_PLAN_COMPENSATED */
+  unsigned flags;         /* IB_PLAN_COMPENSATED | IB_PLAN_BOUNDED_X | _Y | _Z, or 0 */
 } ib_plan_desc;
 
 /* Device scratch bytes ib_plan_create would allocate for `desc`.  Host-only:

@@ -35,6 +35,9 @@ IB_F32 = 0
 IB_F64 = 1
 
 IB_PLAN_COMPENSATED = 0x1
+IB_PLAN_BOUNDED_X = 0x2
+IB_PLAN_BOUNDED_Y = 0x4
+IB_PLAN_BOUNDED_Z = 0x8
 IB_ACCUMULATE = 0x1
 IB_COMPENSATED = 0x2
 IB_REUSE_BINS = 0x4

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libibgb.so")
-SOURCES = ["ib_bin.cu", "ib_ops.cu", "ib_width.cu", "ib_paper.cu", "ib_fluid.cu", "ib_api.cu"]
+SOURCES = ["ib_bin.cu", "ib_ops.cu", "ib_width.cu", "ib_bounds.cu", "ib_paper.cu", "ib_fluid.cu", "ib_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -50,19 +50,29 @@ bool pair_aligned(int n0, const void* f, int dtype) {
   return (n0 % 2 == 0) && ((uintptr_t)f % a == 0);
 }
 
+// Ghost nodes added to a bounded dimension (the periodic grid the kernels
+// see has n + kGhost nodes there, with the domain's spacing).
+constexpr int kGhost = 8;
+
 // Fill the geometry part of a job for a grid of n points and sides L.
-bool fill_job(Job& jb, int dim, const int n[3], const double L[3], int tile) {
+// Dimensions whose bit is set in `bounded` are non-periodic: the job's grid
+// extends them by kGhost nodes, with the scale N/L of the domain.
+bool fill_job(Job& jb, int dim, const int n[3], const double L[3], int tile, unsigned bounded = 0) {
   memset(&jb, 0, sizeof(jb));
   long long ncell = 1;
   double hmd = 1.0;
   for (int b = 0; b < 3; ++b) {
     const bool live = b < dim;
-    const int nb = live ? n[b] : 1;
+    const int nd = live ? n[b] : 1;
     const double Lb = live ? L[b] : 1.0;
-    if (nb < 1 || !(Lb > 0.0) || !isfinite(Lb)) return false;
+    if (nd < 1 || !(Lb > 0.0) || !isfinite(Lb)) return false;
+    const bool bd = live && ((bounded >> b) & 1u);
+    const int nb = bd ? nd + kGhost : nd;
     jb.n[b] = nb;
+    jb.nin[b] = nd;
+    jb.bnd[b] = bd ? 1 : 0;
     jb.ntile[b] = live ? (nb + tile - 1) / tile : 1;
-    jb.scale[b] = (double)nb / Lb;
+    jb.scale[b] = (double)nd / Lb;
     if (!isfinite(jb.scale[b]) || !(jb.scale[b] > 0.0)) return false;
     short_scale(jb.scale[b], &jb.sS[b], &jb.sE[b]);
     jb.fastc[b] = (jb.sS[b] > 0 && jb.sE[b] >= -60 && jb.sE[b] <= 60) ? 1 : 0;
@@ -158,6 +168,8 @@ struct ib_plan_s {
   ib_plan_desc desc;
   Shape sh;
   Job job;             // geometry; per-call fields are filled on a copy
+  bool bounded;        // some dimension is non-periodic: spread / interpolate on the extended grid
+  void* gridx;         // extended grid [ncomp][extended nodes] (bounded plans)
   int tile_plain, tile_comp;
   long long ntiles_plain, ntiles_comp;
   Layout layout;
@@ -191,13 +203,15 @@ namespace {
 bool plan_sizes(const ib_plan_desc* d, Job* jb, int* tp, int* tc, long long* ntp, long long* ntc, Layout* L) {
   if (!d || !valid_shape(d->dim, d->grid, d->kernel, d->dtype, d->ncomp)) return false;
   if (d->max_points < 0 || d->max_points > kMaxPointsTotal) return false;
-  if (d->flags & ~IB_PLAN_COMPENSATED) return false;
+  const unsigned bmask = IB_PLAN_BOUNDED_X | IB_PLAN_BOUNDED_Y | (d->dim == 3 ? IB_PLAN_BOUNDED_Z : 0u);
+  if (d->flags & ~(IB_PLAN_COMPENSATED | bmask)) return false;
+  const unsigned bounded = (d->flags & bmask) >> 1;   // bit b: dimension b is bounded
   const int width = kernel_width(d->kernel);
   if (width != 4 && (d->flags & IB_PLAN_COMPENSATED)) return false;   // compensated sums: 4-point kernels
   const int tile_plain = spread_tile_side(d->dim, entry_bytes(d->dtype, false), false, d->ncomp);
   const int tile_comp = spread_tile_side(d->dim, entry_bytes(d->dtype, false), true, d->ncomp);
   Job j;
-  if (!fill_job(j, d->dim, d->n, d->L, tile_plain)) return false;
+  if (!fill_job(j, d->dim, d->n, d->L, tile_plain, bounded)) return false;
   if (j.ncell > kMaxCellsTotal) return false;
   const long long ntp_ = j.ntiles;
   set_tiles(j, d->dim, tile_comp);
@@ -213,7 +227,8 @@ bool plan_sizes(const ib_plan_desc* d, Job* jb, int* tp, int* tc, long long* ntp
   if (tc) *tc = tile_comp;
   if (ntp) *ntp = ntp_;
   if (ntc) *ntc = ntc_;
-  if (L) *L = make_layout(j.ncell, d->max_points, boxes, 0, 0, ntp_ > ntc_ ? ntp_ : ntc_);
+  const size_t gridx = bounded ? (size_t)j.ncell * (size_t)d->ncomp * (size_t)entry_bytes(d->dtype, false) : 0;
+  if (L) *L = make_layout(j.ncell, d->max_points, boxes, 0, gridx, ntp_ > ntc_ ? ntp_ : ntc_);
   return true;
 }
 
@@ -311,6 +326,8 @@ ib_status ib_plan_create(const ib_plan_desc* desc, ib_plan* out) {
   }
   p->bins = carve((char*)p->arena, p->layout);
   p->boxes = (char*)p->arena + p->layout.boxes;
+  p->bounded = p->job.bnd[0] || p->job.bnd[1] || p->job.bnd[2];
+  p->gridx = p->bounded ? (char*)p->arena + p->layout.io : nullptr;
   if (cudaMemset(p->bins.err, 0, sizeof(uint32_t)) != cudaSuccess) {
     cudaFree(p->arena);
     delete p;
@@ -353,17 +370,23 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   J.one.npts = npts;
   J.one.X = X;
   J.one.G = G ? G : f;  // npts == 0: any non-null marker; no point is read
-  J.one.f = f;
+  // A bounded plan spreads onto its extended grid (overwritten), then copies
+  // the domain's nodes into f.
+  void* fo = p->bounded ? p->gridx : f;
+  const bool acc = (flags & IB_ACCUMULATE) != 0 && !p->bounded;
+  J.one.f = fo;
   if (flags & IB_ADJOINT) J.one.hmd = 1.0;
   J.njobs = 1;
   if (kernel_width(p->desc.kernel) != 4) {
-    if (launch_spread_width(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, p->desc.dtype,
-                            (flags & IB_ACCUMULATE) != 0, s) != cudaSuccess)
+    if (launch_spread_width(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, p->desc.dtype, acc, s) !=
+        cudaSuccess)
       return IB_ERR_CUDA;
-    return IB_OK;
+  } else if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp, acc,
+                           pair_aligned(p->job.n[0], fo, p->desc.dtype), s) != cudaSuccess) {
+    return IB_ERR_CUDA;
   }
-  if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp,
-                    (flags & IB_ACCUMULATE) != 0, pair_aligned(p->job.n[0], f, p->desc.dtype), s) != cudaSuccess)
+  if (p->bounded && launch_bounds_crop(p->job, p->desc.ncomp, p->desc.dtype, p->gridx, f,
+                                       (flags & IB_ACCUMULATE) != 0, s) != cudaSuccess)
     return IB_ERR_CUDA;
   return IB_OK;
 }
@@ -385,6 +408,10 @@ ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u
   J.one.u = u;
   J.one.U = U;
   J.njobs = 1;
+  if (p->bounded) {     // the field on the extended grid, zero on the ghost nodes
+    if (launch_bounds_pad(p->job, p->desc.ncomp, p->desc.dtype, u, p->gridx, s) != cudaSuccess) return IB_ERR_CUDA;
+    J.one.u = p->gridx;
+  }
   const double scale = (flags & IB_ADJOINT) ? p->job.hmd : 1.0;
   if (kernel_width(p->desc.kernel) != 4) {
     if (launch_interp_width(J, p->sh, call_bins(p, npts), J.one.nitiles, p->desc.dtype, scale, s) != cudaSuccess)
@@ -403,7 +430,7 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
   if (npts > 0 && (!field || !v || !D)) return IB_ERR_INVALID_ARG;
   if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
   if (!isfinite(scale)) return IB_ERR_INVALID_ARG;
-  if (kernel_width(p->desc.kernel) != 4) return IB_ERR_NOT_IMPLEMENTED;
+  if (kernel_width(p->desc.kernel) != 4 || p->bounded) return IB_ERR_NOT_IMPLEMENTED;
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare(p, npts, X, flags, s);
   if (st != IB_OK) return st;
@@ -441,7 +468,7 @@ ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* 
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
-  if (kernel_width(p->desc.kernel) != 4) return IB_ERR_NOT_IMPLEMENTED;
+  if (kernel_width(p->desc.kernel) != 4 || p->bounded) return IB_ERR_NOT_IMPLEMENTED;
   const int S = p->desc.dim == 3 ? 64 : 16;        // s^d shifts of the 4-point support
   if (algorithm == IB_PAPER_ALG4) {
     beta = 1;

@@ -35,6 +35,8 @@ struct Job {
   double hmd;            // h^-d = prod_b scale_b
   float Lf[3];           // box side per dimension (FP32, for the position update)
   double Ld[3];          // box side per dimension (FP64)
+  int bnd[3];            // 1: bounded dimension (no wrap; n[b] = nin[b] + ghost nodes)
+  int nin[3];            // nodes of the domain per dimension (n[b] when periodic)
   long long cell_base;   // first global cell id of this job
   long long ncell;       // n0 n1 n2
   long long pt_base;     // first global point index of this job

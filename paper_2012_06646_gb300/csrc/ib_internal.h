@@ -28,6 +28,13 @@ cudaError_t launch_spread_width(const Jobs& J, const Shape& sh, const Bins& B, v
 cudaError_t launch_interp_width(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, int dtype,
                                 double scale, cudaStream_t s);
 
+// Bounded (non-periodic) dimensions (ib_bounds.cu): f [ncomp][domain nodes] =
+// (f +) the domain's nodes of fx [ncomp][extended nodes]; ux = u on the domain's
+// nodes and 0 on the ghost nodes.
+cudaError_t launch_bounds_crop(const Job& jb, int ncomp, int dtype, const void* fx, void* f, bool accumulate,
+                               cudaStream_t s);
+cudaError_t launch_bounds_pad(const Job& jb, int ncomp, int dtype, const void* u, void* ux, cudaStream_t s);
+
 // Cells per block of the cell-count scan, and the number of blocks for m entries.
 constexpr long long kScanChunkCells = 8192;
 long long scan_blocks(long long m);

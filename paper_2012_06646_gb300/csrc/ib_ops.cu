@@ -1210,8 +1210,12 @@ __global__ void __launch_bounds__(kThreads) k_advect(const __grid_constant__ Job
   if (p0 >= n) return;
   const T* X = (const T*)J.one.X;
   T L[D];
+  bool wrap[D];
 #pragma unroll
-  for (int b = 0; b < D; ++b) L[b] = (T)J.one.Ld[b];
+  for (int b = 0; b < D; ++b) {
+    L[b] = (T)J.one.Ld[b];
+    wrap[b] = J.one.bnd[b] == 0;    // bounded dimensions keep the position as it is
+  }
   const long long e0 = p0 * D;
   const bool full = vec && p0 + P <= n;
   const int ne = full ? NE : (int)((n - p0) * D);
@@ -1234,7 +1238,7 @@ __global__ void __launch_bounds__(kThreads) k_advect(const __grid_constant__ Job
   for (int k = 0; k < NE; ++k) {
     const T Lb = L[k % D];
     T x = xv[k] + dt * uv[k];
-    if (x >= Lb || x < (T)0) {
+    if (wrap[k % D] && (x >= Lb || x < (T)0)) {
       x -= Lb * floor(x / Lb);
       if (x >= Lb) x -= Lb;
       if (x < (T)0) x += Lb;

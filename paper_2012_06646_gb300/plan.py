@@ -39,11 +39,13 @@ class Plan:
     """A periodic grid (dim, n, L, MAC or cell-centred, kernel, dtype, ncomp) and its scratch.
 
     Grid fields are tensors of shape (ncomp, n2, n1, n0) in 3-D or (ncomp, n1, n0) in 2-D;
-    point arrays are (npts, dim) and (npts, ncomp).
+    point arrays are (npts, dim) and (npts, ncomp).  `bounded` names the non-periodic
+    dimensions (e.g. (False, False, True): walls at z = 0 and z = L).
     """
 
     def __init__(self, dim: int, n, L, grid: str = "mac", kernel: str = "peskin4", dtype=torch.float32,
-                 ncomp: int | None = None, max_points: int = 0, compensated: bool = False, device=None):
+                 ncomp: int | None = None, max_points: int = 0, compensated: bool = False, device=None,
+                 bounded=(False, False, False)):
         self.lib = _abi.load()
         self.dim = int(dim)
         self.n = tuple(int(v) for v in n)[: self.dim]
@@ -66,6 +68,10 @@ class Plan:
         d.ncomp = self.ncomp
         d.max_points = self.max_points
         d.flags = _abi.IB_PLAN_COMPENSATED if compensated else 0
+        for b, flag in enumerate((_abi.IB_PLAN_BOUNDED_X, _abi.IB_PLAN_BOUNDED_Y, _abi.IB_PLAN_BOUNDED_Z)):
+            if b < len(bounded) and bounded[b]:
+                d.flags |= flag
+        self.bounded = tuple(bool(v) for v in bounded)
         self.desc = d
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -96,6 +96,22 @@ def test_kernel_widths_on_host(abi):
     assert lib.ib_plan_footprint(ctypes.byref(_desc(abi, kernel=4)), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG
 
 
+def test_bounded_flags_on_host(abi):
+    """Bounded dimensions: accepted per dimension (z only in 3-D); the scratch grows by the extended grid."""
+    lib = abi.load()
+    size = ctypes.c_size_t()
+    assert lib.ib_plan_footprint(ctypes.byref(_desc(abi)), ctypes.byref(size)) == abi.IB_OK
+    base = size.value
+    d = _desc(abi, flags=abi.IB_PLAN_BOUNDED_Z)
+    assert lib.ib_plan_footprint(ctypes.byref(d), ctypes.byref(size)) == abi.IB_OK
+    # 128 x 128 x 136 extended cells: boxes of 16 x 16 x 17 tiles, an extended grid of 3 components
+    assert size.value > base + 3 * 128 * 128 * 136 * 4
+    d2 = _desc(abi, dim=2, n=(64, 64), ncomp=2, flags=abi.IB_PLAN_BOUNDED_Z)
+    assert lib.ib_plan_footprint(ctypes.byref(d2), ctypes.byref(size)) == abi.IB_ERR_INVALID_ARG
+    d3 = _desc(abi, dim=2, n=(64, 64), ncomp=2, flags=abi.IB_PLAN_BOUNDED_X | abi.IB_PLAN_BOUNDED_Y)
+    assert lib.ib_plan_footprint(ctypes.byref(d3), ctypes.byref(size)) == abi.IB_OK
+
+
 def test_stokes_validation_on_host(abi):
     """ib_stokes_create rejects what it cannot solve before any CUDA or cuFFT call."""
     lib = abi.load()

@@ -209,13 +209,13 @@ def forces(seed, step, npts):
     return ib_inputs.normal_array(seed * 1000 + step, (npts, 3), purpose="G")
 
 
-def cpu_oracle_rate(sample: int, N: int, seed: int):
+def cpu_oracle_rate(sample: int, N: int, seed: int, kernel: int = 0, bounded=()):
     """The FP64 oracle (single thread) on `sample` points of the workload:
     one spread + one interpolation; returns (pts/s, seconds)."""
     import oracle
     X, u = workload(seed, sample, N)
     G = forces(seed, 0, sample)
-    g = oracle.Grid(dim=3, n=(N, N, N), L=(1.0, 1.0, 1.0), mac=True)
+    g = oracle.Grid(dim=3, n=(N, N, N), L=(1.0, 1.0, 1.0), mac=True, kernel=kernel, bounded=bounded)
     t0 = time.perf_counter()
     oracle.spread(g, X, G)
     oracle.interp(g, X, u)
@@ -403,10 +403,12 @@ def membrane_bench(device, stream, reps: int, peak: float, seed: int = 0, N: int
             "note": "spread + interpolate pair (compensated spread, binning included)"}
 
 
-def kernels_bench(device, stream, X, G, u, reps: int, N: int):
+def kernels_bench(device, stream, X, G, u, reps: int, N: int, peak: float, oracle_sample: int = 0):
     """Bin + spread + interpolate on the bench workload with every kernel of
     the library (support widths 4, 4, 3, 6): CUDA events on the stream, L2
-    flushed before each timed repetition."""
+    flushed before each timed repetition.  Each line carries the pair's HBM
+    roofline fraction (the algorithmic bytes of the headline pair) and, with
+    oracle_sample > 0, the FP64 oracle's single-thread rate on that many points."""
     import torch
     from paper_2012_06646_gb300.plan import Plan
     npts = X.shape[0]
@@ -436,15 +438,23 @@ def kernels_bench(device, stream, X, G, u, reps: int, N: int):
         plan.check(stream)
         plan.close()
         sp, it = statistics.mean(ms["spread"]), statistics.mean(ms["interp"])
-        out[name + ("_walls_z" if walls else "")] = {"support": width, "bin_and_spread_ms": sp, "interp_ms": it,
-                                                    "pts_per_s": npts / ((sp + it) / 1e3)}
+        pair_bytes = 2 * (npts * 24 + 3 * N ** 3 * 4)
+        line = {"support": width, "bin_and_spread_ms": sp, "interp_ms": it, "pts_per_s": npts / ((sp + it) / 1e3),
+                "roofline_frac": pair_bytes / ((sp + it) / 1e3) / 1e9 / peak}
+        if oracle_sample > 0:
+            kid = {"peskin4": 0, "cosine4": 1, "roma3": 2, "bspline6": 3}[name]
+            rate, secs = cpu_oracle_rate(oracle_sample, N, 0, kid, (False, False, walls))
+            line["oracle_pts_per_s"] = rate
+        out[name + ("_walls_z" if walls else "")] = line
     return {"workload": f"{N}^3 MAC grid, {npts} uniform points, FP32, spread (binning included) + interpolate; "
                         "'_walls_z': non-periodic in z (walls at z = 0 and z = L)",
+            "roofline": f"pair bytes 2 (24 n + 12 N^3) / (spread + interp time) over {peak} GB/s (measured HBM)",
+            "oracle": f"FP64 oracle, one thread, {oracle_sample} points of the workload, spread + interpolate",
             "kernels": out}
 
 
 def ib_step_bench(device, stream, X0, ud, G, reps: int, peak: float, N: int, dt: float,
-                  rho: float = 1.0, mu: float = 1.0e-2):
+                  rho: float = 1.0, mu: float = 1.0e-2, oracle_solve: bool = True):
     """The full IB timestep (Section 2, steps (a)-(g)) on the bench workload:
     bin + interpolate, advect, bin + spread the given forces (step (c), the
     elastic model, is outside the library: the forces are a fixed buffer),
@@ -488,11 +498,21 @@ def ib_step_bench(device, stream, X0, ud, G, reps: int, peak: float, N: int, dt:
     stepper.close()
     solve_bytes = 3 * 3 * N ** 3 * 4
     sm = statistics.mean(solve_ms)
+    oracle_ms = None
+    if oracle_solve:
+        from oracle import stokes as ostokes
+        fh = f.double().cpu().numpy()
+        uh = u_a.double().cpu().numpy()
+        t0 = time.perf_counter()
+        ostokes.solve(fh, (N, N, N), (1.0, 1.0, 1.0), rho / dt, mu, uh)
+        oracle_ms = (time.perf_counter() - t0) * 1e3
     return {"workload": f"{N}^3 MAC grid, {npts} points, FP32; per step (a) bin + interpolate, (b) advect, "
                         "(d) bin + spread (forces given), (e) Stokes solve (rho 1, mu 0.01, k = bench dt), "
                         "(f) interpolate, (g) advect",
             "step_ms": statistics.mean(step_ms), "pts_per_s": npts / (statistics.mean(step_ms) / 1e3),
             "stokes_solve_ms": sm,
+            "oracle_stokes_solve_ms": oracle_ms,
+            "oracle_note": "FP64 numpy FFT solve of the same 128^3 MAC problem on the host cores",
             "stokes_roofline": {"bound": "hbm", "achieved_gbs": solve_bytes / (sm / 1e3) / 1e9, "peak": peak,
                                 "frac": solve_bytes / (sm / 1e3) / 1e9 / peak, "algorithmic_bytes": solve_bytes,
                                 "note": "f, u_old read and u written once; the transforms' own passes not counted"}}
@@ -678,7 +698,8 @@ def run_ours(args):
     kern = None
     if args.kernel_reps > 0 and rank == 0:
         try:
-            kern = kernels_bench(device, stream, X, Gs[0], ud, args.kernel_reps, N)
+            kern = kernels_bench(device, stream, X, Gs[0], ud, args.kernel_reps, N, load_peaks()[0],
+                                 0 if args.no_cpu_baseline else 5000)
         except Exception as exc:
             kern = {"error": repr(exc)}
 
@@ -686,7 +707,7 @@ def run_ours(args):
     if args.ib_step_reps > 0 and rank == 0:
         try:
             ibstep = ib_step_bench(device, stream, torch.from_numpy(X0).to(device), ud, Gs[0], args.ib_step_reps,
-                                   load_peaks()[0], N, dt)
+                                   load_peaks()[0], N, dt, oracle_solve=not args.no_cpu_baseline)
         except Exception as exc:
             ibstep = {"error": repr(exc)}
 

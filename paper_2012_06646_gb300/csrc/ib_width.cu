@@ -99,20 +99,24 @@ __device__ __forceinline__ void wweights(T r, T c, T w[S]) {
   }
 }
 
-// One dimension of a point for component a: box offset of its first support
-// node and its s weights.  Returns false when the point's xi = 0 cell is not
-// in the tile (X changed after binning).
-template <typename T, int D, int S, int TS>
-__device__ __forceinline__ bool wpoint_dim(const Job& jb, const Shape& sh, T x, int b, int a, const int T0[3],
-                                           const int TE[3], int& o, T w[S]) {
-  using W = WGeo<D, S, TS>;
-  Cell1<T> cl;
+// Cell of a point in one dimension, relative to the tile: the physical xi = 0
+// cell minus the tile origin, and the exact offsets of both staggerings.
+// Returns false when that cell is not in the tile (X changed after binning).
+template <typename T>
+__device__ __forceinline__ bool wcell_dim(const Job& jb, T x, int b, const int T0[3], const int TE[3], Cell1<T>& cl,
+                                          int& cc) {
   const uint32_t e = point_cell<T>(x, jb, b, cl);
   const int n = jb.n[b];
   const int cphys = ((unsigned)cl.i0 < (unsigned)n) ? cl.i0 : modn(cl.i0, n);
-  const bool inside = e == 0 && (unsigned)(cphys - T0[b]) < (unsigned)TE[b] && (cl.i1 - cl.i0) >= -1 &&
-                      (cl.i1 - cl.i0) <= 0;
-  const bool h = half_stag(sh, a, b);
+  cc = cphys - T0[b];
+  return e == 0 && (unsigned)cc < (unsigned)TE[b] && (cl.i1 - cl.i0) >= -1 && (cl.i1 - cl.i0) <= 0;
+}
+
+// Box offset of the first support node and the s weights of one dimension,
+// for the staggering h (xi = 1/2) or not (xi = 0).
+template <typename T, int D, int S, int TS>
+__device__ __forceinline__ void wselect(const Cell1<T>& cl, int cc, bool h, int& o, T w[S]) {
+  using W = WGeo<D, S, TS>;
   int di;
   T r, c;
   if (W::odd == h) {          // even s with xi = 0, or odd s with xi = 1/2: floor(X N/L)
@@ -128,8 +132,18 @@ __device__ __forceinline__ bool wpoint_dim(const Job& jb, const Shape& sh, T x, 
     r = cl.r1;
     c = cl.c1;
   }
-  o = cphys - T0[b] + di + (W::tlo - W::lo);
+  o = cc + di + (W::tlo - W::lo);
   wweights<T, S>(r, c, w);
+}
+
+// One dimension of a point for component a (wcell_dim, then wselect).
+template <typename T, int D, int S, int TS>
+__device__ __forceinline__ bool wpoint_dim(const Job& jb, const Shape& sh, T x, int b, int a, const int T0[3],
+                                           const int TE[3], int& o, T w[S]) {
+  Cell1<T> cl;
+  int cc;
+  const bool inside = wcell_dim<T>(jb, x, b, T0, TE, cl, cc);
+  wselect<T, D, S, TS>(cl, cc, half_stag(sh, a, b), o, w);
   return inside;
 }
 
@@ -274,6 +288,142 @@ __global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant
   for (int i = lane; i < W::BV; i += 32) dst[i] = box[i];
 }
 
+// ---------------------------------------------------------------------------
+// Three-component fields in 3-D (the MAC velocity grid, or three cell-centred
+// components): one warp per tile owns the three component boxes, so a point's
+// cell map is computed once and each lane's read-modify-writes of the three
+// components are independent (loads first).  Record of a point per component:
+// the s^2 products wx wy h^-d G_a, then the s weights wz; box offsets apart.
+// The boxes are written in the [tile][component][BV] layout of k_spread_w.
+// ---------------------------------------------------------------------------
+template <typename T, int S>
+__global__ void __launch_bounds__(32) k_spread_w3(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
+                                                  T* __restrict__ boxes) {
+  constexpr int TS = 8;
+  using W = WGeo<3, S, TS>;
+  constexpr int RC = S * S + S;                    // record words per component
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t rstart[W::NROWS];
+  __shared__ uint32_t rpre[W::NROWS];
+  __shared__ int roff[kWBatch][3];
+  const int lane = threadIdx.x;
+  T* box = reinterpret_cast<T*>(smem_raw);         // [3][BV]
+  T* rec_s = box + 3 * W::BV;                      // [kWBatch][3 RC]
+  const Job& jb = J.one;
+  const long long gt = blockIdx.x;
+  int T0[3], TE[3];
+  wtile_coords<3, TS>(jb.ntile, jb.n, gt, T0, TE);
+  for (int i = lane; i < 3 * W::BV; i += 32) box[i] = (T)0;
+  const int rows = TE[1] * TE[2];
+  uint32_t M = 0;
+#pragma unroll
+  for (int k = 0; k < W::NROWS / 32; ++k) {
+    const int r = lane + 32 * k;
+    uint32_t st = 0, cnt = 0;
+    if (r < rows) {
+      const int y = T0[1] + r % TE[1];
+      const int z = T0[2] + r / TE[1];
+      const long long cell = T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
+      st = B.count[cell];
+      cnt = B.count[cell + TE[0]] - st;
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    rstart[r] = st;
+    rpre[r] = M + inc - cnt;
+    M += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+  const T* Xg = (const T*)jb.X;
+  const T* Gp = (const T*)jb.G;
+  const T hmd = (T)jb.hmd;
+  auto load_point = [&](uint32_t q, T xs[3], T gs[3]) {
+    int lo = 0;
+#pragma unroll
+    for (int step = W::NROWS / 2; step >= 1; step >>= 1)
+      if (lo + step < rows && rpre[lo + step] <= q) lo += step;
+    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) xs[b] = Xg[li * 3 + b];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) gs[b] = Gp[li * 3 + b];
+  };
+  int loff[W::PER], lxy[W::PER], lz[W::PER];
+  bool lon[W::PER];
+#pragma unroll
+  for (int k = 0; k < W::PER; ++k) {
+    const int q = lane + 32 * k;
+    lon[k] = q < W::NODES;
+    const int tx = q % S, ty = (q / S) % S, tz = q / (S * S);
+    loff[k] = tx + W::BS * (ty + W::BS * tz);
+    lxy[k] = tx + S * ty;
+    lz[k] = S * S + tz;
+  }
+  T xs[3], gs[3] = {(T)0, (T)0, (T)0};
+  if (lane < M) load_point(lane, xs, gs);
+  for (uint32_t base = 0; base < M; base += kWBatch) {
+    if (base + lane < M) {
+      Cell1<T> cl[3];
+      int cc[3];
+      bool inside = true;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) inside = wcell_dim<T>(jb, xs[b], b, T0, TE, cl[b], cc[b]) && inside;
+      if (!inside) atomicOr(B.err, ERR_STALE);     // X changed after binning: contribute nothing, report
+      T* rec = rec_s + lane * 3 * RC;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int o[3];
+        T w[3][S];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) wselect<T, 3, S, TS>(cl[b], cc[b], half_stag(sh, a, b), o[b], w[b]);
+        const T ga = inside ? hmd * gs[a] : (T)0;
+        T* ra = rec + a * RC;
+#pragma unroll
+        for (int ty = 0; ty < S; ++ty)
+#pragma unroll
+          for (int tx = 0; tx < S; ++tx) ra[tx + S * ty] = inside ? (w[0][tx] * ga) * w[1][ty] : (T)0;
+#pragma unroll
+        for (int tz = 0; tz < S; ++tz) ra[S * S + tz] = inside ? w[2][tz] : (T)0;
+        roff[lane][a] = inside ? o[0] + W::BS * (o[1] + W::BS * o[2]) : 0;
+      }
+    }
+    const uint32_t nq = base + kWBatch + lane;     // next batch's point data, fetched during the additions
+    if (nq < M) load_point(nq, xs, gs);
+    __syncwarp();
+    const int cnt = (int)min((uint32_t)kWBatch, M - base);
+    for (int i = 0; i < cnt; ++i) {
+      const T* rp = rec_s + i * 3 * RC;
+      T v[3][W::PER], add[3][W::PER];
+      int idx[3][W::PER];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int off = roff[i][a] + a * W::BV;
+#pragma unroll
+        for (int k = 0; k < W::PER; ++k) {
+          if (lon[k]) {
+            idx[a][k] = off + loff[k];
+            add[a][k] = rp[a * RC + lxy[k]] * rp[a * RC + lz[k]];
+            v[a][k] = box[idx[a][k]];
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < W::PER; ++k)
+          if (lon[k]) box[idx[a][k]] = v[a][k] + add[a][k];
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  T* dst = boxes + gt * (long long)(3 * W::BV);    // [tile][comp][BV]: the three boxes, contiguous
+  for (int i = lane; i < 3 * W::BV; i += 32) dst[i] = box[i];
+}
+
 // Boxes covering node x of a dimension with n nodes and ntile tiles: every
 // unwrapped copy v = x + k n inside some tile's used box range (offsets
 // 0 .. TE + s - 1 from the box origin), in increasing v, then tile.
@@ -301,6 +451,46 @@ __device__ __forceinline__ int wcover(int x, int n, int ntile, int* tl, int* of)
   return cnt;
 }
 
+// Fast cover list for n >= TS + s (a box never wraps onto its own tile): in
+// increasing unwrapped position, then tile -- the periodic copy x - n in tile
+// 0, the previous tile, the node's own tile, the next tile, and the copy
+// x + n in the last two tiles -- at most 3 at once, the same entries in the
+// same order as wcover.
+struct WCover3 {        // three scalar slots (no dynamically indexed array: the list stays in registers)
+  int t0, o0, t1, o1, t2, o2, n;
+  __device__ __forceinline__ void push(int tt, int oo) {
+    if (n == 0) { t0 = tt; o0 = oo; } else if (n == 1) { t1 = tt; o1 = oo; } else { t2 = tt; o2 = oo; }
+    ++n;
+  }
+  __device__ __forceinline__ int t(int i) const { return i == 0 ? t0 : (i == 1 ? t1 : t2); }
+  __device__ __forceinline__ int o(int i) const { return i == 0 ? o0 : (i == 1 ? o1 : o2); }
+};
+
+template <int S, int TS>
+__device__ __forceinline__ WCover3 wcover_fast(int x, int n, int ntile) {
+  using W = WGeo<3, S, TS>;
+  WCover3 c;
+  c.n = 0;
+  c.t0 = c.o0 = c.t1 = c.o1 = c.t2 = c.o2 = 0;
+  const int t = x / TS, xl = x - t * TS;
+  const int last = ntile - 1, te_last = n - last * TS;
+  if (x - n >= W::lo) c.push(0, x - n - W::lo);                       // copy x - n in tile 0
+  if (t >= 1 && xl + TS - W::lo < TS + S) c.push(t - 1, xl + TS - W::lo);
+  c.push(t, xl - W::lo);
+  if (t + 1 <= last && xl - TS - W::lo >= 0) {
+    const int te = min(TS, n - (t + 1) * TS);
+    if (xl - TS - W::lo < te + S) c.push(t + 1, xl - TS - W::lo);
+  }
+  // copy x + n: the last tile, and the one before it when the last tile is short
+  if (ntile >= 2) {
+    const int o2 = x + n - (last - 1) * TS - W::lo;
+    if (o2 < TS + S) c.push(last - 1, o2);
+  }
+  const int o1 = x + n - last * TS - W::lo;
+  if (o1 < te_last + S) c.push(last, o1);
+  return c;
+}
+
 template <typename T, int D, int S, int TS>
 __global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ Jobs J, const Shape sh,
                                                          const T* __restrict__ boxes, int accumulate) {
@@ -313,6 +503,54 @@ __global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ 
   const long long q = lc / jb.n[0];
   x[1] = (int)(q % jb.n[1]);
   x[2] = (D == 3) ? (int)(q / jb.n[1]) : 0;
+  const int nc = sh.ncomp;
+  T* f = (T*)jb.f;
+  bool fast = nc <= 4;
+#pragma unroll
+  for (int b = 0; b < D; ++b) fast = fast && jb.n[b] >= TS + S;
+  if (fast) {
+    const WCover3 cx = wcover_fast<S, TS>(x[0], jb.n[0], jb.ntile[0]);
+    const WCover3 cy = wcover_fast<S, TS>(x[1], jb.n[1], jb.ntile[1]);
+    WCover3 cz;
+    if (D == 3) {
+      cz = wcover_fast<S, TS>(x[2], jb.n[2], jb.ntile[2]);
+    } else {
+      cz.n = 1;
+      cz.t0 = cz.o0 = cz.t1 = cz.o1 = cz.t2 = cz.o2 = 0;
+    }
+    // up to 27 boxes, all entries loaded before the sums (in the fixed order)
+    T S4[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+    for (int iz = 0; iz < 3; ++iz) {
+      if (iz >= cz.n) break;
+#pragma unroll
+      for (int iy = 0; iy < 3; ++iy) {
+        if (iy >= cy.n) break;
+        const long long trow = cy.t(iy) + (long long)jb.ntile[1] * cz.t(iz);
+        const int orow = (cz.o(iz) * W::BS + cy.o(iy)) * W::BS;
+        T v[3][4];
+#pragma unroll
+        for (int ix = 0; ix < 3; ++ix) {
+          const long long tile = cx.t(ix) + (long long)jb.ntile[0] * trow;
+          const T* bp = boxes + tile * nc * W::BV + orow + cx.o(ix);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) v[ix][a] = (ix < cx.n && a < nc) ? bp[a * W::BV] : (T)0;
+        }
+#pragma unroll
+        for (int ix = 0; ix < 3; ++ix)
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            if (ix < cx.n) S4[a] += v[ix][a];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (a >= nc) break;
+      const long long o = a * jb.ncell + lc;
+      f[o] = accumulate ? f[o] + S4[a] : S4[a];
+    }
+    return;
+  }
   int tl[3][kWCover], of[3][kWCover], nco[3];
 #pragma unroll
   for (int b = 0; b < D; ++b) nco[b] = wcover<S, TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
@@ -321,8 +559,6 @@ __global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ 
     tl[2][0] = 0;
     of[2][0] = 0;
   }
-  const int nc = sh.ncomp;
-  T* f = (T*)jb.f;
   for (int a = 0; a < nc; ++a) {
     T s = 0;
     for (int iz = 0; iz < nco[2]; ++iz)
@@ -346,8 +582,8 @@ __global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ 
 // the tile (cell order) and sums their s^d support per component.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int S, int TS>
-__global__ void __launch_bounds__(kWInterpThreads) k_interp_w(const __grid_constant__ Jobs J, const Shape sh,
-                                                               const Bins B, const T scale) {
+__global__ void __launch_bounds__(kWInterpThreads, sizeof(T) == 4 ? 6 : 4) k_interp_w(const __grid_constant__ Jobs J, const Shape sh,
+                                                                  const Bins B, const T scale) {
   using W = WGeo<D, S, TS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* box = reinterpret_cast<T*>(smem_raw);
@@ -409,17 +645,21 @@ __global__ void __launch_bounds__(kWInterpThreads) k_interp_w(const __grid_const
 #pragma unroll
     for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
     T* U = (T*)jb.U + li * nc;
+    Cell1<T> cl[D];
+    int cc[D];
+    bool inside = true;
+#pragma unroll
+    for (int b = 0; b < D; ++b) inside = wcell_dim<T>(jb, xs[b], b, T0, TE, cl[b], cc[b]) && inside;
+    if (!inside) {
+      atomicOr(B.err, ERR_STALE);        // X changed after binning: no gather outside the box
+      for (int a = 0; a < nc; ++a) U[a] = (T)NAN;
+      continue;
+    }
     for (int a = 0; a < nc; ++a) {
       int o[3] = {0, 0, 0};
       T w[3][S];
-      bool inside = true;
 #pragma unroll
-      for (int b = 0; b < D; ++b) inside = wpoint_dim<T, D, S, TS>(jb, sh, xs[b], b, a, T0, TE, o[b], w[b]) && inside;
-      if (!inside) {
-        atomicOr(B.err, ERR_STALE);      // X changed after binning: no gather outside the box
-        U[a] = (T)NAN;
-        continue;
-      }
+      for (int b = 0; b < D; ++b) wselect<T, D, S, TS>(cl[b], cc[b], half_stag(sh, a, b), o[b], w[b]);
       const T* bp = box + a * W::BV + (o[2] * W::BS + o[1]) * W::BS + o[0];
       T acc = 0;
 #pragma unroll
@@ -450,6 +690,17 @@ cudaError_t spread_w(const Jobs& J, const Shape& sh, const Bins& B, void* boxes,
                      cudaStream_t s) {
   using W = WGeo<D, S, TS>;
   const long long nunits = ntiles * sh.ncomp;
+  if constexpr (D == 3 && TS == 8 && S == 3) {
+    if (sh.ncomp == 3 && ntiles > 0) {             // three components: one warp per tile for all of them
+      const size_t bytes = (size_t)(3 * W::BV + kWBatch * 3 * (S * S + S)) * sizeof(T);
+      allow_smem_w(k_spread_w3<T, S>, bytes);
+      k_spread_w3<T, S><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes);
+      if (J.one.ncell > 0)
+        k_combine_w<T, D, S, TS><<<grid_for(J.one.ncell, kThreads), kThreads, 0, s>>>(J, sh, (const T*)boxes,
+                                                                                       accumulate ? 1 : 0);
+      return cudaGetLastError();
+    }
+  }
   if (nunits > 0) {
     const size_t bytes = (size_t)kWWarps * (W::BV + kWBatch * W::REC) * sizeof(T);
     allow_smem_w(k_spread_w<T, D, S, TS>, bytes);

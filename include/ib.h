@@ -95,7 +95,7 @@ enum { IB_F32 = 0, IB_F64 = 1 };
  * plan works on the grid extended by 8 ghost nodes per bounded dimension (the
  * de facto cells of the extended grid of Section 3.1, with the same spacing)
  * and copies the domain's nodes out of it (spreading) or into it with zero
- * ghosts (interpolation).  ib_pos_grad and ib_spread_paper return
+ * ghosts (interpolation, position gradients).  ib_spread_paper returns
  * IB_ERR_NOT_IMPLEMENTED on such plans; ib_plan_bins describes the cells of
  * the extended grid. */
 #define IB_PLAN_BOUNDED_X 0x2u

@@ -314,10 +314,17 @@ int or_interp(const or_grid* g, long long n, const double* X, const double* u, d
 
 int or_pos_grad(const or_grid* g, long long n, const double* X, const double* field, const double* v,
                 double* D, double* Dabs) {
-  if (check_grid(g) || g->bounded) return 1;   /* gradients: periodic grids only */
+  if (check_grid(g)) return 1;
   long long ncell = ncell_of(g);
   int nshift = nshift_of(g);
   for (long long j = 0; j < n; ++j) {
+    if (!point_in_domain(g, X + j * g->dim)) {   /* outside a bounded dimension: no gradient */
+      for (int b = 0; b < g->dim; ++b) {
+        D[j * g->dim + b] = NAN;
+        if (Dabs) Dabs[j * g->dim + b] = 0.0;
+      }
+      continue;
+    }
     for (int b = 0; b < g->dim; ++b) {
       double acc = 0.0, aabs = 0.0;
       /* d r_b / d X_b = N_b / L_b, and the weight depends on r_b through phi(t_b - r_b). */
@@ -332,7 +339,9 @@ int or_pos_grad(const or_grid* g, long long n, const double* X, const double* fi
           double w = chain * or_dphi(g->kernel, karg(t[b], c.r[b]));
           for (int e = 0; e < g->dim; ++e)
             if (e != b) w *= or_phi(g->kernel, karg(t[e], c.r[e]));
-          double term = v[j * g->ncomp + a] * w * field[a * ncell + node_index(g, &c, t)];
+          long long k = node_index(g, &c, t);
+          if (k < 0) continue;
+          double term = v[j * g->ncomp + a] * w * field[a * ncell + k];
           acc += term;
           aabs += fabs(term);
         }

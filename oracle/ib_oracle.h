@@ -91,7 +91,8 @@ int or_spread(const or_grid* g, long long n, const double* X, const double* G, d
  * NULL, receives sum_k |weight * u| per point and component. */
 int or_interp(const or_grid* g, long long n, const double* X, const double* u, double* U, double* Uabs);
 
-/* Position derivative of the interpolation sum contracted with v (periodic grids):
+/* Position derivative of the interpolation sum contracted with v (NaN for a
+ * point outside a bounded dimension):
  *   D_{j,b} = sum_a v_{j,a} sum_k (d/dX_b) [prod_c phi(t_c - r_c)] field_a[k],
  * (d/dX_b) r_b = N_b / L_b.  For interpolation, dLoss/dX = D(field = u, v = dLoss/dU);
  * for spreading, dLoss/dX = h^-d D(field = dLoss/df, v = G).  D is (n, dim). */

@@ -430,7 +430,7 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
   if (npts > 0 && (!field || !v || !D)) return IB_ERR_INVALID_ARG;
   if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
   if (!isfinite(scale)) return IB_ERR_INVALID_ARG;
-  if (kernel_width(p->desc.kernel) != 4 || p->bounded) return IB_ERR_NOT_IMPLEMENTED;
+  if (kernel_width(p->desc.kernel) != 4) return IB_ERR_NOT_IMPLEMENTED;
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare(p, npts, X, flags, s);
   if (st != IB_OK) return st;
@@ -440,6 +440,11 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
   J.one.npts = npts;
   J.one.X = X;
   J.njobs = 1;
+  if (p->bounded) {     // the field on the extended grid, zero on the ghost nodes
+    if (launch_bounds_pad(p->job, p->desc.ncomp, p->desc.dtype, field, p->gridx, s) != cudaSuccess)
+      return IB_ERR_CUDA;
+    field = p->gridx;
+  }
   if (launch_pos_grad(J, p->sh, call_bins(p, npts), p->desc.dtype, field, v, scale, D, s) != cudaSuccess)
     return IB_ERR_CUDA;
   return IB_OK;

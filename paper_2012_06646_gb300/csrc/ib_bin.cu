@@ -39,9 +39,7 @@ __device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, cons
   for (int b = 0; b < D; ++b) {
     Cell1<T> c;
     err |= point_cell<T>(X[b], jb, b, c);
-    // Bounded dimension: the position must lie in [0, L] (cell 0 .. nin - 1, or
-    // exactly the far face).
-    if (jb.bnd[b] && !(c.i0 >= 0 && (c.i0 < jb.nin[b] || (c.i0 == jb.nin[b] && c.r0 == (T)0)))) err |= ERR_RANGE;
+    if (!in_bounds(jb, b, c)) err |= ERR_RANGE;   // bounded dimension: outside [0, L]
     const int n = jb.n[b];
     const int ib = (key_comp >= 0 && half_stag(sh, key_comp, b)) ? c.i1 : c.i0;
     const int cb = ((unsigned)ib < (unsigned)n) ? ib : modn(ib, n);

@@ -250,6 +250,14 @@ __device__ __forceinline__ uint32_t point_cell<double>(double X, const Job& jb, 
   return cell_fp64<double>(X, jb.scale[b], c);
 }
 
+// Bounded (non-periodic) dimension b: the position must lie in [0, L_b], i.e.
+// its xi = 0 cell is 0 .. nin - 1, or nin exactly on the far face.  Always true
+// for periodic dimensions.
+template <typename T>
+__device__ __forceinline__ bool in_bounds(const Job& jb, int b, const Cell1<T>& c) {
+  return !jb.bnd[b] || (c.i0 >= 0 && (c.i0 < jb.nin[b] || (c.i0 == jb.nin[b] && c.r0 == (T)0)));
+}
+
 // x / d for 0 <= x < 2^32 and d >= 1, with M = floor(2^64 / d) + 1 (M unused for
 // d = 1): floor(x M / 2^64) = floor(x / d) because x d < 2^64.
 __device__ __forceinline__ int udiv(int x, int d, unsigned long long M) {

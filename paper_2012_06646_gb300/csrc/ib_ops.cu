@@ -1125,7 +1125,10 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad(const __grid_constant__ J
   Cell1<T> c[D];
   uint32_t err = 0;
 #pragma unroll
-  for (int b = 0; b < D; ++b) err |= point_cell<T>(Xp[b], jb, b, c[b]);
+  for (int b = 0; b < D; ++b) {
+    err |= point_cell<T>(Xp[b], jb, b, c[b]);
+    if (!in_bounds(jb, b, c[b])) err |= ERR_RANGE;
+  }
   if (err) {
 #pragma unroll
     for (int b = 0; b < D; ++b) Dp[b] = (T)NAN;

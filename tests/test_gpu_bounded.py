@@ -141,12 +141,34 @@ def test_bounded_unsupported_calls(P):
     from paper_2012_06646_gb300._abi import IBError
     plan = P(3, (16, 16, 16), (1.0, 1.0, 1.0), max_points=10, bounded=(True, False, False))
     X = dev(ib_inputs.uniform_points(1, 10, (1.0, 1.0, 1.0), 3))
-    u = dev(ib_inputs.normal_array(2, (3, 16, 16, 16)))
     v = dev(ib_inputs.normal_array(3, (10, 3)))
-    for call in (lambda: plan.pos_grad(X, u, v), lambda: plan.spread_paper(X, v, algorithm=4)):
-        with pytest.raises(IBError) as e:
-            call()
-        assert e.value.status == _abi.IB_ERR_NOT_IMPLEMENTED
+    with pytest.raises(IBError) as e:
+        plan.spread_paper(X, v, algorithm=4)
+    assert e.value.status == _abi.IB_ERR_NOT_IMPLEMENTED
+    plan.close()
+
+
+@pytest.mark.parametrize("mac", [True, False])
+def test_bounded_pos_grad_matches_oracle(P, orc, mac):
+    """Walls in x and z, points on and near the walls included; tolerance as the periodic gradients."""
+    from paper_2012_06646_gb300._abi import IB_ERR_RANGE, IBError
+    n, L, npts = (20, 16, 24), (1.0, 0.8, 1.2), 800
+    bounded = (True, False, True)
+    plan = P(3, n, L, grid="mac" if mac else "cc", max_points=npts + 1, bounded=bounded)
+    g = orc.Grid(dim=3, n=n, L=L, mac=mac, bounded=bounded)
+    X = np.concatenate([ib_inputs.uniform_points(61, npts, L, 3),
+                        np.array([[-1e-3, 0.4, 0.6]], dtype=np.float32)])      # outside the x wall
+    X[:20, 0] = 0.0
+    X[20:40, 2] = np.float32(1.2) - np.float32(2 ** -22)
+    field = ib_inputs.normal_array(62, plan.grid_shape())
+    v = ib_inputs.normal_array(63, (npts + 1, 3))
+    D = host(plan.pos_grad(dev(X), dev(field), dev(v), scale=2.5))
+    with pytest.raises(IBError) as e:
+        plan.check()
+    assert e.value.status == IB_ERR_RANGE
+    D_ref, Dabs = orc.pos_grad(g, X, field, v)
+    assert np.isnan(D[-1]).all() and np.isnan(D_ref[-1]).all()
+    assert_interp_close(D[:-1], 2.5 * D_ref[:-1], 2.5 * Dabs[:-1], rel=2e-5, what="pos_grad")
     plan.close()
 
 

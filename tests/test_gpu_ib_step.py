@@ -38,7 +38,7 @@ def tether_torch(Xs, X0, L):
 
 
 def oracle_loop(orc, n, L, X, u, X0, rho, mu, k, steps):
-    g = orc.Grid(3, n, L, mac=True)
+    g = orc.Grid(len(n), n, L, mac=True)
     Lv = np.asarray(L, dtype=np.float64)
     X = X.astype(np.float64)
     u = u.astype(np.float64)
@@ -89,4 +89,27 @@ def test_ib_step_matches_oracle_loop(orc, dtype, steps):
     assert periodic_err(Xg, Xw, L).max() <= xtol
     assert np.abs(ug - uw).max() <= utol * np.abs(uw).max()
     assert disp > 100 * xtol                 # the points moved by much more than the tolerance
+    stepper.close()
+
+
+def test_ib_step_2d_matches_oracle_loop(orc):
+    """The same loop in 2-D (MAC grid, FP64, three steps)."""
+    from paper_2012_06646_gb300 import build
+    build()
+    from paper_2012_06646_gb300.step import IBStep
+    n, L = (40, 24), (1.0, 0.6)
+    rho, mu, k, npts, steps = 1.0, 0.02, 0.01, 300, 3
+    X = ib_inputs.uniform_points(71, npts, L, 2, dtype=np.float64)
+    X0 = np.mod(X + 0.01 * ib_inputs.normal_array(72, (npts, 2), dtype=np.float64), np.asarray(L))
+    u = 0.1 * ib_inputs.normal_array(73, (2, 24, 40), dtype=np.float64, purpose="u")
+    stepper = IBStep(2, n, L, rho, mu, k, dtype=torch.float64, max_points=npts)
+    Xd, ud = dev(X), dev(u)
+    X0d = dev(X0)
+    Lt = torch.tensor(L, dtype=torch.float64, device="cuda")
+    for _ in range(steps):
+        Xd, ud = stepper.step(Xd, ud, lambda Xs: tether_torch(Xs, X0d, Lt))
+    stepper.plan_n.check()
+    Xw, uw = oracle_loop(orc, n, L, X, u, X0, rho, mu, k, steps)
+    assert periodic_err(host(Xd), Xw, L).max() <= 1e-11
+    assert np.abs(host(ud) - uw).max() <= 1e-10 * np.abs(uw).max()
     stepper.close()

@@ -102,3 +102,30 @@ def test_wall_point_keeps_half_or_more(orc, kernel):
         keep0 = (1.0 + orc.phi(kernel, 0.0)[0]) / 2 if x == 0.0 else (1.0 - orc.phi(kernel, 0.0)[0]) / 2
         assert tot[0] == pytest.approx(keep0 * G[0, 0], abs=1e-14)
         assert np.allclose(tot[1:], 0.5 * G[0, 1:], atol=1e-14)
+
+
+@pytest.mark.parametrize("mac", [True, False])
+def test_bounded_position_gradients_match_central_differences(orc, mac):
+    """Walls in x and z; points within the support of a wall (at least 4 eps inside): the analytic
+    gradient of loss = sum(v . U(X)) against FP64 central differences, eps = 1e-6."""
+    n, L = (12, 10, 8), (1.0, 0.8, 0.64)
+    bounded = (True, False, True)
+    g = orc.Grid(dim=3, n=n, L=L, mac=mac, bounded=bounded, ncomp=3)
+    h = np.array(L) / np.array(n)
+    X = ib_inputs.uniform_points(51, 120, L, 3, dtype=np.float64)
+    X[:40, 0] = 1e-4 + 1.9 * h[0] * ib_inputs.uniform_points(52, 40, (1.0,), 1, dtype=np.float64)[:, 0]
+    X[40:80, 2] = L[2] - 1e-4 - 1.9 * h[2] * ib_inputs.uniform_points(53, 40, (1.0,), 1, dtype=np.float64)[:, 0]
+    field = ib_inputs.normal_array(54, g.shape(), dtype=np.float64)
+    v = ib_inputs.normal_array(55, (120, 3), dtype=np.float64)
+    D, _ = orc.pos_grad(g, X, field, v)
+    eps = 1e-6
+    fd = np.zeros_like(X)
+    for b in range(3):
+        Xp, Xm = X.copy(), X.copy()
+        Xp[:, b] += eps
+        Xm[:, b] -= eps
+        fd[:, b] = (np.sum(v * orc.interp(g, Xp, field)[0], 1) - np.sum(v * orc.interp(g, Xm, field)[0], 1)) / (2 * eps)
+    assert np.max(np.abs(D - fd)) <= 1e-6 * np.max(np.abs(D))
+    # outside a wall: NaN
+    Xo = np.array([[-1e-3, 0.3, 0.3], [0.5, 0.3, L[2] + 1e-3]])
+    assert np.isnan(orc.pos_grad(g, Xo, field, v[:2])[0]).all()

@@ -69,6 +69,8 @@ def parse():
                     help="timed repetitions of the clustered red-cell membrane workload (0: skip)")
     ap.add_argument("--paper-reps", type=int, default=3,
                     help="timed repetitions of the paper's spreading algorithms 4-6 on the workload (0: skip)")
+    ap.add_argument("--grad-reps", type=int, default=10,
+                    help="timed repetitions of the differentiable spread (forward and backward; 0: skip)")
     ap.add_argument("--kernel-reps", type=int, default=10,
                     help="timed repetitions of spread + interpolate with each other kernel (0: skip)")
     ap.add_argument("--ib-step-reps", type=int, default=10,
@@ -455,6 +457,66 @@ def kernels_bench(device, stream, X, G, u, reps: int, N: int, peak: float, oracl
             "kernels": out}
 
 
+def autograd_bench(device, stream, reps: int, N: int, npts: int = 200_000, seed: int = 5):
+    """The differentiable workload: 128^3 MAC grid, 2 x 10^5 uniform points,
+    f = spread(X, G) through the autograd Function, loss = sum(w f) with
+    w ~ N(0, 1), then loss.backward(): binning, the adjoint interpolation
+    (dloss/dG) and the position gradient (dloss/dX).  CUDA events on the
+    stream around forward + backward, L2 flushed before each repetition."""
+    import torch
+    import ib_inputs
+    from paper_2012_06646_gb300 import autograd as ag
+    from paper_2012_06646_gb300.plan import Plan
+    X = torch.from_numpy(ib_inputs.uniform_points(seed, npts, (1.0, 1.0, 1.0), 3)).to(device).requires_grad_(True)
+    G = torch.from_numpy(ib_inputs.normal_array(seed + 1, (npts, 3))).to(device).requires_grad_(True)
+    w = torch.from_numpy(ib_inputs.normal_array(seed + 2, (3, N, N, N))).to(device)
+    plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", max_points=npts, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    ms = []
+    with torch.cuda.stream(stream):
+        for r in range(reps + 2):
+            flush.fill_(r & 0xFF)
+            X.grad = None
+            G.grad = None
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f = ag.spread(X, G, plan)
+            loss = (w * f).sum()
+            loss.backward()
+            b.record(stream)
+            b.synchronize()
+            if r >= 2:
+                ms.append(a.elapsed_time(b))
+    plan.check(stream)
+    ok = bool(torch.isfinite(X.grad).all().item() and torch.isfinite(G.grad).all().item())
+    # The same forward and backward captured once as a CUDA graph (the
+    # library's calls are stream-ordered launches), replayed per repetition.
+    gms = []
+    with torch.cuda.stream(stream):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            fg = ag.spread(X, G, plan)
+            gX, gG = torch.autograd.grad((w * fg).sum(), (X, G))
+        for r in range(reps + 2):
+            flush.fill_(r & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+            b.synchronize()
+            if r >= 2:
+                gms.append(a.elapsed_time(b))
+    plan.check(stream)
+    same = bool(torch.equal(gX, X.grad) and torch.equal(gG, G.grad))
+    plan.close()
+    t, tg = statistics.mean(ms), statistics.mean(gms)
+    return {"workload": f"{N}^3 MAC grid, {npts} uniform points, FP32; f = spread(X, G), loss = sum(w f), "
+                        "backward: dloss/dG by adjoint interpolation, dloss/dX by the position gradient",
+            "step_ms": t, "pts_per_s": npts / (t / 1e3), "gradients_finite": ok,
+            "step_ms_cuda_graph": tg, "pts_per_s_cuda_graph": npts / (tg / 1e3),
+            "graph_gradients_equal_eager": same}
+
+
 def ib_step_bench(device, stream, X0, ud, G, reps: int, peak: float, N: int, dt: float,
                   rho: float = 1.0, mu: float = 1.0e-2, oracle_solve: bool = True):
     """The full IB timestep (Section 2, steps (a)-(g)) on the bench workload:
@@ -734,6 +796,13 @@ def run_ours(args):
         except Exception as exc:
             paper = {"error": repr(exc)}
 
+    grad = None
+    if args.grad_reps > 0 and rank == 0:
+        try:
+            grad = autograd_bench(device, stream, args.grad_reps, N)
+        except Exception as exc:
+            grad = {"error": repr(exc)}
+
     kern = None
     if args.kernel_reps > 0 and rank == 0:
         try:
@@ -805,6 +874,7 @@ def run_ours(args):
             "serving": serving,
             "membranes": membranes,
             "paper_algorithms": paper,
+            "differentiable": grad,
             "kernel_widths": kern,
             "ib_step": ibstep}
     print(json.dumps(line), flush=True)

@@ -11,7 +11,8 @@ disc-interp; S* = S^T, Eqs. matrix-interp and matrix-spread).  Hence
 
 where D(field, v)_{j,b} = sum_a v_{j,a} sum_k field_a[k] dW_jk/dX_{j,b}, the
 position derivative of the weights.  Every backward step runs in the CUDA
-kernels of libibgb.so.
+kernels of libibgb.so.  The backward reuses the forward call's bins when the
+plan has not re-binned since and X is the same, unmodified tensor.
 """
 
 from __future__ import annotations
@@ -21,11 +22,25 @@ import torch
 from .plan import Plan
 
 
+def _bins_token(plan: Plan, Xc, X):
+    """What must be unchanged for the bins of the forward call to serve the backward."""
+    return (plan.bin_epoch, Xc.data_ptr(), X._version)
+
+
+def _ensure_bins(ctx, plan: Plan, Xc, X) -> None:
+    """Re-bin X unless the plan still holds the bins the forward call made for the
+    same, unmodified positions."""
+    if _bins_token(plan, Xc, X) != ctx.bins:
+        plan.bin(Xc)
+
+
 class SpreadFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, G, plan: Plan, compensated: bool = False):
-        f = plan.spread(X.detach().contiguous(), G.detach().contiguous(), compensated=compensated)
+        Xc = X.detach().contiguous()
+        f = plan.spread(Xc, G.detach().contiguous(), compensated=compensated)
         ctx.plan = plan
+        ctx.bins = _bins_token(plan, Xc, X)
         ctx.save_for_backward(X, G)
         return f
 
@@ -36,7 +51,7 @@ class SpreadFunction(torch.autograd.Function):
         gf = gf.contiguous()
         Xc = X.detach().contiguous()
         gX = gG = None
-        plan.bin(Xc)
+        _ensure_bins(ctx, plan, Xc, X)
         if ctx.needs_input_grad[1]:
             gG = plan.interpolate(Xc, gf, reuse_bins=True, adjoint=True)
         if ctx.needs_input_grad[0]:
@@ -47,8 +62,10 @@ class SpreadFunction(torch.autograd.Function):
 class InterpolateFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, u, plan: Plan):
-        U = plan.interpolate(X.detach().contiguous(), u.detach().contiguous())
+        Xc = X.detach().contiguous()
+        U = plan.interpolate(Xc, u.detach().contiguous())
         ctx.plan = plan
+        ctx.bins = _bins_token(plan, Xc, X)
         ctx.save_for_backward(X, u)
         return U
 
@@ -59,7 +76,7 @@ class InterpolateFunction(torch.autograd.Function):
         gU = gU.contiguous()
         Xc = X.detach().contiguous()
         gX = gu = None
-        plan.bin(Xc)
+        _ensure_bins(ctx, plan, Xc, X)
         if ctx.needs_input_grad[1]:
             gu = plan.spread(Xc, gU, reuse_bins=True, adjoint=True)
         if ctx.needs_input_grad[0]:

@@ -77,6 +77,10 @@ class Plan:
         with torch.cuda.device(self.device):
             check(self.lib.ib_plan_create(ctypes.byref(d), ctypes.byref(h)), "ib_plan_create")
         self.handle = h
+        # Incremented by every call that replaces the plan's bins (binning, a call
+        # without reuse_bins, the paper's algorithms, an in-place position update):
+        # callers that keep bins across calls compare it to decide whether to re-bin.
+        self.bin_epoch = 0
 
     # -- helpers ---------------------------------------------------------
     def grid_shape(self):
@@ -107,6 +111,7 @@ class Plan:
     def bin(self, X, stream=None):
         n = self._points(X)
         check(self.lib.ib_bin(self.handle, n, _ptr(X), _stream_ptr(stream)), "ib_bin")
+        self.bin_epoch += 1
 
     def spread(self, X, G, f=None, accumulate=False, compensated=False, reuse_bins=False, adjoint=False,
                stream=None):
@@ -118,6 +123,8 @@ class Plan:
         flags = ((_abi.IB_ACCUMULATE if accumulate else 0) | (_abi.IB_COMPENSATED if compensated else 0)
                  | (_abi.IB_REUSE_BINS if reuse_bins else 0) | (_abi.IB_ADJOINT if adjoint else 0))
         check(self.lib.ib_spread(self.handle, n, _ptr(X), _ptr(G), _ptr(f), flags, _stream_ptr(stream)), "ib_spread")
+        if not reuse_bins:
+            self.bin_epoch += 1
         return f
 
     def spread_paper(self, X, G, algorithm: int = 4, beta: int = 8, f=None, buffer=None, stream=None):
@@ -131,6 +138,7 @@ class Plan:
         self._check(f, self.grid_shape(), "f")
         if algorithm == 5 and buffer is None:
             buffer = torch.empty((beta,) + tuple(reversed(self.n)), dtype=self.dtype, device=self.device)
+        self.bin_epoch += 1
         check(self.lib.ib_spread_paper(self.handle, n, _ptr(X), _ptr(G), _ptr(f), int(algorithm), int(beta),
                                        _ptr(buffer), _stream_ptr(stream)), "ib_spread_paper")
         return f
@@ -142,6 +150,8 @@ class Plan:
             U = self._new((n, self.ncomp))
         self._check(U, (n, self.ncomp), "U")
         flags = (_abi.IB_REUSE_BINS if reuse_bins else 0) | (_abi.IB_ADJOINT if adjoint else 0)
+        if not reuse_bins:
+            self.bin_epoch += 1
         check(self.lib.ib_interpolate(self.handle, n, _ptr(X), _ptr(u), _ptr(U), flags, _stream_ptr(stream)),
               "ib_interpolate")
         return U
@@ -154,6 +164,8 @@ class Plan:
             D = self._new((n, self.dim))
         self._check(D, (n, self.dim), "D")
         flags = _abi.IB_REUSE_BINS if reuse_bins else 0
+        if not reuse_bins:
+            self.bin_epoch += 1
         check(self.lib.ib_pos_grad(self.handle, n, _ptr(X), _ptr(field), _ptr(v), float(scale), _ptr(D), flags,
                                    _stream_ptr(stream)), "ib_pos_grad")
         return D
@@ -164,6 +176,8 @@ class Plan:
         if out is None:
             out = self._new((n, self.dim))
         self._check(out, (n, self.dim), "out")
+        if out.data_ptr() == X.data_ptr():
+            self.bin_epoch += 1
         check(self.lib.ib_advect(self.handle, n, _ptr(X), _ptr(U), float(dt), _ptr(out), _stream_ptr(stream)),
               "ib_advect")
         return out

@@ -99,3 +99,34 @@ def test_gradcheck_fp64(mods):
     u = dev(ib_inputs.normal_array(83, plan.grid_shape(), dtype=np.float64)).requires_grad_(True)
     assert torch.autograd.gradcheck(lambda x, gg: ag.spread(x, gg, plan), (X, G), eps=1e-6, atol=1e-5, rtol=1e-4)
     assert torch.autograd.gradcheck(lambda x, uu: ag.interpolate(x, uu, plan), (X, u), eps=1e-6, atol=1e-5, rtol=1e-4)
+
+
+def test_backward_rebins_after_other_calls(mods, orc):
+    """The backward reuses the forward's bins only while the plan holds them: here the plan
+    interpolates other points between forward and backward, so the backward must bin X again."""
+    Plan, ag = mods
+    n, npts = (16, 16, 16), 300
+    plan = Plan(3, n, (1.0, 1.0, 1.0), max_points=npts)
+    X = ib_inputs.uniform_points(81, npts, (1.0, 1.0, 1.0), 3)
+    G = ib_inputs.normal_array(82, (npts, 3))
+    w = ib_inputs.normal_array(83, plan.grid_shape())
+    Xd = dev(X).requires_grad_(True)
+    Gd = dev(G).requires_grad_(True)
+    f = ag.spread(Xd, Gd, plan)
+    epoch = plan.bin_epoch
+    plan.interpolate(dev(ib_inputs.uniform_points(84, npts, (1.0, 1.0, 1.0), 3)), dev(w))
+    assert plan.bin_epoch == epoch + 1
+    gX, gG = torch.autograd.grad((dev(w) * f).sum(), (Xd, Gd))
+    plan.check()
+    g = orc.Grid(dim=3, n=n, L=(1.0, 1.0, 1.0))
+    hmd = orc.inv_cell_volume(g)
+    Uw, Uwabs = orc.interp(g, X, w)
+    assert_interp_close(host(gG), hmd * Uw, hmd * Uwabs, what="dL/dG")
+    D, Dabs = orc.pos_grad(g, X, w, G)
+    assert_interp_close(host(gX), hmd * D, hmd * Dabs, rel=2e-5, what="dL/dX")
+    # and with nothing in between, the bins are reused (no new binning)
+    f = ag.spread(Xd, Gd, plan)
+    epoch = plan.bin_epoch
+    gX2, _ = torch.autograd.grad((dev(w) * f).sum(), (Xd, Gd))
+    assert plan.bin_epoch == epoch
+    assert torch.equal(gX2, gX)

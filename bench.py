@@ -115,10 +115,15 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+# Sources of the kernels whose DRAM counters profiles/traffic.txt records (the
+# spreading and interpolation kernels and the headers they are built from).
+TRAFFIC_SOURCES = ("ib_ops.cu", "ib_common.cuh", "ib_internal.h")
+
+
 def csrc_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2012_06646_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in TRAFFIC_SOURCES:
         with open(os.path.join(d, name), "rb") as fh:
             h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]

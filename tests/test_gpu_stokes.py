@@ -40,6 +40,11 @@ CASES = [
     ((64, 40), (2.0, 1.25), 4.0, 0.1, True, np.float32),
     ((2, 2, 2), (1.0, 1.0, 1.0), 1.0, 1.0, True, np.float64),
     ((128, 128, 128), (1.0, 1.0, 1.0), 1.0e3, 1.0e-2, True, np.float32),
+    # n2 a power of two: (y, x) plane transforms and the z-column kernel
+    ((24, 20, 16), (1.0, 0.8, 0.5), 3.0, 0.2, True, np.float64),
+    ((17, 12, 32), (1.0, 1.0, 2.0), 1.0, 0.05, True, np.float32),      # odd n0: a partial block of kx
+    ((8, 6, 256), (0.25, 0.2, 1.0), 0.0, 1.0, False, np.float32),     # the largest n2 of that path, steady
+    ((40, 33, 4), (1.0, 1.0, 0.1), 10.0, 0.01, True, np.float64),
 ]
 
 
@@ -67,10 +72,11 @@ def test_stokes_matches_oracle(S, case):
     solver.close()
 
 
-def test_stokes_in_place_and_repeated(S):
-    """u may alias u_old; repeated solves on one object give identical results."""
-    n, L = (20, 16, 12), (1.0, 0.8, 0.6)
-    shape = (3, 12, 16, 20)
+@pytest.mark.parametrize("n", [(20, 16, 12), (20, 16, 16)])
+def test_stokes_in_place_and_repeated(S, n):
+    """u may alias u_old; repeated solves on one object give identical results (both solve paths)."""
+    L = (1.0, 0.8, 0.6)
+    shape = (3,) + tuple(reversed(n))
     f = dev(ib_inputs.normal_array(5, shape, purpose="f"))
     u0 = dev(ib_inputs.normal_array(6, shape, purpose="u"))
     solver = S(3, n, L)

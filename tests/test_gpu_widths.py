@@ -130,3 +130,23 @@ def test_width_kernels_unsupported_calls(P):
         P(3, (16, 16, 16), (1.0, 1.0, 1.0), kernel="roma3", max_points=10, compensated=True)
     assert e.value.status == _abi.IB_ERR_INVALID_ARG
     plan.close()
+
+
+@pytest.mark.parametrize("kernel,bounded", [("roma3", (False, False, False)), ("bspline6", (False, False, False)),
+                                            ("bspline6", (True, False, True)), ("peskin4", (True, True, True))])
+def test_empty_point_sets(P, kernel, bounded):
+    """No points: spreading writes zeros (or leaves f as it was with accumulate), interpolation returns nothing."""
+    n = (16, 12, 8)
+    plan = P(3, n, (1.0, 1.0, 1.0), kernel=kernel, max_points=10, bounded=bounded)
+    X = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    G = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    u = dev(ib_inputs.normal_array(5, (3, 8, 12, 16)))
+    f = plan.spread(X, G)
+    assert torch.count_nonzero(f).item() == 0
+    f0 = dev(ib_inputs.normal_array(6, (3, 8, 12, 16)))
+    f2 = plan.spread(X, G, f=f0.clone(), accumulate=True)
+    assert torch.equal(f2, f0)
+    U = plan.interpolate(X, u)
+    plan.check()
+    assert tuple(U.shape) == (0, 3)
+    plan.close()

@@ -81,8 +81,37 @@ double or_phi(int kernel, double r) {
 }
 
 /* d phi / d r of the same formulas (both kernels are C^1 on the real line). */
+/* Derivatives of the 3-point and 6-point kernels, from the same pieces:
+ * 3-point: -r / sqrt(1 - 3 r^2) on |r| <= 1/2; sign(r) (-(1 + (1 - |r|) / q) / 2)
+ *   with q = sqrt(1 - 3 (1 - |r|)^2) on 1/2 <= |r| <= 3/2 (0 at |r| = 3/2);
+ * 6-point B-spline: sign(r) times (-120 a + 120 a^3 - 50 a^4) / 120 on [0, 1),
+ *   -(5 + 20c + 30c^2 + 20c^3 - 25c^4) / 120 with c = 2 - a on [1, 2), and
+ *   -(3 - a)^4 / 24 on [2, 3), a = |r|. */
+static double dphi_roma3(double r) {
+  double a = fabs(r), sgn = (r < 0.0) ? -1.0 : 1.0;
+  if (a >= 1.5) return 0.0;
+  if (a <= 0.5) return -r / sqrt(1.0 - 3.0 * r * r);
+  double q = sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a));
+  return sgn * (-(1.0 + (1.0 - a) / q) / 2.0);
+}
+
+static double dphi_bspline6(double r) {
+  double a = fabs(r), sgn = (r < 0.0) ? -1.0 : 1.0;
+  if (a >= 3.0) return 0.0;
+  if (a >= 2.0) {
+    double c = 3.0 - a;
+    return sgn * (-(c * c * c * c) / 24.0);
+  }
+  if (a >= 1.0) {
+    double c = 2.0 - a;
+    return sgn * (-(5.0 + 20.0 * c + 30.0 * c * c + 20.0 * c * c * c - 25.0 * c * c * c * c) / 120.0);
+  }
+  return sgn * (-120.0 * a + 120.0 * a * a * a - 50.0 * a * a * a * a) / 120.0;
+}
+
 double or_dphi(int kernel, double r) {
-  if (kernel >= 2) return NAN;   /* position gradients are defined for the 4-point kernels only */
+  if (kernel == 2) return dphi_roma3(r);
+  if (kernel == 3) return dphi_bspline6(r);
   double a = fabs(r);
   double sgn = (r < 0.0) ? -1.0 : 1.0;
   if (a >= 2.0) return 0.0;

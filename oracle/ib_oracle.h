@@ -59,7 +59,7 @@ typedef struct {
 } or_grid;
 
 /* 1-D kernel phi(r) and its derivative (Section 2; kernels of Peskin 2002 and
- * the 3- and 6-point kernels above; the derivative is NaN for those two). */
+ * the 3- and 6-point kernels above). */
 double or_phi(int kernel, double r);
 double or_dphi(int kernel, double r);
 

@@ -111,13 +111,17 @@ def test_other_width_kernels_match_independent_copies(orc):
     assert np.max(np.abs(orc.phi(3, r) - phi_bspline6(r))) < 1e-15
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_dphi_closed_forms_and_difference_quotients(orc, kernel):
+    """Values at 0, +-1 and the support edge; central differences of phi everywhere (every piece)."""
+    edge = {0: 2.0, 1: 2.0, 2: 1.5, 3: 3.0}[kernel]
+    # phi'(1): standard -1/2, cosine -pi/8, 3-point -(1 + 0 / q) / 2 = -1/2, B-spline -50/120
+    at1 = {0: -0.5, 1: -math.pi / 8, 2: -0.5, 3: -50.0 / 120.0}[kernel]
     assert orc.dphi(kernel, 0.0)[0] == pytest.approx(0.0, abs=1e-15)
-    assert orc.dphi(kernel, 2.0)[0] == 0.0
-    assert orc.dphi(kernel, 1.0)[0] == pytest.approx(-0.5 if kernel == 0 else -math.pi / 8, abs=1e-14)
-    assert orc.dphi(kernel, -1.0)[0] == pytest.approx(0.5 if kernel == 0 else math.pi / 8, abs=1e-14)
-    r = np.linspace(-2.3, 2.3, 461) + 1e-3
+    assert orc.dphi(kernel, edge)[0] == pytest.approx(0.0, abs=1e-15)
+    assert orc.dphi(kernel, 1.0)[0] == pytest.approx(at1, abs=1e-14)
+    assert orc.dphi(kernel, -1.0)[0] == pytest.approx(-at1, abs=1e-14)
+    r = np.linspace(-edge - 0.3, edge + 0.3, 461) + 1e-3
     eps = 1e-6
     fd = (orc.phi(kernel, r + eps) - orc.phi(kernel, r - eps)) / (2 * eps)
     assert np.max(np.abs(fd - orc.dphi(kernel, r))) < 1e-6
@@ -306,7 +310,7 @@ def test_single_point_on_a_node(orc):
 
 # -------------------------------------------------------------- gradients --
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_position_gradients_match_central_differences(orc, kernel):
     """16^3 MAC grid, 200 points, eps = 1e-6: analytic dLoss/dX against FP64 central differences."""
     g = orc.Grid(dim=3, n=(16, 16, 16), L=(1.0, 1.0, 1.0), mac=True, kernel=kernel)

@@ -116,8 +116,8 @@ def load_peaks():
 
 
 # Sources of the kernels whose DRAM counters profiles/traffic.txt records (the
-# spreading and interpolation kernels and the headers they are built from).
-TRAFFIC_SOURCES = ("ib_ops.cu", "ib_common.cuh", "ib_internal.h")
+# spreading and interpolation kernels and the device header they include).
+TRAFFIC_SOURCES = ("ib_ops.cu", "ib_common.cuh")
 
 
 def csrc_hash():

@@ -75,8 +75,8 @@ typedef enum {
  *                       cell of a point is centred on its nearest node (Fig. 1b)
  *   IB_KERNEL_BSPLINE6  6-point kernel: the centred quintic B-spline
  * The 3- and 6-point kernels are available to ib_bin, ib_spread (not
- * IB_COMPENSATED), ib_interpolate and ib_advect; ib_pos_grad and
- * ib_spread_paper return IB_ERR_NOT_IMPLEMENTED for them, and batches, the
+ * IB_COMPENSATED), ib_interpolate, ib_pos_grad and ib_advect;
+ * ib_spread_paper returns IB_ERR_NOT_IMPLEMENTED for them, and batches, the
  * no-alloc interpolation and IB_PLAN_COMPENSATED plans reject them
  * (IB_ERR_INVALID_ARG). */
 enum { IB_KERNEL_PESKIN4 = 0, IB_KERNEL_COSINE4 = 1, IB_KERNEL_ROMA3 = 2, IB_KERNEL_BSPLINE6 = 3 };

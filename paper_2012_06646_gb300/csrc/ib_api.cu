@@ -430,7 +430,6 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
   if (npts > 0 && (!field || !v || !D)) return IB_ERR_INVALID_ARG;
   if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
   if (!isfinite(scale)) return IB_ERR_INVALID_ARG;
-  if (kernel_width(p->desc.kernel) != 4) return IB_ERR_NOT_IMPLEMENTED;
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare(p, npts, X, flags, s);
   if (st != IB_OK) return st;
@@ -445,8 +444,10 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
       return IB_ERR_CUDA;
     field = p->gridx;
   }
-  if (launch_pos_grad(J, p->sh, call_bins(p, npts), p->desc.dtype, field, v, scale, D, s) != cudaSuccess)
-    return IB_ERR_CUDA;
+  const cudaError_t e = kernel_width(p->desc.kernel) != 4
+                            ? launch_pos_grad_width(J, p->sh, call_bins(p, npts), p->desc.dtype, field, v, scale, D, s)
+                            : launch_pos_grad(J, p->sh, call_bins(p, npts), p->desc.dtype, field, v, scale, D, s);
+  if (e != cudaSuccess) return IB_ERR_CUDA;
   return IB_OK;
 }
 

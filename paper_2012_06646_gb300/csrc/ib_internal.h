@@ -27,6 +27,8 @@ cudaError_t launch_spread_width(const Jobs& J, const Shape& sh, const Bins& B, v
                                 int dtype, bool accumulate, cudaStream_t s);
 cudaError_t launch_interp_width(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, int dtype,
                                 double scale, cudaStream_t s);
+cudaError_t launch_pos_grad_width(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,
+                                  const void* v, double scale, void* D, cudaStream_t s);
 
 // Bounded (non-periodic) dimensions (ib_bounds.cu): f [ncomp][domain nodes] =
 // (f +) the domain's nodes of fx [ncomp][extended nodes]; ux = u on the domain's

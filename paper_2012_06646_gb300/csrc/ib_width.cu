@@ -99,6 +99,40 @@ __device__ __forceinline__ void wweights(T r, T c, T w[S]) {
   }
 }
 
+// Weights and their derivatives with respect to the fraction r (dw[k] =
+// d w[k] / dr; c = 1 - r), from the same pieces as wweights:
+//   3-point: with e = (c - r) / (2q), dw = (-(1 + e) / 2, e, (1 - e) / 2);
+//   6-point: -c^4/24, -m'(c), p'(r), -p'(c), m'(r), r^4/24 with
+//     p'(x) = x (-120 + x^2 (120 - 50 x)) / 120,
+//     m'(x) = (5 + x (20 + x (30 + x (20 - 25 x)))) / 120.
+template <typename T>
+__device__ __forceinline__ T bspline_pd(T x) {
+  return x * ((T)-120 + x * x * ((T)120 - (T)50 * x)) * (T)(1.0 / 120.0);
+}
+template <typename T>
+__device__ __forceinline__ T bspline_md(T x) {
+  return ((T)5 + x * ((T)20 + x * ((T)30 + x * ((T)20 - (T)25 * x)))) * (T)(1.0 / 120.0);
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void wweights_d(T r, T c, T w[S], T dw[S]) {
+  wweights<T, S>(r, c, w);
+  if constexpr (S == 3) {
+    const T q = sqrt(fma((T)3 * r, c, (T)0.25));
+    const T e = (c - r) / ((T)2 * q);
+    dw[0] = -((T)1 + e) * (T)0.5;
+    dw[1] = e;
+    dw[2] = ((T)1 - e) * (T)0.5;
+  } else {
+    dw[0] = -c * c * c * c * (T)(1.0 / 24.0);
+    dw[1] = -bspline_md(c);
+    dw[2] = bspline_pd(r);
+    dw[3] = -bspline_pd(c);
+    dw[4] = bspline_md(r);
+    dw[5] = r * r * r * r * (T)(1.0 / 24.0);
+  }
+}
+
 // Cell of a point in one dimension, relative to the tile: the physical xi = 0
 // cell minus the tile origin, and the exact offsets of both staggerings.
 // Returns false when that cell is not in the tile (X changed after binning).
@@ -680,6 +714,92 @@ __global__ void __launch_bounds__(kWInterpThreads, sizeof(T) == 4 ? 6 : 4) k_int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Position gradient for width s: thread per point (cell order), the field
+// gathered from global memory over the s^d support of each component:
+// D_b = scale (N_b / L_b) sum_a v_a sum_nodes field_a[node] dW / dr_b.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int S>
+__global__ void __launch_bounds__(kThreads) k_pos_grad_w(const __grid_constant__ Jobs J, const Shape sh,
+                                                         const Bins B, const T* __restrict__ field,
+                                                         const T* __restrict__ v, T scale, T* __restrict__ Dout) {
+  using W = WGeo<D, S, 8>;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= B.npts_total) return;
+  const Job& jb = J.one;
+  const long long li = (long long)B.perm[p];
+  const int nc = sh.ncomp;
+  const T* Xp = (const T*)jb.X + li * D;
+  T* Dp = Dout + li * D;
+  Cell1<T> cl[D];
+  uint32_t err = 0;
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    err |= point_cell<T>(Xp[b], jb, b, cl[b]);
+    if (!in_bounds(jb, b, cl[b])) err |= ERR_RANGE;
+  }
+  if (err) {
+#pragma unroll
+    for (int b = 0; b < D; ++b) Dp[b] = (T)NAN;
+    return;
+  }
+  const long long stride[3] = {1, (long long)jb.n[0], (long long)jb.n[0] * jb.n[1]};
+  T out[3] = {0, 0, 0};
+  for (int a = 0; a < nc; ++a) {
+    long long off[3][S];
+    T w[3][S], dw[3][S];
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const bool h = half_stag(sh, a, b);
+      int i;
+      T r, c;
+      if (W::odd == h) {
+        i = cl[b].i0;
+        r = cl[b].r0;
+        c = cl[b].c0;
+      } else if (!W::odd) {
+        i = cl[b].i1;
+        r = cl[b].r1;
+        c = cl[b].c1;
+      } else {
+        i = cl[b].i1 + 1;
+        r = cl[b].r1;
+        c = cl[b].c1;
+      }
+      wweights_d<T, S>(r, c, w[b], dw[b]);
+#pragma unroll
+      for (int k = 0; k < S; ++k) off[b][k] = (long long)modn(i + W::tlo + k, jb.n[b]) * stride[b];
+    }
+    const T* fa = field + a * jb.ncell;
+    T g[3] = {0, 0, 0};
+#pragma unroll
+    for (int tz = 0; tz < ((D == 3) ? S : 1); ++tz) {
+      const T wz = (D == 3) ? w[D - 1][tz] : (T)1;
+      const T dzv = (D == 3) ? dw[D - 1][tz] : (T)0;
+      const long long oz = (D == 3) ? off[D - 1][tz] : 0;
+#pragma unroll
+      for (int ty = 0; ty < S; ++ty) {
+        const T* row = fa + oz + off[1][ty];
+        T rx = 0, rdx = 0;
+#pragma unroll
+        for (int tx = 0; tx < S; ++tx) {
+          const T val = __ldg(row + off[0][tx]);
+          rx += w[0][tx] * val;
+          rdx += dw[0][tx] * val;
+        }
+        g[0] += w[1][ty] * wz * rdx;
+        g[1] += dw[1][ty] * wz * rx;
+        if (D == 3) g[2] += w[1][ty] * dzv * rx;
+      }
+    }
+    const T va = v[li * nc + a];
+#pragma unroll
+    for (int b = 0; b < D; ++b) out[b] += va * g[b];
+  }
+#pragma unroll
+  for (int b = 0; b < D; ++b) Dp[b] = scale * (T)jb.scale[b] * out[b];
+}
+
 template <typename K>
 void allow_smem_w(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -746,6 +866,30 @@ cudaError_t launch_spread_width(const Jobs& J, const Shape& sh, const Bins& B, v
                                 : spread_w_dim<float, 6>(J, sh, B, boxes, ntiles, accumulate, s);
   return S == 3 ? spread_w_dim<double, 3>(J, sh, B, boxes, ntiles, accumulate, s)
                 : spread_w_dim<double, 6>(J, sh, B, boxes, ntiles, accumulate, s);
+}
+
+cudaError_t launch_pos_grad_width(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,
+                                  const void* v, double scale, void* D, cudaStream_t s) {
+  const long long n = B.npts_total;
+  if (n == 0) return cudaSuccess;
+  const int S = kernel_width(sh.kernel);
+  const unsigned g = grid_for(n, kThreads);
+  if (dtype == 0) {
+    const float *fl = (const float*)field, *vv = (const float*)v;
+    float* Dd = (float*)D;
+    if (sh.dim == 3 && S == 3) k_pos_grad_w<float, 3, 3><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, (float)scale, Dd);
+    else if (sh.dim == 3) k_pos_grad_w<float, 3, 6><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, (float)scale, Dd);
+    else if (S == 3) k_pos_grad_w<float, 2, 3><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, (float)scale, Dd);
+    else k_pos_grad_w<float, 2, 6><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, (float)scale, Dd);
+  } else {
+    const double *fl = (const double*)field, *vv = (const double*)v;
+    double* Dd = (double*)D;
+    if (sh.dim == 3 && S == 3) k_pos_grad_w<double, 3, 3><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, scale, Dd);
+    else if (sh.dim == 3) k_pos_grad_w<double, 3, 6><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, scale, Dd);
+    else if (S == 3) k_pos_grad_w<double, 2, 3><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, scale, Dd);
+    else k_pos_grad_w<double, 2, 6><<<g, kThreads, 0, s>>>(J, sh, B, fl, vv, scale, Dd);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_interp_width(const Jobs& J, const Shape& sh, const Bins& B, long long nitiles, int dtype,

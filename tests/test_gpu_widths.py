@@ -121,9 +121,6 @@ def test_width_kernels_unsupported_calls(P):
     u = dev(ib_inputs.normal_array(2, (3, 16, 16, 16)))
     v = dev(ib_inputs.normal_array(3, (10, 3)))
     with pytest.raises(IBError) as e:
-        plan.pos_grad(X, u, v)
-    assert e.value.status == _abi.IB_ERR_NOT_IMPLEMENTED
-    with pytest.raises(IBError) as e:
         plan.spread_paper(X, v, algorithm=4)
     assert e.value.status == _abi.IB_ERR_NOT_IMPLEMENTED
     with pytest.raises(IBError) as e:
@@ -149,4 +146,54 @@ def test_empty_point_sets(P, kernel, bounded):
     U = plan.interpolate(X, u)
     plan.check()
     assert tuple(U.shape) == (0, 3)
+    plan.close()
+
+
+GRAD_CASES = [
+    # dim, n, L, mac, kernel, dtype, bounded
+    (3, (20, 16, 24), (1.0, 0.8, 1.2), True, 2, np.float32, (False, False, False)),
+    (3, (20, 16, 24), (1.0, 0.8, 1.2), True, 3, np.float32, (False, False, False)),
+    (3, (12, 10, 9), (1.0, 1.0, 1.0), False, 3, np.float64, (False, False, False)),
+    (3, (12, 10, 9), (1.0, 1.0, 1.0), True, 2, np.float64, (True, False, True)),
+    (2, (40, 24), (1.0, 0.6), True, 3, np.float32, (False, True)),
+]
+
+
+@pytest.mark.parametrize("case", GRAD_CASES, ids=[f"{c[0]}d-{NAMES[c[4]]}-{'mac' if c[3] else 'cc'}-"
+                                                   f"{np.dtype(c[5]).name}-b{sum(c[6])}" for c in GRAD_CASES])
+def test_width_pos_grad_matches_oracle(P, orc, case):
+    dim, n, L, mac, kernel, dtype, bounded = case
+    npts = 600
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    plan = P(dim, n, L, grid="mac" if mac else "cc", kernel=NAMES[kernel], dtype=tdt, max_points=npts,
+             bounded=bounded)
+    g = orc.Grid(dim=dim, n=n, L=L, mac=mac, kernel=kernel, bounded=bounded)
+    X = ib_inputs.uniform_points(91 + kernel, npts, L, dim, dtype=dtype)
+    field = ib_inputs.normal_array(92, plan.grid_shape(), dtype=dtype)
+    v = ib_inputs.normal_array(93, (npts, dim), dtype=dtype)
+    D = host(plan.pos_grad(dev(X), dev(field), dev(v), scale=2.5))
+    plan.check()
+    D_ref, Dabs = orc.pos_grad(g, X, field, v)
+    rel, floor = (2e-5, FLOOR32) if dtype == np.float32 else (1e-12, FLOOR64)
+    assert_interp_close(D, 2.5 * D_ref, 2.5 * Dabs, rel=rel, floor=floor, what="pos_grad")
+    plan.close()
+
+
+def test_width_autograd_bspline(P, orc):
+    """loss = sum(w * spread(G, X)) with the 6-point kernel: dL/dG and dL/dX against the oracle."""
+    from paper_2012_06646_gb300 import autograd as ag
+    n, npts = (16, 16, 16), 400
+    plan = P(3, n, (1.0, 1.0, 1.0), kernel="bspline6", max_points=npts)
+    X = ib_inputs.uniform_points(95, npts, (1.0, 1.0, 1.0), 3)
+    G = ib_inputs.normal_array(96, (npts, 3))
+    w = ib_inputs.normal_array(97, plan.grid_shape())
+    Xd = dev(X).requires_grad_(True)
+    Gd = dev(G).requires_grad_(True)
+    gX, gG = torch.autograd.grad((dev(w) * ag.spread(Xd, Gd, plan)).sum(), (Xd, Gd))
+    g = orc.Grid(dim=3, n=n, L=(1.0, 1.0, 1.0), kernel=3)
+    hmd = orc.inv_cell_volume(g)
+    Uw, Uwabs = orc.interp(g, X, w)
+    assert_interp_close(host(gG), hmd * Uw, hmd * Uwabs, what="dL/dG")
+    D, Dabs = orc.pos_grad(g, X, w, G)
+    assert_interp_close(host(gX), hmd * D, hmd * Dabs, rel=2e-5, what="dL/dX")
     plan.close()

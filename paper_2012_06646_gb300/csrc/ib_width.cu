@@ -51,6 +51,23 @@ struct WGeo {
 
 inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Rounds of k_spread_w's read-modify-writes: lane L takes the support nodes
+// whose box offset is L mod 32, so the lanes of a round hit distinct banks
+// whatever the box corner; the rounds needed are the largest number of
+// support nodes sharing one residue.
+template <int D, int S, int BS>
+__host__ __device__ constexpr int residue_rounds() {
+  int cnt[32] = {};
+  int m = 0;
+  for (int q = 0; q < ((D == 3) ? S * S * S : S * S); ++q) {
+    const int tx = q % S, ty = (q / S) % S, tz = q / (S * S);
+    const int o = tx + BS * (ty + BS * tz);
+    ++cnt[o & 31];
+    if (cnt[o & 31] > m) m = cnt[o & 31];
+  }
+  return m;
+}
+
 template <int D, int TS>
 __device__ __forceinline__ void wtile_coords(const int* ntile, const int* n, long long lt, int T0[3], int TE[3]) {
   const int l = (int)lt;
@@ -185,19 +202,22 @@ __device__ __forceinline__ bool wpoint_dim(const Job& jb, const Shape& sh, T x, 
 // Spreading into tile boxes: one warp per (tile, component), the two stages
 // of the 4-point path.  Stage 1 (lanes = points): a point's record holds the
 // s^2 products wx[tx] wy[ty] h^-d G and the s weights wz, plus its box offset.
-// Stage 2 (warp = point): lane l owns support nodes l, l + 32, ... of the s^d
-// (distinct nodes, so plain read-modify-writes are race-free); the lane's
-// loads come before its stores, and __syncwarp orders consecutive points.
+// Stage 2 (warp = point): lane l owns the support nodes whose box offset is
+// l mod 32 (distinct nodes, so plain read-modify-writes are race-free, and the
+// lanes of each round hit distinct banks); the lane's loads come before its
+// stores, and __syncwarp orders consecutive points.
 // ---------------------------------------------------------------------------
 template <typename T, int D, int S, int TS>
 __global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant__ Jobs J, const Shape sh,
                                                             const Bins B, T* __restrict__ boxes, long long nunits) {
   using W = WGeo<D, S, TS>;
   static_assert(W::NROWS % 32 == 0, "rows: a multiple of 32");
+  constexpr int R = residue_rounds<D, S, W::BS>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t rstart_s[kWWarps][W::NROWS];
   __shared__ uint32_t rpre_s[kWWarps][W::NROWS];
   __shared__ int roff_s[kWWarps][kWBatch];
+  __shared__ uint32_t ltab_s[kWWarps][R][32];      // per round and lane: box offset | xy product << 16 | z << 24
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long unit = (long long)blockIdx.x * kWWarps + warp;
   if (unit >= nunits) return;                      // the whole warp leaves; no block barrier follows
@@ -253,16 +273,30 @@ __global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant
     gs = Gp[li * nc + a];
   };
 
-  int loff[W::PER], lxy[W::PER], lz[W::PER];
-  bool lon[W::PER];
+  // This lane's support nodes: those whose box offset is lane mod 32.
+  {
+    uint32_t(*ltab)[32] = ltab_s[warp];
+    int cnt = 0;
+    for (int q = 0; q < W::NODES; ++q) {
+      const int tx = q % S, ty = (q / S) % S, tz = (D == 3) ? q / (S * S) : 0;
+      const int o = tx + W::BS * (ty + W::BS * tz);
+      if ((o & 31) == lane) {
+        ltab[cnt][lane] = (uint32_t)o | ((uint32_t)(tx + S * ty) << 16) | ((uint32_t)(S * S + tz) << 24);
+        ++cnt;
+      }
+    }
+    for (int k = cnt; k < R; ++k) ltab[k][lane] = 0xFFFFFFFFu;
+    __syncwarp();
+  }
+  int loff[R], lxy[R], lz[R];
+  bool lon[R];
 #pragma unroll
-  for (int k = 0; k < W::PER; ++k) {
-    const int q = lane + 32 * k;
-    lon[k] = q < W::NODES;
-    const int tx = q % S, ty = (q / S) % S, tz = (D == 3) ? q / (S * S) : 0;
-    loff[k] = tx + W::BS * (ty + W::BS * tz);
-    lxy[k] = tx + S * ty;
-    lz[k] = S * S + tz;
+  for (int k = 0; k < R; ++k) {
+    const uint32_t e = ltab_s[warp][k][lane];
+    lon[k] = e != 0xFFFFFFFFu;
+    loff[k] = (int)(e & 0xFFFFu);
+    lxy[k] = (int)((e >> 16) & 0xFFu);
+    lz[k] = (int)(e >> 24);
   }
 
   T xs[D], gs = (T)0;
@@ -303,16 +337,16 @@ __global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant
     for (int i = 0; i < cnt; ++i) {
       const T* rp = rec_s + i * W::REC;
       const int off = roff[i];
-      T v[W::PER], add[W::PER];
+      T v[R], add[R];
 #pragma unroll
-      for (int k = 0; k < W::PER; ++k) {
+      for (int k = 0; k < R; ++k) {
         if (lon[k]) {
           add[k] = (D == 3) ? rp[lxy[k]] * rp[lz[k]] : rp[lxy[k]];
           v[k] = box[off + loff[k]];
         }
       }
 #pragma unroll
-      for (int k = 0; k < W::PER; ++k)
+      for (int k = 0; k < R; ++k)
         if (lon[k]) box[off + loff[k]] = v[k] + add[k];
       __syncwarp();
     }

@@ -9,7 +9,9 @@
  *   interpolation  U_{j,a} = sum_k delta_h(x_k - X_j) u_a[k] h^d       (Eq. disc-interp, Eq. matrix-interp)
  *
  * with delta_h(x) = prod_b h_b^-1 phi(x_b / h_b) (Section 2) on a periodic
- * box, G = F dtheta premultiplied by the caller.  The operator statements
+ * box (or one with non-periodic dimensions, IB_PLAN_BOUNDED_*), G = F dtheta
+ * premultiplied by the caller.  It also solves the Eulerian step of the
+ * timestep on the periodic MAC grid (ib_stokes_*).  The operator statements
  * par-spread(Gamma_h, Omega_h, L) and par-interpolate(Gamma_h, Omega_h, e)
  * of Algorithms 3 and 4 map onto ib_spread and ib_interpolate: a point set,
  * a grid description (the plan) and one field per component.
@@ -21,10 +23,14 @@
  *   - Cell of a point: i_b = floor(X_b * (N_b/L_b) - xi_b), evaluated so that
  *     the integer agrees exactly with the FP64 evaluation of that formula;
  *     support nodes i + t, t in {-1, 0, 1, 2}, weight prod_b phi(t_b - r_b)
- *     with r = X (N/L) - xi - i (Eq. delta-defs, Fig. 1a).
- *   - Node indices wrap modulo N_b (triply periodic box, Section 4).
- *   - Points may lie outside [0, L); they are wrapped.  A position with
- *     |X_b N_b / L_b| >= 2^30, or a non-finite one, is reported through
+ *     with r = X (N/L) - xi - i (Eq. delta-defs, Fig. 1a), for the 4-point
+ *     kernels; kernels of other support widths s take the s nodes around the
+ *     cell of Section 3.1 (see the kernel list below).
+ *   - Node indices wrap modulo N_b (triply periodic box, Section 4), except
+ *     along a bounded dimension (see IB_PLAN_BOUNDED_X).
+ *   - Points may lie outside [0, L) along periodic dimensions; they are
+ *     wrapped.  A position with |X_b N_b / L_b| >= 2^30, one outside [0, L_b]
+ *     along a bounded dimension, or a non-finite one is reported through
  *     ib_plan_check (IB_ERR_RANGE / IB_ERR_NONFINITE); such a point spreads
  *     nothing and interpolates to NaN.
  *   - Layouts: X is row-major (npts, dim); G and U are row-major
@@ -61,7 +67,8 @@ typedef enum {
   IB_ERR_CAPACITY = 5,        /* npts (or a batch wave) exceeds the capacity given at creation */
   IB_ERR_NOT_IMPLEMENTED = 6,
   IB_ERR_NONFINITE = 7,       /* a position was NaN or infinite (reported by ib_plan_check) */
-  IB_ERR_RANGE = 8,           /* a position was 2^30 or more cells away from the box */
+  IB_ERR_RANGE = 8,           /* a position was 2^30 or more cells away from the box, or outside
+                                 [0, L] along a bounded dimension */
   IB_ERR_NO_BINS = 9,         /* IB_REUSE_BINS without a matching ib_bin call */
   IB_ERR_BINS_STALE = 10      /* positions changed after binning (or X aliased an output):
                                  the points concerned spread nothing and interpolate to NaN */

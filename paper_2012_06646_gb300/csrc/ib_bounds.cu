@@ -14,67 +14,67 @@
 namespace ibgb {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 
-inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+constexpr unsigned kMaxGridYZ = 65535;
 
-// One thread per domain node (all components): f = fx (or f + fx).
+// Blocks over x-rows of the domain (y in grid y, (component a, z) in grid z,
+// both strided), threads along x: f = fx (or f + fx).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bounds_crop(const __grid_constant__ Job jb, int ncomp,
                                                           const T* __restrict__ fx, T* __restrict__ f,
                                                           int accumulate) {
-  const long long nd = (long long)jb.nin[0] * jb.nin[1] * jb.nin[2];
-  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (i >= nd * ncomp) return;
-  const int a = (int)(i / nd);
-  const long long r = i - a * nd;
-  const int x = (int)(r % jb.nin[0]);
-  const long long q = r / jb.nin[0];
-  const int y = (int)(q % jb.nin[1]);
-  const int z = (int)(q / jb.nin[1]);
-  const T v = fx[a * jb.ncell + x + (long long)jb.n[0] * (y + (long long)jb.n[1] * z)];
-  f[i] = accumulate ? f[i] + v : v;
+  const int x = blockIdx.x * kThreads + threadIdx.x;
+  if (x >= jb.nin[0]) return;
+  for (int az = blockIdx.z; az < jb.nin[2] * ncomp; az += gridDim.z) {
+    const int a = az / jb.nin[2], z = az - a * jb.nin[2];
+    for (int y = blockIdx.y; y < jb.nin[1]; y += gridDim.y) {
+      const long long o = (((long long)a * jb.nin[2] + z) * jb.nin[1] + y) * jb.nin[0] + x;
+      const T v = fx[a * jb.ncell + ((long long)z * jb.n[1] + y) * jb.n[0] + x];
+      f[o] = accumulate ? f[o] + v : v;
+    }
+  }
 }
 
-// One thread per extended node (all components): ux = u inside the domain, 0 on ghosts.
+// Blocks over x-rows of the extended grid (as k_bounds_crop): ux = u inside the
+// domain, 0 on the ghost nodes.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bounds_pad(const __grid_constant__ Job jb, int ncomp,
                                                          const T* __restrict__ u, T* __restrict__ ux) {
-  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (i >= jb.ncell * ncomp) return;
-  const int a = (int)(i / jb.ncell);
-  const long long r = i - a * jb.ncell;
-  const int x = (int)(r % jb.n[0]);
-  const long long q = r / jb.n[0];
-  const int y = (int)(q % jb.n[1]);
-  const int z = (int)(q / jb.n[1]);
-  const bool in = x < jb.nin[0] && y < jb.nin[1] && z < jb.nin[2];
-  const long long nd = (long long)jb.nin[0] * jb.nin[1] * jb.nin[2];
-  ux[i] = in ? u[a * nd + x + (long long)jb.nin[0] * (y + (long long)jb.nin[1] * z)] : (T)0;
+  const int x = blockIdx.x * kThreads + threadIdx.x;
+  if (x >= jb.n[0]) return;
+  for (int az = blockIdx.z; az < jb.n[2] * ncomp; az += gridDim.z) {
+    const int a = az / jb.n[2], z = az - a * jb.n[2];
+    for (int y = blockIdx.y; y < jb.n[1]; y += gridDim.y) {
+      const bool in = x < jb.nin[0] && y < jb.nin[1] && z < jb.nin[2];
+      T v = (T)0;
+      if (in) v = u[(((long long)a * jb.nin[2] + z) * jb.nin[1] + y) * jb.nin[0] + x];
+      ux[a * jb.ncell + ((long long)z * jb.n[1] + y) * jb.n[0] + x] = v;
+    }
+  }
+}
+
+dim3 rows_grid(int nx, int ny, long long nzc) {
+  return dim3((unsigned)((nx + kThreads - 1) / kThreads), (unsigned)(ny < (int)kMaxGridYZ ? ny : (int)kMaxGridYZ),
+              (unsigned)(nzc < (long long)kMaxGridYZ ? nzc : (long long)kMaxGridYZ));
 }
 
 }  // namespace
 
 cudaError_t launch_bounds_crop(const Job& jb, int ncomp, int dtype, const void* fx, void* f, bool accumulate,
                                cudaStream_t s) {
-  const long long n = (long long)jb.nin[0] * jb.nin[1] * jb.nin[2] * ncomp;
-  if (n == 0) return cudaSuccess;
+  const dim3 grid = rows_grid(jb.nin[0], jb.nin[1], (long long)jb.nin[2] * ncomp);
   if (dtype == 0)
-    k_bounds_crop<float><<<grid_for(n, kThreads), kThreads, 0, s>>>(jb, ncomp, (const float*)fx, (float*)f,
-                                                                     accumulate ? 1 : 0);
+    k_bounds_crop<float><<<grid, kThreads, 0, s>>>(jb, ncomp, (const float*)fx, (float*)f, accumulate ? 1 : 0);
   else
-    k_bounds_crop<double><<<grid_for(n, kThreads), kThreads, 0, s>>>(jb, ncomp, (const double*)fx, (double*)f,
-                                                                      accumulate ? 1 : 0);
+    k_bounds_crop<double><<<grid, kThreads, 0, s>>>(jb, ncomp, (const double*)fx, (double*)f, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bounds_pad(const Job& jb, int ncomp, int dtype, const void* u, void* ux, cudaStream_t s) {
-  const long long n = jb.ncell * ncomp;
-  if (n == 0) return cudaSuccess;
-  if (dtype == 0)
-    k_bounds_pad<float><<<grid_for(n, kThreads), kThreads, 0, s>>>(jb, ncomp, (const float*)u, (float*)ux);
-  else
-    k_bounds_pad<double><<<grid_for(n, kThreads), kThreads, 0, s>>>(jb, ncomp, (const double*)u, (double*)ux);
+  const dim3 grid = rows_grid(jb.n[0], jb.n[1], (long long)jb.n[2] * ncomp);
+  if (dtype == 0) k_bounds_pad<float><<<grid, kThreads, 0, s>>>(jb, ncomp, (const float*)u, (float*)ux);
+  else k_bounds_pad<double><<<grid, kThreads, 0, s>>>(jb, ncomp, (const double*)u, (double*)ux);
   return cudaGetLastError();
 }
 

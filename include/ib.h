@@ -63,7 +63,7 @@ typedef enum {
   IB_ERR_INVALID_ARG = 1,     /* bad descriptor, null pointer, unsupported combination */
   IB_ERR_OOM = 2,             /* device or pinned host allocation failed */
   IB_ERR_CUDA = 3,            /* a CUDA runtime call failed (launch or copy) */
-  IB_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up */
+  IB_ERR_TIMEOUT = 4,         /* reserved for a bounded device-side wait; no entry point waits on the device */
   IB_ERR_CAPACITY = 5,        /* npts (or a batch wave) exceeds the capacity given at creation */
   IB_ERR_NOT_IMPLEMENTED = 6,
   IB_ERR_NONFINITE = 7,       /* a position was NaN or infinite (reported by ib_plan_check) */
@@ -136,9 +136,32 @@ typedef struct {
  * no CUDA call.  Returns IB_ERR_INVALID_ARG for an invalid descriptor. */
 ib_status ib_plan_footprint(const ib_plan_desc* desc, size_t* bytes);
 
-/* Validate `desc`, allocate the plan's device scratch (one cudaMalloc arena)
- * on the current device, and return the plan in *out.  Errors:
- * IB_ERR_INVALID_ARG (descriptor), IB_ERR_OOM (allocation). */
+/* Device memory of the scratch arenas of plans and batches.  By default each
+ * ib_plan_create / ib_batch_create takes its arena from cudaMalloc and the
+ * matching destroy returns it with cudaFree.  ib_set_allocator installs a
+ * caller pair instead (a framework's caching allocator, or an allocator that
+ * fails on purpose to exercise out-of-memory handling):
+ *   - alloc(bytes, ctx): device memory of at least `bytes` bytes on the
+ *     current device, 256-byte aligned, or NULL when none is available;
+ *   - free_fn(ptr, ctx): releases a pointer alloc returned.
+ * Every object records the pair in force when it is created and frees its
+ * arena through that pair (after synchronising the device), so the pair may
+ * change while objects exist; the caller keeps the functions and ctx valid
+ * until those objects are destroyed.  alloc = free_fn = NULL restores
+ * cudaMalloc / cudaFree; exactly one NULL is IB_ERR_INVALID_ARG.  A create
+ * call whose alloc returns NULL returns IB_ERR_OOM with nothing held; an
+ * arena that is not 256-byte aligned is handed back to free_fn and the create
+ * call returns IB_ERR_INVALID_ARG.  The Stokes solver's buffers, cuFFT's
+ * work area and a batch's pinned host staging do not go through the pair.
+ * Host-only; may be called from any thread.  Paper counterpart: none. */
+typedef void* (*ib_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*ib_free_fn)(void* ptr, void* ctx);
+ib_status ib_set_allocator(ib_alloc_fn alloc, ib_free_fn free_fn, void* ctx);
+
+/* Validate `desc`, allocate the plan's device scratch (one arena, from
+ * cudaMalloc or the ib_set_allocator pair) on the current device, and return
+ * the plan in *out.  Errors: IB_ERR_INVALID_ARG (descriptor, or a misaligned
+ * arena from the allocator pair), IB_ERR_OOM (allocation). */
 ib_status ib_plan_create(const ib_plan_desc* desc, ib_plan* out);
 
 /* Synchronise the device, free the plan's scratch and the plan.  NULL is a no-op. */
@@ -181,9 +204,10 @@ ib_status ib_pos_grad(ib_plan plan, long long npts, const void* X, const void* f
 ib_status ib_advect(ib_plan plan, long long npts, const void* X, const void* U, double dt, void* Xout,
                     void* stream);
 
-/* Synchronise `stream`, then read and clear the plan's device error word:
- * IB_OK, IB_ERR_NONFINITE, IB_ERR_RANGE or IB_ERR_BINS_STALE (or IB_ERR_CUDA
- * if the stream reports an error). */
+/* Read and clear the plan's device error word with copies ordered on
+ * `stream`, waiting for that stream only (work on other streams keeps
+ * running): IB_OK, IB_ERR_NONFINITE, IB_ERR_RANGE or IB_ERR_BINS_STALE (or
+ * IB_ERR_CUDA if the stream reports an error). */
 ib_status ib_plan_check(ib_plan plan, void* stream);
 
 /* The paper's own parallel spreading algorithms, kept as comparators of

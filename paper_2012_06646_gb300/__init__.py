@@ -18,7 +18,7 @@ def load():
 
 
 def __getattr__(name):
-    if name in ("Plan", "Batch", "Stokes"):
+    if name in ("Plan", "Batch", "Stokes", "set_allocator", "use_torch_allocator"):
         from . import plan
         return getattr(plan, name)
     raise AttributeError(name)

@@ -81,6 +81,10 @@ _vp = ctypes.c_void_p
 _ll = ctypes.c_longlong
 _st = ctypes.c_int
 
+# ib_alloc_fn / ib_free_fn of ib_set_allocator (called with no argument: NULL)
+ib_alloc_fn = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp)
+ib_free_fn = ctypes.CFUNCTYPE(None, _vp, _vp)
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "ib_plan_footprint": (_st, [ctypes.POINTER(ib_plan_desc), ctypes.POINTER(ctypes.c_size_t)]),
@@ -106,6 +110,7 @@ SIGNATURES = {
     "ib_stokes_create": (_st, [ctypes.POINTER(ib_plan_desc), ctypes.POINTER(_vp)]),
     "ib_stokes_solve": (_st, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "ib_stokes_destroy": (_st, [_vp]),
+    "ib_set_allocator": (_st, [ib_alloc_fn, ib_free_fn, _vp]),
     "ib_status_string": (ctypes.c_char_p, [_st]),
     "ib_version": (ctypes.c_char_p, []),
 }

@@ -21,6 +21,47 @@ constexpr long long kMaxPointsTotal = (1ll << 31) - 16;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// Arena allocator: cudaMalloc / cudaFree unless ib_set_allocator installed a
+// caller pair.  Each plan and batch records the pair it was created with and
+// frees its arena through it.
+struct Allocator {
+  ib_alloc_fn alloc;
+  ib_free_fn free;
+  void* ctx;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc = {nullptr, nullptr, nullptr};
+
+ib_status arena_alloc(Allocator* own, void** p, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    *own = g_alloc;
+  }
+  *p = nullptr;
+  if (!own->alloc) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return IB_ERR_OOM;
+    }
+    return IB_OK;
+  }
+  void* q = own->alloc(bytes, own->ctx);
+  if (!q) return IB_ERR_OOM;
+  if ((uintptr_t)q % kAlign != 0) {   // the carve-up assumes 256-byte sections
+    own->free(q, own->ctx);
+    return IB_ERR_INVALID_ARG;
+  }
+  *p = q;
+  return IB_OK;
+}
+
+void arena_free(const Allocator& own, void* p) {
+  if (!p) return;
+  if (own.alloc) own.free(p, own.ctx);
+  else cudaFree(p);
+}
+
 // scale = S 2^E with 0 < S < 2^24 when possible (X * scale is then exact in
 // FP64 for every FP32 X); S = 0 otherwise.
 void short_scale(double s, int* S, int* E) {
@@ -152,10 +193,15 @@ Bins carve(char* base, const Layout& L) {
 }
 
 ib_status check_error_word(uint32_t* err_dev, cudaStream_t s) {
-  if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
+  // Read (and clear) on the caller's stream, so the check waits for that
+  // stream's work only, not for other streams as the legacy stream would.
   uint32_t e = 0;
-  if (cudaMemcpy(&e, err_dev, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return IB_ERR_CUDA;
-  if (e != 0 && cudaMemset(err_dev, 0, sizeof(uint32_t)) != cudaSuccess) return IB_ERR_CUDA;
+  if (cudaMemcpyAsync(&e, err_dev, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IB_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
+  if (e != 0) {
+    if (cudaMemsetAsync(err_dev, 0, sizeof(uint32_t), s) != cudaSuccess) return IB_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
+  }
   if (e & ERR_NONFINITE) return IB_ERR_NONFINITE;
   if (e & ERR_RANGE) return IB_ERR_RANGE;
   if (e & ERR_STALE) return IB_ERR_BINS_STALE;
@@ -173,6 +219,7 @@ struct ib_plan_s {
   int tile_plain, tile_comp;
   long long ntiles_plain, ntiles_comp;
   Layout layout;
+  Allocator alloc;     // the allocator the arena came from
   void* arena;
   Bins bins;
   void* boxes;
@@ -187,6 +234,7 @@ struct ib_batch_s {
   Shape sh;
   int tile;
   Layout layout;
+  Allocator alloc;     // the allocator the arena came from
   void* arena;
   Bins bins;
   void* boxes;
@@ -297,6 +345,13 @@ const char* ib_status_string(ib_status st) {
 
 const char* ib_version(void) { return "ibgb 0.1 (sm_103a)"; }
 
+ib_status ib_set_allocator(ib_alloc_fn alloc, ib_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return IB_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = Allocator{alloc, free_fn, alloc ? ctx : nullptr};
+  return IB_OK;
+}
+
 ib_status ib_plan_footprint(const ib_plan_desc* desc, size_t* bytes) {
   Layout L;
   if (!bytes || !plan_sizes(desc, nullptr, nullptr, nullptr, nullptr, nullptr, &L)) return IB_ERR_INVALID_ARG;
@@ -319,17 +374,17 @@ ib_status ib_plan_create(const ib_plan_desc* desc, ib_plan* out) {
   p->sh.ncomp = desc->ncomp;
   p->sh.mac = desc->grid == IB_GRID_MAC ? 1 : 0;
   p->sh.kernel = desc->kernel;
-  if (cudaMalloc(&p->arena, p->layout.total) != cudaSuccess) {
-    cudaGetLastError();
+  const ib_status ast = arena_alloc(&p->alloc, &p->arena, p->layout.total);
+  if (ast != IB_OK) {
     delete p;
-    return IB_ERR_OOM;
+    return ast;
   }
   p->bins = carve((char*)p->arena, p->layout);
   p->boxes = (char*)p->arena + p->layout.boxes;
   p->bounded = p->job.bnd[0] || p->job.bnd[1] || p->job.bnd[2];
   p->gridx = p->bounded ? (char*)p->arena + p->layout.io : nullptr;
   if (cudaMemset(p->bins.err, 0, sizeof(uint32_t)) != cudaSuccess) {
-    cudaFree(p->arena);
+    arena_free(p->alloc, p->arena);
     delete p;
     return IB_ERR_CUDA;
   }
@@ -340,7 +395,7 @@ ib_status ib_plan_create(const ib_plan_desc* desc, ib_plan* out) {
 ib_status ib_plan_destroy(ib_plan p) {
   if (!p) return IB_OK;
   cudaDeviceSynchronize();
-  cudaFree(p->arena);
+  arena_free(p->alloc, p->arena);
   delete p;
   return IB_OK;
 }
@@ -606,20 +661,20 @@ ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out) {
   b->sh.ncomp = desc->ncomp;
   b->sh.mac = desc->grid == IB_GRID_MAC ? 1 : 0;
   b->sh.kernel = desc->kernel;
-  if (cudaMalloc(&b->arena, b->layout.total) != cudaSuccess) {
-    cudaGetLastError();
+  const ib_status ast = arena_alloc(&b->alloc, &b->arena, b->layout.total);
+  if (ast != IB_OK) {
     delete b;
-    return IB_ERR_OOM;
+    return ast;
   }
   if (cudaMallocHost((void**)&b->h_stage, sizeof(Job) * (size_t)desc->max_jobs) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(b->arena);
+    arena_free(b->alloc, b->arena);
     delete b;
     return IB_ERR_OOM;
   }
   if (cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess) {
     cudaFreeHost(b->h_stage);
-    cudaFree(b->arena);
+    arena_free(b->alloc, b->arena);
     delete b;
     return IB_ERR_CUDA;
   }
@@ -628,7 +683,7 @@ ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out) {
     if (!b->h_jobs) {
       cudaEventDestroy(b->uploaded);
       cudaFreeHost(b->h_stage);
-      cudaFree(b->arena);
+      arena_free(b->alloc, b->arena);
       delete b;
       return IB_ERR_OOM;
     }
@@ -647,7 +702,7 @@ ib_status ib_batch_destroy(ib_batch b) {
   cudaDeviceSynchronize();
   cudaEventDestroy(b->uploaded);
   cudaFreeHost(b->h_stage);
-  cudaFree(b->arena);
+  arena_free(b->alloc, b->arena);
   delete[] b->h_jobs;
   delete b;
   return IB_OK;

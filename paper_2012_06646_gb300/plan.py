@@ -28,6 +28,49 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
+# The ib_set_allocator pair in force: (alloc, free) ctypes callbacks, or None
+# for cudaMalloc / cudaFree.  Plans and batches keep a reference to the pair
+# they were created with, since they free their arena through it.
+_allocator = None
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """Arena allocator of the plans and batches created from now on (ib_set_allocator).
+
+    alloc(nbytes) -> int device pointer (0 when out of memory, 256-byte aligned);
+    free(ptr) -> None.  set_allocator() restores cudaMalloc / cudaFree.  An
+    exception raised by alloc counts as out of memory.
+    """
+    global _allocator
+    lib = _abi.load()
+    if (alloc is None) != (free is None):
+        raise ValueError("set_allocator needs both alloc and free, or neither")
+    if alloc is None:
+        check(lib.ib_set_allocator(_abi.ib_alloc_fn(), _abi.ib_free_fn(), None), "ib_set_allocator")
+        _allocator = None
+        return
+
+    def _alloc(nbytes, _ctx):
+        try:
+            return int(alloc(int(nbytes)) or 0)
+        except Exception:
+            return 0
+
+    def _free(ptr, _ctx):
+        free(int(ptr))
+
+    pair = (_abi.ib_alloc_fn(_alloc), _abi.ib_free_fn(_free))
+    check(lib.ib_set_allocator(pair[0], pair[1], None), "ib_set_allocator")
+    _allocator = pair
+
+
+def use_torch_allocator(device=None) -> None:
+    """Take plan and batch arenas from PyTorch's caching allocator on `device`."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n, dev),
+                  torch.cuda.caching_allocator_delete)
+
+
 class _DeviceArray:
     """Zero-copy view of library-owned device memory through __cuda_array_interface__."""
 
@@ -74,6 +117,7 @@ class Plan:
         self.bounded = tuple(bool(v) for v in bounded)
         self.desc = d
         h = ctypes.c_void_p()
+        self._allocator = _allocator
         with torch.cuda.device(self.device):
             check(self.lib.ib_plan_create(ctypes.byref(d), ctypes.byref(h)), "ib_plan_create")
         self.handle = h
@@ -305,6 +349,7 @@ class Batch:
         d.flags = _abi.IB_BATCH_HOST_IO if host_io else 0
         self.desc = d
         h = ctypes.c_void_p()
+        self._allocator = _allocator
         with torch.cuda.device(self.device):
             check(self.lib.ib_batch_create(ctypes.byref(d), ctypes.byref(h)), "ib_batch_create")
         self.handle = h
@@ -354,6 +399,10 @@ class Batch:
 
     def check(self, stream=None) -> None:
         check(self.lib.ib_batch_check(self.handle, _stream_ptr(stream)), "ib_batch_check")
+
+    def status(self, stream=None) -> int:
+        """ib_batch_check without raising: the status code of the error word (read and cleared)."""
+        return int(self.lib.ib_batch_check(self.handle, _stream_ptr(stream)))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -14,8 +14,19 @@ never leaves the device).  The loop
     from pinned host memory into the slot's device buffers, the wave runs
     in a fixed number of launches for any number of jobs, and U is copied
     back, all on the slot's stream;
-  * retires a wave when its completion event fires and records each
-    request's latency (completion minus arrival).
+  * retires a wave when its completion event fires, reads the wave's device
+    error word on the slot's stream and records each request's outcome and
+    latency (completion minus arrival).
+
+Failures are handled on the host, per request: a job that can never fit a
+wave slot (points, cells or tiles above the slot's capacity, or an invalid
+grid) is rejected when it arrives instead of waiting forever; a request whose
+`cancelled` flag is set before admission is dropped, and one cancelled while
+its wave runs finishes on the device but is reported as cancelled; a wave
+whose error word reports non-finite or out-of-range positions marks the
+requests whose results carry NaN (the kernels' output for such points) as
+invalid and the others as done.  If the arena of a wave slot after the first
+cannot be allocated (IB_ERR_OOM), the server runs with the slots it has.
 
 `single_job_loop` is the comparison: per job, copy in, ib_spread +
 ib_interpolate on a plan for its grid size, copy U out, wait.
@@ -32,7 +43,12 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
+from . import _abi
+from ._abi import IBError
 from .plan import Batch, Plan
+
+# Outcomes of a request (Request.status).
+WAITING, DONE, REJECTED, CANCELLED, INVALID = "waiting", "done", "rejected", "cancelled", "invalid_positions"
 
 
 @dataclass
@@ -46,6 +62,9 @@ class Request:
     U: torch.Tensor | None = None    # result, pinned host
     t_admit: float = -1.0
     t_done: float = -1.0
+    cancelled: bool = False          # set by the caller (Server.cancel) at any time
+    status: str = WAITING            # outcome once served: done, rejected, cancelled, invalid_positions
+    reason: str = ""                 # why a request was rejected
 
     @property
     def npts(self) -> int:
@@ -71,10 +90,11 @@ class ServeStats:
     jobs: int = 0
     waves: int = 0
     max_inflight_bytes: int = 0
+    outcomes: dict = field(default_factory=dict)
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        return {"jobs": self.jobs, "waves": self.waves, "wall_s": self.wall_s,
+        return {"jobs": self.jobs, "waves": self.waves, "wall_s": self.wall_s, "outcomes": dict(self.outcomes),
                 "pts_per_s": self.points / self.wall_s if self.wall_s > 0 else None,
                 "jobs_per_s": self.jobs / self.wall_s if self.wall_s > 0 else None,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -87,6 +107,17 @@ class WaveCaps:
     points: int
     cells: int
     tiles: int
+
+
+def never_fits(npts: int, cells: int, tiles: int, caps: WaveCaps) -> str:
+    """Why a job can never join a wave of a slot with capacities `caps` ('' if it can)."""
+    if npts > caps.points:
+        return f"{npts} points exceed the slot's {caps.points}"
+    if cells > caps.cells:
+        return f"{cells} grid cells exceed the slot's {caps.cells}"
+    if tiles > caps.tiles:
+        return f"{tiles} spreading tiles exceed the slot's {caps.tiles}"
+    return ""
 
 
 def admit_wave(queue, caps: WaveCaps, inflight: int, budget: int):
@@ -116,16 +147,30 @@ class Server:
     def __init__(self, nstreams: int = 3, max_jobs: int = 256, max_points: int = 1 << 23,
                  max_cells: int = 1 << 26, budget_bytes: int | None = None, device=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.nstreams = nstreams
-        self.batches = [Batch(dim=3, grid="mac", max_jobs=max_jobs, max_points=max_points, max_cells=max_cells,
-                              max_tiles=max_cells // 512 + 8 * max_jobs, host_io=True, device=self.device)
-                        for _ in range(nstreams)]
-        self.streams = [torch.cuda.Stream(self.device) for _ in range(nstreams)]
+        self.batches, self.streams = [], []
+        for k in range(nstreams):
+            try:
+                b = Batch(dim=3, grid="mac", max_jobs=max_jobs, max_points=max_points, max_cells=max_cells,
+                          max_tiles=max_cells // 512 + 8 * max_jobs, host_io=True, device=self.device)
+            except IBError as e:
+                if e.status != _abi.IB_ERR_OOM or k == 0:
+                    raise
+                break                   # run with the slots that could be allocated
+            self.batches.append(b)
+            self.streams.append(torch.cuda.Stream(self.device))
+        self.nstreams = len(self.batches)
         self.cap = (max_jobs, max_points, max_cells)
         if budget_bytes is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget_bytes = int(0.5 * free)
         self.budget = int(budget_bytes)
+
+    def cancel(self, r: Request) -> None:
+        """Cancel a request: dropped if not yet admitted, else reported as cancelled when its wave ends."""
+        r.cancelled = True
+
+    def caps(self, slot: int = 0) -> WaveCaps:
+        return WaveCaps(self.cap[0], self.cap[1], self.cap[2], self.batches[slot].desc.max_tiles)
 
     def footprint(self, r: Request) -> tuple:
         job = self.batches[0].job_struct((r.N, r.N, r.N), (r.L, r.L, r.L), r.X)
@@ -151,25 +196,53 @@ class Server:
         inflight = 0
         t0 = time.perf_counter()
         sizes = {}
+        caps0 = self.caps(0)
         while pending or waiting or any(w is not None for w in slots):
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
-                waiting.append(pending.popleft())
+                r = pending.popleft()
+                try:
+                    sizes[r.rid] = self.footprint(r)
+                    r.reason = never_fits(r.npts, r.N ** 3, sizes[r.rid][1], caps0)
+                except IBError as e:          # invalid job description
+                    r.reason = str(e)
+                if r.reason:
+                    r.status = REJECTED
+                    r.t_done = time.perf_counter() - t0
+                    stats.add(r)
+                else:
+                    waiting.append(r)
             for i, w in enumerate(slots):
                 if w is not None and w.event.query():
                     tdone = time.perf_counter() - t0
+                    err = self.batches[i].status(self.streams[i])
+                    if err not in (_abi.IB_OK, _abi.IB_ERR_NONFINITE, _abi.IB_ERR_RANGE):
+                        raise IBError(err, "served wave")
                     for r in w.reqs:
                         r.t_done = tdone
+                        if r.cancelled:
+                            r.status = CANCELLED
+                        elif err != _abi.IB_OK and not bool(torch.isfinite(r.U).all()):
+                            r.status = INVALID
+                        else:
+                            r.status = DONE
                         stats.add(r)
                     inflight -= w.footprint
                     slots[i] = None
+            if any(r.cancelled for r in waiting):
+                keep = collections.deque()
+                for r in waiting:
+                    if r.cancelled:
+                        r.status = CANCELLED
+                        r.t_done = time.perf_counter() - t0
+                        stats.add(r)
+                    else:
+                        keep.append(r)
+                waiting = keep
             for i in range(self.nstreams):
                 if slots[i] is not None or not waiting:
                     continue
-                for r in waiting:
-                    if r.rid not in sizes:
-                        sizes[r.rid] = self.footprint(r)
-                caps = WaveCaps(self.cap[0], self.cap[1], self.cap[2], self.batches[i].desc.max_tiles)
+                caps = self.caps(i)
                 take, fp = admit_wave([(r.npts, r.N ** 3) + sizes[r.rid] for r in waiting], caps, inflight,
                                       self.budget)
                 wave = [waiting.popleft() for _ in range(take)]
@@ -201,15 +274,22 @@ class StatsAccumulator:
         self.jobs = 0
         self.waves = 0
         self.max_inflight = 0
+        self.outcomes = {}
 
     def add(self, r: Request):
+        """Count a finished request; latency and throughput count completed jobs only."""
+        if r.status == WAITING:
+            r.status = DONE
+        self.outcomes[r.status] = self.outcomes.get(r.status, 0) + 1
+        if r.status != DONE:
+            return
         self.lat.append(1e3 * (r.t_done - r.arrival))
         self.points += r.npts
         self.jobs += 1
 
     def finish(self, wall: float) -> ServeStats:
         return ServeStats(latencies_ms=self.lat, wall_s=wall, points=self.points, jobs=self.jobs, waves=self.waves,
-                          max_inflight_bytes=self.max_inflight)
+                          max_inflight_bytes=self.max_inflight, outcomes=dict(self.outcomes))
 
 
 def single_job_loop(requests: list, realtime: bool = True, device=None) -> ServeStats:

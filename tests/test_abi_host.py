@@ -160,6 +160,36 @@ def test_wave_admission_is_fifo_and_respects_caps_and_budget():
     assert admit_wave(big_first, caps, 0, 10 ** 9) == (1, 1)                   # FIFO: no overtaking
 
 
+def test_jobs_that_never_fit_a_slot_are_named():
+    from paper_2012_06646_gb300.serve import WaveCaps, never_fits
+    caps = WaveCaps(jobs=4, points=1000, cells=4096, tiles=64)
+    assert never_fits(1000, 4096, 64, caps) == ""
+    assert "points" in never_fits(1001, 8, 1, caps)
+    assert "cells" in never_fits(10, 4097, 1, caps)
+    assert "tiles" in never_fits(10, 8, 65, caps)
+
+
+def test_allocator_pair_checks_on_host(abi):
+    # ib_set_allocator makes no CUDA call: both NULL restores cudaMalloc, one NULL is an error.
+    lib = abi.load()
+    null_a, null_f = abi.ib_alloc_fn(), abi.ib_free_fn()
+    calls = []
+    a = abi.ib_alloc_fn(lambda n, c: calls.append(n) or 0)
+    f = abi.ib_free_fn(lambda p, c: calls.append(p))
+    assert lib.ib_set_allocator(a, null_f, None) == abi.IB_ERR_INVALID_ARG
+    assert lib.ib_set_allocator(null_a, f, None) == abi.IB_ERR_INVALID_ARG
+    assert lib.ib_set_allocator(a, f, None) == abi.IB_OK
+    assert lib.ib_set_allocator(null_a, null_f, None) == abi.IB_OK
+    assert calls == []                            # installing a pair allocates nothing
+    from paper_2012_06646_gb300 import plan
+    with pytest.raises(ValueError):
+        plan.set_allocator(lambda n: 0, None)
+    plan.set_allocator(lambda n: 0, lambda p: None)
+    assert plan._allocator is not None
+    plan.set_allocator()
+    assert plan._allocator is None
+
+
 def test_inputs_are_deterministic_and_stream_separated():
     import numpy as np
     import ib_inputs

@@ -783,10 +783,13 @@ def run_ours(args):
         Uh = torch.empty((npts, 3), dtype=torch.float32).pin_memory()
         fh = torch.empty(plan.grid_shape(), dtype=torch.float32).pin_memory()
         Xd = torch.empty_like(X)
+        Xn = torch.empty_like(X)
         Gd = torch.empty_like(Gs[0])
-        # Copies overlap the kernels that do not need them, on a copy stream:
-        # G uploads while X is binned, f downloads during interpolation and U
-        # during the position update; the step ends when both streams are done.
+        # Copies overlap the kernels that do not need them, on a copy stream.
+        # Interpolation and the position update do not depend on spreading, so
+        # the overlapped step runs them first: G uploads during binning and
+        # interpolation, U and the new X download while G is spread, and f
+        # downloads last; the step ends when both streams are done.
         cs = torch.cuda.Stream(device)
 
         def sync_ev():
@@ -806,32 +809,37 @@ def run_ours(args):
                         Gd.copy_(Gh[s % len(Gh)], non_blocking=True)
                     e_g = sync_ev()
                     e_g.record(cs)
-                else:
-                    Gd.copy_(Gh[s % len(Gh)], non_blocking=True)
-                plan.bin(Xd, stream=stream)
-                if overlapped:
+                    plan.bin(Xd, stream=stream)
+                    plan.interpolate(Xd, ud, U=U, reuse_bins=True, stream=stream)
+                    e_in = sync_ev()
+                    e_in.record(stream)
+                    plan.advect(Xd, U, dt, out=Xn, stream=stream)
+                    e_ad = sync_ev()
+                    e_ad.record(stream)
+                    with torch.cuda.stream(cs):
+                        cs.wait_event(e_in)
+                        Uh.copy_(U, non_blocking=True)
+                        cs.wait_event(e_ad)
+                        Xh.copy_(Xn, non_blocking=True)
                     stream.wait_event(e_g)
-                plan.spread(Xd, Gd, f=f, reuse_bins=True, stream=stream)
-                e_sp = sync_ev()
-                e_sp.record(stream)
-                plan.interpolate(Xd, ud, U=U, reuse_bins=True, stream=stream)
-                e_in = sync_ev()
-                e_in.record(stream)
-                if overlapped:
+                    plan.spread(Xd, Gd, f=f, reuse_bins=True, stream=stream)
+                    e_sp = sync_ev()
+                    e_sp.record(stream)
                     with torch.cuda.stream(cs):
                         cs.wait_event(e_sp)
                         fh.copy_(f, non_blocking=True)
-                        cs.wait_event(e_in)
-                        Uh.copy_(U, non_blocking=True)
-                plan.advect(Xd, U, dt, out=Xd, stream=stream)
-                if not overlapped:
-                    Uh.copy_(U, non_blocking=True)
-                    fh.copy_(f, non_blocking=True)
-                Xh.copy_(Xd, non_blocking=True)
-                if overlapped:
                     e_cs = sync_ev()
                     e_cs.record(cs)
                     stream.wait_event(e_cs)
+                else:
+                    Gd.copy_(Gh[s % len(Gh)], non_blocking=True)
+                    plan.bin(Xd, stream=stream)
+                    plan.spread(Xd, Gd, f=f, reuse_bins=True, stream=stream)
+                    plan.interpolate(Xd, ud, U=U, reuse_bins=True, stream=stream)
+                    plan.advect(Xd, U, dt, out=Xd, stream=stream)
+                    Uh.copy_(U, non_blocking=True)
+                    fh.copy_(f, non_blocking=True)
+                    Xh.copy_(Xd, non_blocking=True)
                 b.record(stream)
                 b.synchronize()
                 if s % nsteps >= args.warmup:
@@ -841,8 +849,9 @@ def run_ours(args):
         e2e = {"value": job_rate(npts, world, args.steps, tot), "unit": "pts/s",
                "h2d_bytes_per_step": int(Xd.numel() * 4 + Gd.numel() * 4),
                "d2h_bytes_per_step": int(Uh.numel() * 4 + fh.numel() * 4 + Xh.numel() * 4),
-               "copies": "G upload during binning, f download during interpolation, U during the update "
-                         "(copy stream); X in and out on the compute stream",
+               "copies": "X upload on the compute stream; G upload during binning and interpolation, U and the "
+                         "new X download while G is spread, f download after it (copy stream); interpolation and "
+                         "the position update run before spreading, which they do not depend on",
                "value_copies_serialised": job_rate(npts, world, args.steps, tot_seq)}
 
     membranes = None

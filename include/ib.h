@@ -70,8 +70,11 @@ typedef enum {
   IB_ERR_RANGE = 8,           /* a position was 2^30 or more cells away from the box, or outside
                                  [0, L] along a bounded dimension */
   IB_ERR_NO_BINS = 9,         /* IB_REUSE_BINS without a matching ib_bin call */
-  IB_ERR_BINS_STALE = 10      /* positions changed after binning (or X aliased an output):
+  IB_ERR_BINS_STALE = 10,     /* positions changed after binning (or X aliased an output):
                                  the points concerned spread nothing and interpolate to NaN */
+  IB_ERR_BOUNDS = 11          /* a library built with IB_DEBUG_BOUNDS found an index outside its
+                                 array and skipped the access (a library defect; never returned
+                                 by the release build, whose checks compile away) */
 } ib_status;
 
 /* One-dimensional kernel phi of delta_h (Section 2; the methods do not depend
@@ -206,7 +209,8 @@ ib_status ib_advect(ib_plan plan, long long npts, const void* X, const void* U, 
 
 /* Read and clear the plan's device error word with copies ordered on
  * `stream`, waiting for that stream only (work on other streams keeps
- * running): IB_OK, IB_ERR_NONFINITE, IB_ERR_RANGE or IB_ERR_BINS_STALE (or
+ * running): IB_OK, IB_ERR_NONFINITE, IB_ERR_RANGE, IB_ERR_BINS_STALE or
+ * IB_ERR_BOUNDS (debug build only; it takes precedence over the others) (or
  * IB_ERR_CUDA if the stream reports an error). */
 ib_status ib_plan_check(ib_plan plan, void* stream);
 

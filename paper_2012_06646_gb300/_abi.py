@@ -12,6 +12,13 @@ import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libibgb.so")
+# The index-checking build (build(debug_bounds=True)); loaded instead of the
+# release library when the environment sets IBGB_DEBUG_BOUNDS=1.
+DEBUG_LIB_PATH = os.path.join(_HERE, "_lib_debug", "libibgb.so")
+
+
+def default_path() -> str:
+    return DEBUG_LIB_PATH if os.environ.get("IBGB_DEBUG_BOUNDS") == "1" else LIB_PATH
 
 IB_OK = 0
 IB_ERR_INVALID_ARG = 1
@@ -24,6 +31,7 @@ IB_ERR_NONFINITE = 7
 IB_ERR_RANGE = 8
 IB_ERR_NO_BINS = 9
 IB_ERR_BINS_STALE = 10
+IB_ERR_BOUNDS = 11
 
 IB_KERNEL_PESKIN4 = 0
 IB_KERNEL_COSINE4 = 1
@@ -118,11 +126,12 @@ SIGNATURES = {
 _lib = None
 
 
-def load(path: str = LIB_PATH):
+def load(path: str | None = None):
     """Load libibgb.so and declare every entry point; raises if the library is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or default_path()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing: build it with paper_2012_06646_gb300.build.build() "
                            "(there is no CPU fallback)")

@@ -202,6 +202,7 @@ ib_status check_error_word(uint32_t* err_dev, cudaStream_t s) {
     if (cudaMemsetAsync(err_dev, 0, sizeof(uint32_t), s) != cudaSuccess) return IB_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
   }
+  if (e & ERR_BOUNDS) return IB_ERR_BOUNDS;
   if (e & ERR_NONFINITE) return IB_ERR_NONFINITE;
   if (e & ERR_RANGE) return IB_ERR_RANGE;
   if (e & ERR_STALE) return IB_ERR_BINS_STALE;
@@ -339,11 +340,16 @@ const char* ib_status_string(ib_status st) {
     case IB_ERR_RANGE: return "IB_ERR_RANGE";
     case IB_ERR_NO_BINS: return "IB_ERR_NO_BINS";
     case IB_ERR_BINS_STALE: return "IB_ERR_BINS_STALE";
+    case IB_ERR_BOUNDS: return "IB_ERR_BOUNDS";
   }
   return "IB_ERR_UNKNOWN";
 }
 
+#ifdef IB_DEBUG_BOUNDS
+const char* ib_version(void) { return "ibgb 0.1 (sm_103a, IB_DEBUG_BOUNDS)"; }
+#else
 const char* ib_version(void) { return "ibgb 0.1 (sm_103a)"; }
+#endif
 
 ib_status ib_set_allocator(ib_alloc_fn alloc, ib_free_fn free_fn, void* ctx) {
   if ((alloc == nullptr) != (free_fn == nullptr)) return IB_ERR_INVALID_ARG;

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__
     if (full || g0 + i < n) key[i] = point_key<float, D>(jb, B, x + i * D, sh, key_comp);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
-    if (full || g0 + i < n) rank[i] = atomicAdd(&B.count[key[i]], 1u);
+    if (full || g0 + i < n) rank[i] = IB_IN(B.err, key[i], B.ncell_total + 1) ? atomicAdd(&B.count[key[i]], 1u) : 0u;
   if (full) {
     *reinterpret_cast<uint4*>(B.key + g0) = make_uint4(key[0], key[1], key[2], key[3]);
     *reinterpret_cast<uint4*>(B.rank + g0) = make_uint4(rank[0], rank[1], rank[2], rank[3]);
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ 
   const Job& jb = job_at(J, job_of_point(J, g));
   const uint32_t k = point_key<T, D>(jb, B, (const T*)jb.X + (g - jb.pt_base) * D, sh, key_comp);
   B.key[g] = k;
-  B.rank[g] = atomicAdd(&B.count[k], 1u);
+  B.rank[g] = IB_IN(B.err, k, B.ncell_total + 1) ? atomicAdd(&B.count[k], 1u) : 0u;
 }
 
 // Block-level exclusive scan of per-thread totals; returns this thread's
@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter(const Bins B) {
   const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (g >= B.npts_total) return;
   const uint32_t k = B.key[g];
-  B.perm_tmp[B.count[k] + B.rank[g]] = make_uint2((uint32_t)g, k);
+  if (!IB_IN(B.err, k, B.ncell_total + 1)) return;
+  const long long dst = (long long)B.count[k] + B.rank[g];
+  if (IB_IN(B.err, dst, B.npts_total)) B.perm_tmp[dst] = make_uint2((uint32_t)g, k);
 }
 
 // Stable order inside a cell, one thread per sorted position q: the point at
@@ -259,12 +261,14 @@ __global__ void __launch_bounds__(kThreads) k_bin_stable(const Bins B) {
   const long long q = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (q >= B.npts_total) return;
   const uint2 e = B.perm_tmp[q];
+  if (!IB_IN(B.err, e.y, B.ncell_total + 1)) return;
   const uint32_t s = B.count[e.y];
   const uint32_t t = B.count[e.y + 1];
   if (t - s == 1) {
     B.perm[q] = e.x;
     return;
   }
+  if (!IB_IN(B.err, t, B.npts_total + 1) || !IB_IN(B.err, s, (long long)t)) return;
   uint32_t r = 0;
   for (uint32_t j = s; j < t; ++j) r += (B.perm_tmp[j].x < e.x) ? 1u : 0u;
   B.perm[s + r] = e.x;

@@ -17,6 +17,23 @@ namespace ibgb {
 constexpr uint32_t ERR_NONFINITE = 1u;
 constexpr uint32_t ERR_RANGE = 2u;
 constexpr uint32_t ERR_STALE = 4u;   // a point's cell no longer matches its bin (X changed after binning)
+constexpr uint32_t ERR_BOUNDS = 8u;  // an index check of the IB_DEBUG_BOUNDS build failed (access skipped)
+
+// Index checks of the debug build.  Compiled with IB_DEBUG_BOUNDS, IB_IN(err,
+// i, n) is true when 0 <= i < n; otherwise it sets ERR_BOUNDS in the error
+// word and the access it guards is skipped, so a wrong index is reported
+// through ib_plan_check / ib_batch_check instead of touching memory.  In the
+// release build it is the constant true and the checks compile away.
+#ifdef IB_DEBUG_BOUNDS
+__device__ __forceinline__ bool ib_in(uint32_t* err, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(err, ERR_BOUNDS);
+  return false;
+}
+#define IB_IN(err, i, n) ::ibgb::ib_in((err), (long long)(i), (long long)(n))
+#else
+#define IB_IN(err, i, n) true
+#endif
 
 // Positions are accepted while |X_b N_b / L_b| < 2^30 (cell indices fit in int).
 constexpr double kMaxCells = 1073741824.0;

@@ -227,8 +227,10 @@ __global__ void __launch_bounds__(32 * W) k_spread_warp(const __grid_constant__ 
       const int y = T0[1] + ((D == 3) ? r % TE[1] : r);
       const int z = (D == 3) ? T0[2] + r / TE[1] : 0;
       const long long cell = jb.cell_base + T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
-      st = B.count[cell];
-      cnt = B.count[cell + TE[0]] - st;
+      if (IB_IN(B.err, cell + TE[0], B.ncell_total + 1)) {
+        st = B.count[cell];
+        cnt = B.count[cell + TE[0]] - st;
+      }
     }
     uint32_t inc = cnt;
 #pragma unroll
@@ -255,7 +257,9 @@ __global__ void __launch_bounds__(32 * W) k_spread_warp(const __grid_constant__ 
 #pragma unroll
     for (int step = NROWS / 2; step >= 1; step >>= 1)
       if (lo + step < rows && rpre[lo + step] <= q) lo += step;
-    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])] - jb.pt_base;
+    const long long pi = (long long)rstart[lo] + (q - rpre[lo]);
+    long long li = IB_IN(B.err, pi, B.npts_total) ? (long long)B.perm[pi] - jb.pt_base : 0;
+    if (!IB_IN(B.err, li, jb.npts)) li = 0;
 #pragma unroll
     for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
     gs = Gp[li * nc + a];
@@ -273,7 +277,9 @@ __global__ void __launch_bounds__(32 * W) k_spread_warp(const __grid_constant__ 
     if (base + lane < M) {
       int o[3] = {0, 0, 0};
       T w[3][4];
-      const bool inside = point_comp<T, D>(jb, sh, xs, T0, TE, a, o, w);
+      bool inside = point_comp<T, D>(jb, sh, xs, T0, TE, a, o, w);
+#pragma unroll
+      for (int b = 0; b < D; ++b) inside = inside && IB_IN(B.err, o[b], Gm::BX - 3);
       T ga = hmd * gs;
       if (!inside) {                 // X changed after binning: contribute nothing, report
         atomicOr(B.err, ERR_STALE);
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(32 * W) k_spread_warp(const __grid_constant__ 
         if (D == 3) load3(rn + zsel, nz0, nz1, nob);
         else nob = rn[16];
       }
-      if (lane_on) {
+      if (lane_on && IB_IN(B.err, idx, (D == 3) ? Gm::BV - ZSTEP : Gm::BV)) {
         if (D == 3) {
           if (COMP) {
             two_sum_into(boxS + idx, boxE + idx, pv * z0);
@@ -406,6 +412,9 @@ __device__ __forceinline__ void tile3_record(const Job& jb, const Shape& sh, con
   T g[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) g[a] = hmd * gs[a];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)   // both staggerings' corners inside the box (debug build)
+    inside = inside && IB_IN(B.err, o0[b], Gm::BX - 3) && IB_IN(B.err, o0[b] + dl[b], Gm::BX - 3);
   if (!inside) {                 // X changed after binning: contribute nothing, report
     atomicOr(B.err, ERR_STALE);
 #pragma unroll
@@ -442,7 +451,7 @@ __device__ __forceinline__ void tile3_record(const Job& jb, const Shape& sh, con
 // Stage 2 for one batch of cnt records starting at rb (one record past the
 // batch is allocated, so the look-ahead read of record cnt stays in bounds).
 template <typename T, bool COMP>
-__device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane) {
+__device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane, uint32_t* err) {
   using Gm = Geo<3, 8>;
   constexpr int PLANES = COMP ? 2 : 1;
   constexpr int ZSTEP = 2 * Gm::BY * Gm::BX;
@@ -463,6 +472,11 @@ __device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane
     const int q0 = (pk & 4095) + lane_off;
     const int q1 = q0 + ((pk >> 12) & 1023) - 512 + PLANES * Gm::BV;
     const int q2 = q0 + (int)((unsigned)pk >> 22) - 512 + 2 * PLANES * Gm::BV;
+    if (!(IB_IN(err, q0, Gm::BV - ZSTEP) && IB_IN(err, q1 - PLANES * Gm::BV, Gm::BV - ZSTEP) &&
+          IB_IN(err, q2 - 2 * PLANES * Gm::BV, Gm::BV - ZSTEP))) {
+      __syncwarp();
+      continue;
+    }
     if (COMP) {
       two_sum_into(box + q0, box + q0 + Gm::BV, c0 * z0);
       two_sum_into(box + q0 + ZSTEP, box + q0 + ZSTEP + Gm::BV, c0 * z1);
@@ -525,8 +539,10 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
       const int y = T0[1] + r % TE[1];
       const int z = T0[2] + r / TE[1];
       const long long cell = jb.cell_base + T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
-      st[k] = B.count[cell];
-      cn[k] = B.count[cell + TE[0]];
+      if (IB_IN(B.err, cell + TE[0], B.ncell_total + 1)) {
+        st[k] = B.count[cell];
+        cn[k] = B.count[cell + TE[0]];
+      }
     }
   }
   {
@@ -562,10 +578,12 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
 #pragma unroll
     for (int step = NROWS / 2; step >= 1; step >>= 1)
       if (lo + step < rows && rpre[lo + step] <= q) lo += step;
-    return B.perm[rstart[lo] + (q - rpre[lo])];
+    const long long pi = (long long)rstart[lo] + (q - rpre[lo]);
+    return IB_IN(B.err, pi, B.npts_total) ? B.perm[pi] : (uint32_t)jb.pt_base;
   };
   auto fetch = [&](uint32_t g, T xs[3], T gs[3]) {
-    const long long li = (long long)g - jb.pt_base;
+    long long li = (long long)g - jb.pt_base;
+    if (!IB_IN(B.err, li, jb.npts)) li = 0;
 #pragma unroll
     for (int b = 0; b < 3; ++b) xs[b] = Xg[li * 3 + b];
 #pragma unroll
@@ -580,7 +598,7 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
     if (base + kSpreadBatch + lane < M) fetch(pn, xs, gs);
     if (base + 2 * kSpreadBatch + lane < M) pn = point_of(base + 2 * kSpreadBatch + lane);
     __syncwarp();
-    tile3_add<T, COMP>(box, rec_s, (int)min((uint32_t)kSpreadBatch, M - base), lane);
+    tile3_add<T, COMP>(box, rec_s, (int)min((uint32_t)kSpreadBatch, M - base), lane, B.err);
     __syncwarp();
   }
   // Boxes -> scratch [tile][comp][plane][BV]: the shared layout, one contiguous copy.
@@ -658,14 +676,33 @@ __device__ __forceinline__ Cover3 cover_fast(int x, int n, int ntile) {
   return c;
 }
 
+// Debug build: every entry of a cover list names a tile of the job's row of
+// tiles and an offset inside its box (room for `width` consecutive nodes).
+template <int TS>
+__device__ __forceinline__ bool cover_ok(uint32_t* err, const Cover3& c, int ntile, int width) {
+#ifdef IB_DEBUG_BOUNDS
+  bool ok = IB_IN(err, c.n, 4);
+  for (int i = 0; i < 3; ++i)
+    if (i < c.n) ok = ok && IB_IN(err, c.t(i), ntile) && IB_IN(err, c.o(i), TS + 4 - (width - 1));
+  return ok;
+#else
+  (void)err; (void)c; (void)ntile; (void)width;
+  return true;
+#endif
+}
+
 template <typename T, int D, int TS, bool CP, bool CHECK>
 __device__ __noinline__ void combine_general(const Jobs& J, int j, const Shape& sh, const T* __restrict__ boxes,
                                              const uint32_t* __restrict__ tflags, const int* x, long long lc,
-                                             int accumulate) {
+                                             int accumulate, uint32_t* err) {
   using Gm = Geo<D, TS>;
   const Job& jb = job_at(J, j);
   int tl[3][kMaxCover], of[3][kMaxCover], nco[3];
-  for (int b = 0; b < D; ++b) nco[b] = cover_list<TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
+  for (int b = 0; b < D; ++b) {
+    nco[b] = cover_list<TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
+    for (int i = 0; i < nco[b]; ++i)
+      if (!(IB_IN(err, tl[b][i], jb.ntile[b]) && IB_IN(err, of[b][i], TS + 4))) return;
+  }
   if (D == 2) {
     nco[2] = 1;
     tl[2][0] = 0;
@@ -739,7 +776,7 @@ template <typename T, int D, int TS, bool CP, int V, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_constant__ Jobs J, const Shape sh,
                                                              const T* __restrict__ boxes,
                                                              const uint32_t* __restrict__ tflags, long long ncell_total,
-                                                             int accumulate) {
+                                                             int accumulate, uint32_t* err) {
   using Gm = Geo<D, TS>;
   // Blocks walk the grid from its end: the tile kernel writes the boxes in
   // tile order, so the last-written boxes (the ones still in L2) are read first.
@@ -766,7 +803,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       int xv[3] = {x[0] + v, x[1], x[2]};
-      combine_general<T, D, TS, CP, CHECK>(J, jj, sh, boxes, tflags, xv, lc + v, accumulate);
+      combine_general<T, D, TS, CP, CHECK>(J, jj, sh, boxes, tflags, xv, lc + v, accumulate, err);
     }
     return;
   }
@@ -779,6 +816,9 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
     cz.n = 1;
     cz.t0 = cz.o0 = cz.t1 = cz.o1 = cz.t2 = cz.o2 = 0;
   }
+  if (!(cover_ok<TS>(err, cx, jb.ntile[0], V) && cover_ok<TS>(err, cy, jb.ntile[1], 1) &&
+        (D == 2 || cover_ok<TS>(err, cz, jb.ntile[2], 1))))
+    return;
   const int nc = sh.ncomp;
   const long long plane = (long long)(CP ? 2 : 1) * Gm::BV;
   T S[4][V], E[4][V];
@@ -977,8 +1017,9 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
         const int bz = rem / Gm::BY;
         const int by = rem - bz * Gm::BY;
         const int xw = wrapn(T0[0] - 2 + 2 * c, n0);
-        const T* src = u + (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
-        __pipeline_memcpy_async(box + row * Gm::BX + 2 * c, src, 2 * sizeof(T));
+        const long long si = (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
+        if (IB_IN(B.err, si, nc * jb.ncell - 1))
+          __pipeline_memcpy_async(box + row * Gm::BX + 2 * c, u + si, 2 * sizeof(T));
       }
     } else {
       for (int bx0 = tid % BXP; bx0 < Gm::BX; bx0 += BXP) {
@@ -988,8 +1029,8 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
           const int rem = row - a * (Gm::BZ * Gm::BY);
           const int bz = rem / Gm::BY;
           const int by = rem - bz * Gm::BY;
-          const T* src = u + (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
-          __pipeline_memcpy_async(box + row * Gm::BX + bx0, src, sizeof(T));
+          const long long si = (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
+          if (IB_IN(B.err, si, nc * jb.ncell)) __pipeline_memcpy_async(box + row * Gm::BX + bx0, u + si, sizeof(T));
         }
       }
     }
@@ -1042,7 +1083,9 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
       const int mid = (lo + hi + 1) >> 1;
       if (rpre[mid] <= q) lo = mid; else hi = mid - 1;
     }
-    return B.perm[rstart[lo] + (q - rpre[lo])];
+    const long long pi = (long long)rstart[lo] + (q - rpre[lo]);
+    const uint32_t gp = IB_IN(B.err, pi, B.npts_total) ? B.perm[pi] : (uint32_t)jb.pt_base;
+    return IB_IN(B.err, (long long)gp - jb.pt_base, jb.npts) ? gp : (uint32_t)jb.pt_base;
   };
   const T* Xg = (const T*)jb.X;
   // Software pipeline over this thread's points: the next point's index is
@@ -1061,7 +1104,10 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     const long long li = (long long)g - jb.pt_base;
     PointBox<T, D> Pb;
     T* U = (T*)jb.U + li * nc;
-    const bool ok = point_box<T, D>(jb, sh, xs, T0, TE, Pb);
+    bool ok = point_box<T, D>(jb, sh, xs, T0, TE, Pb);
+#pragma unroll
+    for (int b = 0; b < D; ++b)   // both staggerings' corners inside the box (debug build)
+      ok = ok && IB_IN(B.err, Pb.o0[b], Gm::BX - 3) && IB_IN(B.err, Pb.o1[b], Gm::BX - 3);
     if (more) {
 #pragma unroll
       for (int b = 0; b < D; ++b) xs[b] = Xg[((long long)gn - jb.pt_base) * D + b];
@@ -1119,6 +1165,7 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad(const __grid_constant__ J
   const uint32_t g = B.perm[p];
   const Job jb = job_at(J, job_of_point(J, (long long)g));
   const long long li = (long long)g - jb.pt_base;
+  if (!IB_IN(B.err, li, jb.npts)) return;
   const int nc = sh.ncomp;
   const T* Xp = (const T*)jb.X + li * D;
   T* Dp = Dout + li * D;
@@ -1176,7 +1223,7 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad(const __grid_constant__ J
         T rx = 0, rdx = 0;
 #pragma unroll
         for (int tx = 0; tx < 4; ++tx) {
-          const T val = __ldg(row + ox[tx]);
+          const T val = IB_IN(B.err, oz[tz] + oy[ty] + ox[tx], jb.ncell) ? __ldg(row + ox[tx]) : (T)0;
           rx += wx[tx] * val;
           rdx += dx[tx] * val;
         }
@@ -1295,9 +1342,11 @@ void launch_combine(const Jobs& J, const Shape& sh, const Bins& B, const void* b
                     cudaStream_t s) {
   const unsigned g = grid_for((B.ncell_total + V - 1) / V, kThreads);
   if (sparse)
-    k_spread_combine<T, D, TS, CP, V, true><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total, acc);
+    k_spread_combine<T, D, TS, CP, V, true><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total, acc,
+                                                                   B.err);
   else
-    k_spread_combine<T, D, TS, CP, V, false><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total, acc);
+    k_spread_combine<T, D, TS, CP, V, false><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total,
+                                                                    acc, B.err);
 }
 
 template <typename T, int D, int TS>

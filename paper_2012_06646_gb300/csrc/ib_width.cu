@@ -244,8 +244,10 @@ __global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant
       const int y = T0[1] + ((D == 3) ? r % TE[1] : r);
       const int z = (D == 3) ? T0[2] + r / TE[1] : 0;
       const long long cell = T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
-      st = B.count[cell];
-      cnt = B.count[cell + TE[0]] - st;
+      if (IB_IN(B.err, cell + TE[0], B.ncell_total + 1)) {
+        st = B.count[cell];
+        cnt = B.count[cell + TE[0]] - st;
+      }
     }
     uint32_t inc = cnt;
 #pragma unroll
@@ -267,7 +269,9 @@ __global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant
 #pragma unroll
     for (int step = W::NROWS / 2; step >= 1; step >>= 1)
       if (lo + step < rows && rpre[lo + step] <= q) lo += step;
-    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])];
+    const long long pi = (long long)rstart[lo] + (q - rpre[lo]);
+    long long li = IB_IN(B.err, pi, B.npts_total) ? (long long)B.perm[pi] : 0;
+    if (!IB_IN(B.err, li, jb.npts)) li = 0;
 #pragma unroll
     for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
     gs = Gp[li * nc + a];
@@ -308,6 +312,8 @@ __global__ void __launch_bounds__(32 * kWWarps) k_spread_w(const __grid_constant
       bool inside = true;
 #pragma unroll
       for (int b = 0; b < D; ++b) inside = wpoint_dim<T, D, S, TS>(jb, sh, xs[b], b, a, T0, TE, o[b], w[b]) && inside;
+#pragma unroll
+      for (int b = 0; b < D; ++b) inside = inside && IB_IN(B.err, o[b], W::BS - S + 1);
       T ga = hmd * gs;
       if (!inside) {                 // X changed after binning: contribute nothing, report
         atomicOr(B.err, ERR_STALE);
@@ -392,8 +398,10 @@ __global__ void __launch_bounds__(32) k_spread_w3(const __grid_constant__ Jobs J
       const int y = T0[1] + r % TE[1];
       const int z = T0[2] + r / TE[1];
       const long long cell = T0[0] + (long long)jb.n[0] * (y + (long long)jb.n[1] * z);
-      st = B.count[cell];
-      cnt = B.count[cell + TE[0]] - st;
+      if (IB_IN(B.err, cell + TE[0], B.ncell_total + 1)) {
+        st = B.count[cell];
+        cnt = B.count[cell + TE[0]] - st;
+      }
     }
     uint32_t inc = cnt;
 #pragma unroll
@@ -414,7 +422,9 @@ __global__ void __launch_bounds__(32) k_spread_w3(const __grid_constant__ Jobs J
 #pragma unroll
     for (int step = W::NROWS / 2; step >= 1; step >>= 1)
       if (lo + step < rows && rpre[lo + step] <= q) lo += step;
-    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])];
+    const long long pi = (long long)rstart[lo] + (q - rpre[lo]);
+    long long li = IB_IN(B.err, pi, B.npts_total) ? (long long)B.perm[pi] : 0;
+    if (!IB_IN(B.err, li, jb.npts)) li = 0;
 #pragma unroll
     for (int b = 0; b < 3; ++b) xs[b] = Xg[li * 3 + b];
 #pragma unroll
@@ -448,7 +458,11 @@ __global__ void __launch_bounds__(32) k_spread_w3(const __grid_constant__ Jobs J
         T w[3][S];
 #pragma unroll
         for (int b = 0; b < 3; ++b) wselect<T, 3, S, TS>(cl[b], cc[b], half_stag(sh, a, b), o[b], w[b]);
-        const T ga = inside ? hmd * gs[a] : (T)0;
+        bool in_a = inside;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) in_a = in_a && IB_IN(B.err, o[b], W::BS - S + 1);
+        if (!in_a) o[0] = o[1] = o[2] = 0;
+        const T ga = in_a ? hmd * gs[a] : (T)0;
         T* ra = rec + a * RC;
 #pragma unroll
         for (int ty = 0; ty < S; ++ty)
@@ -561,7 +575,7 @@ __device__ __forceinline__ WCover3 wcover_fast(int x, int n, int ntile) {
 
 template <typename T, int D, int S, int TS>
 __global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ Jobs J, const Shape sh,
-                                                         const T* __restrict__ boxes, int accumulate) {
+                                                         const T* __restrict__ boxes, int accumulate, uint32_t* err) {
   using W = WGeo<D, S, TS>;
   const Job& jb = J.one;
   const long long lc = (long long)blockIdx.x * kThreads + threadIdx.x;
@@ -586,6 +600,16 @@ __global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ 
       cz.n = 1;
       cz.t0 = cz.o0 = cz.t1 = cz.o1 = cz.t2 = cz.o2 = 0;
     }
+#ifdef IB_DEBUG_BOUNDS
+    {
+      const WCover3* cv[3] = {&cx, &cy, &cz};
+      for (int b = 0; b < D; ++b) {
+        if (!IB_IN(err, cv[b]->n, 4)) return;
+        for (int i = 0; i < cv[b]->n; ++i)
+          if (!(IB_IN(err, cv[b]->t(i), jb.ntile[b]) && IB_IN(err, cv[b]->o(i), W::BS))) return;
+      }
+    }
+#endif
     // up to 27 boxes, all entries loaded before the sums (in the fixed order)
     T S4[4] = {(T)0, (T)0, (T)0, (T)0};
 #pragma unroll
@@ -621,7 +645,11 @@ __global__ void __launch_bounds__(kThreads) k_combine_w(const __grid_constant__ 
   }
   int tl[3][kWCover], of[3][kWCover], nco[3];
 #pragma unroll
-  for (int b = 0; b < D; ++b) nco[b] = wcover<S, TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
+  for (int b = 0; b < D; ++b) {
+    nco[b] = wcover<S, TS>(x[b], jb.n[b], jb.ntile[b], tl[b], of[b]);
+    for (int i = 0; i < nco[b]; ++i)
+      if (!(IB_IN(err, tl[b][i], jb.ntile[b]) && IB_IN(err, of[b][i], W::BS))) return;
+  }
   if (D == 2) {
     nco[2] = 1;
     tl[2][0] = 0;
@@ -708,7 +736,9 @@ __global__ void __launch_bounds__(kWInterpThreads, sizeof(T) == 4 ? 6 : 4) k_int
       const int mid = (lo + hi + 1) >> 1;
       if (rpre[mid] <= q) lo = mid; else hi = mid - 1;
     }
-    const long long li = (long long)B.perm[rstart[lo] + (q - rpre[lo])];
+    const long long pi = (long long)rstart[lo] + (q - rpre[lo]);
+    const long long li = IB_IN(B.err, pi, B.npts_total) ? (long long)B.perm[pi] : -1;
+    if (!IB_IN(B.err, li, jb.npts)) continue;
     T xs[D];
 #pragma unroll
     for (int b = 0; b < D; ++b) xs[b] = Xg[li * D + b];
@@ -728,6 +758,10 @@ __global__ void __launch_bounds__(kWInterpThreads, sizeof(T) == 4 ? 6 : 4) k_int
       T w[3][S];
 #pragma unroll
       for (int b = 0; b < D; ++b) wselect<T, D, S, TS>(cl[b], cc[b], half_stag(sh, a, b), o[b], w[b]);
+      bool in_a = true;
+#pragma unroll
+      for (int b = 0; b < D; ++b) in_a = in_a && IB_IN(B.err, o[b], W::BS - S + 1);
+      if (!in_a) continue;
       const T* bp = box + a * W::BV + (o[2] * W::BS + o[1]) * W::BS + o[0];
       T acc = 0;
 #pragma unroll
@@ -762,6 +796,7 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad_w(const __grid_constant__
   if (p >= B.npts_total) return;
   const Job& jb = J.one;
   const long long li = (long long)B.perm[p];
+  if (!IB_IN(B.err, li, jb.npts)) return;
   const int nc = sh.ncomp;
   const T* Xp = (const T*)jb.X + li * D;
   T* Dp = Dout + li * D;
@@ -817,7 +852,7 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad_w(const __grid_constant__
         T rx = 0, rdx = 0;
 #pragma unroll
         for (int tx = 0; tx < S; ++tx) {
-          const T val = __ldg(row + off[0][tx]);
+          const T val = IB_IN(B.err, oz + off[1][ty] + off[0][tx], jb.ncell) ? __ldg(row + off[0][tx]) : (T)0;
           rx += w[0][tx] * val;
           rdx += dw[0][tx] * val;
         }
@@ -851,7 +886,7 @@ cudaError_t spread_w(const Jobs& J, const Shape& sh, const Bins& B, void* boxes,
       k_spread_w3<T, S><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes);
       if (J.one.ncell > 0)
         k_combine_w<T, D, S, TS><<<grid_for(J.one.ncell, kThreads), kThreads, 0, s>>>(J, sh, (const T*)boxes,
-                                                                                       accumulate ? 1 : 0);
+                                                                                       accumulate ? 1 : 0, B.err);
       return cudaGetLastError();
     }
   }
@@ -862,7 +897,7 @@ cudaError_t spread_w(const Jobs& J, const Shape& sh, const Bins& B, void* boxes,
   }
   if (J.one.ncell > 0)
     k_combine_w<T, D, S, TS><<<grid_for(J.one.ncell, kThreads), kThreads, 0, s>>>(J, sh, (const T*)boxes,
-                                                                                   accumulate ? 1 : 0);
+                                                                                   accumulate ? 1 : 0, B.err);
   return cudaGetLastError();
 }
 

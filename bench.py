@@ -804,7 +804,10 @@ def run_ours(args):
                 a.record(stream)
                 Xd.copy_(Xh, non_blocking=True)
                 if overlapped:
-                    cs.wait_event(a)
+                    # G follows X on the link (binning waits for X only)
+                    e_x = sync_ev()
+                    e_x.record(stream)
+                    cs.wait_event(e_x)
                     with torch.cuda.stream(cs):
                         Gd.copy_(Gh[s % len(Gh)], non_blocking=True)
                     e_g = sync_ev()
@@ -849,7 +852,7 @@ def run_ours(args):
         e2e = {"value": job_rate(npts, world, args.steps, tot), "unit": "pts/s",
                "h2d_bytes_per_step": int(Xd.numel() * 4 + Gd.numel() * 4),
                "d2h_bytes_per_step": int(Uh.numel() * 4 + fh.numel() * 4 + Xh.numel() * 4),
-               "copies": "X upload on the compute stream; G upload during binning and interpolation, U and the "
+               "copies": "X upload on the compute stream; G upload after it, during binning and interpolation, U and the "
                          "new X download while G is spread, f download after it (copy stream); interpolation and "
                          "the position update run before spreading, which they do not depend on",
                "value_copies_serialised": job_rate(npts, world, args.steps, tot_seq)}

@@ -129,6 +129,15 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
+def step_distribution(ms: list):
+    """p50 / p99 / min / max / mean of this rank's timed step durations (ms)."""
+    if not ms:
+        return None
+    a = np.asarray(ms, dtype=np.float64)
+    return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)), "min": float(a.min()),
+            "max": float(a.max()), "mean": float(a.mean()), "n": int(a.size)}
+
+
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
     captured on the current kernel sources (else None)."""
@@ -954,6 +963,7 @@ def run_ours(args):
             "calls_ms": mean_ms,
             "step_ms_as_separate_calls": statistics.mean(plain_ms) if plain_ms else None,
             "step_as_cuda_graph": bool(graphs),
+            "step_ms_distribution": step_distribution(step_ms),
             "serving": serving,
             "membranes": membranes,
             "paper_algorithms": paper,

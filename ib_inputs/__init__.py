@@ -110,6 +110,29 @@ def shear_field_mac(N: int, L: float, gamma: float, dtype=np.float32) -> np.ndar
     return u.astype(dtype)
 
 
+def uniform_array(seed: int, shape, lo: float = -1.0, hi: float = 1.0, dtype=np.float32,
+                  purpose: str = "G") -> np.ndarray:
+    """Uniform [lo, hi) array of the given shape, generated in FP64 and rounded once to dtype
+    (a cheaper stand-in for normal_array on very large inputs)."""
+    count = int(np.prod(shape))
+    return (lo + (hi - lo) * uniform(stream_key(seed, purpose), count)).reshape(shape).astype(dtype)
+
+
+def wave_field(N: int, ncomp: int = 3, dtype=np.float32) -> np.ndarray:
+    """A deterministic grid field [ncomp][N][N][N] of plane waves up to the Nyquist range:
+    u_a = sin(2 pi (k_a x + l_a y + m_a z) / N + phase_a) over node indices, with wavenumbers
+    that make neighbouring nodes differ strongly (for interpolation checks on grids too
+    large for a random field to be generated quickly)."""
+    waves = [(3, 251, 17, 0.3), (199, 5, 101, 1.1), (61, 127, 233, 2.0), (255, 64, 7, 0.7)]
+    i = np.arange(N, dtype=np.float64) * (2.0 * np.pi / N)
+    out = np.empty((ncomp, N, N, N), dtype=dtype)
+    for a in range(ncomp):
+        k, l, m, ph = waves[a % len(waves)]
+        for z in range(N):
+            out[a, z] = np.sin(k * i[None, :] + l * i[:, None] + (m * i[z] + ph))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Red-blood-cell membranes (Section 4.2, Omori reference shape)
 # ---------------------------------------------------------------------------

@@ -300,31 +300,44 @@ def cpu_oracle_parallel(N: int, seed: int, npts: int):
     return npts / dt, dt, procs
 
 
-def serving_bench(device, njobs: int, loads, seed: int = 1):
+def serving_bench(device, njobs: int, loads, seed: int = 1, world: int = 1, rank: int = 0):
     """Served batch: independent spread + interpolate jobs, N in {32, 64, 96, 128}, n log-uniform in
     [1e3, 1e5], half uniform / half on RBC shells.  The one-job-per-launch loop is first run back to
     back to measure its capacity, and the continuous-batching server likewise; then Poisson arrivals
     at each offered load (a multiple of the loop's capacity) are served by the server and by the
-    loop.  Latency = completion - arrival."""
+    loop.  Latency = completion - arrival.  Under torchrun the jobs are sharded over the ranks
+    (serve.place_jobs, no data-path collective): each rank serves its own share, the capacities
+    count every rank's jobs over the slowest rank's wall time, and the latencies are rank 0's."""
     import ib_inputs
     import torch
     from paper_2012_06646_gb300 import serve
-    specs = ib_inputs.job_mix(seed, njobs)
-    warm = serve.make_requests(specs[: min(16, njobs)])
+    all_specs = ib_inputs.job_mix(seed, njobs)
+    owner = serve.place_jobs([sp.npts + sp.N ** 3 for sp in all_specs], world)
+    specs = [sp for sp, o in zip(all_specs, owner) if o == rank]
+    share = len(specs)
+    warm = serve.make_requests(specs[: min(16, share)])
     serve.single_job_loop(warm, realtime=False, device=device)
     srv = serve.Server(nstreams=3, max_jobs=64, max_points=1 << 22, max_cells=1 << 25, device=device)
-    srv.serve(serve.make_requests(specs[: min(16, njobs)]), realtime=False)
+    srv.serve(serve.make_requests(specs[: min(16, share)]), realtime=False)
     reqs = serve.make_requests(specs)
     cap_loop = serve.single_job_loop(reqs, realtime=False, device=device)
     loop_U = [r.U.clone() for r in reqs]
     cap_srv = srv.serve(reqs, realtime=False)
     same = all(torch.equal(a, r.U) for a, r in zip(loop_U, reqs))
-    cap = cap_loop.jobs / cap_loop.wall_s
-    out = {"jobs": njobs, "points": int(sum(sp.npts for sp in specs)),
-           "capacity_jobs_per_s": {"single_job_loop": cap, "batched": cap_srv.jobs / cap_srv.wall_s},
+    cap = cap_loop.jobs / cap_loop.wall_s           # this rank's loop capacity (sets its offered loads)
+    wall_loop = max_over_ranks(cap_loop.wall_s, device)
+    wall_srv = max_over_ranks(cap_srv.wall_s, device)
+    same = max_over_ranks(0.0 if same else 1.0, device) == 0.0
+    out = {"jobs": njobs, "points": int(sum(sp.npts for sp in all_specs)),
+           "capacity_jobs_per_s": {"single_job_loop": njobs / wall_loop, "batched": njobs / wall_srv},
            "results_identical_alone_and_in_mix": bool(same), "loads": []}
+    if world > 1:
+        out["sharding"] = {"ranks": world, "placement": "longest job first onto the least-loaded rank "
+                                                       "(cost = points + grid cells); no data-path collective",
+                           "jobs_rank0": share, "latencies": "rank 0's share, offered at the load times "
+                                                               "rank 0's own loop capacity"}
     for load in loads:
-        arrivals = ib_inputs.poisson_arrivals(seed, njobs, load * cap)
+        arrivals = ib_inputs.poisson_arrivals(seed, share, load * cap)
         for r, t in zip(reqs, arrivals):
             r.arrival, r.t_done = float(t), -1.0
         st_b = srv.serve(reqs)
@@ -904,6 +917,14 @@ def run_ours(args):
         except Exception as exc:
             ibstep = {"error": repr(exc)}
 
+    serving = None
+    if args.serve_jobs > 0:
+        try:
+            serving = serving_bench(device, args.serve_jobs, [float(x) for x in args.serve_loads.split(",")],
+                                    world=world, rank=rank)
+        except Exception as exc:
+            serving = {"error": repr(exc)}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -941,12 +962,6 @@ def run_ours(args):
         except Exception as exc:
             cpu_all = {"value": None, "unit": "pts/s", "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
 
-    serving = None
-    if args.serve_jobs > 0:
-        try:
-            serving = serving_bench(device, args.serve_jobs, [float(x) for x in args.serve_loads.split(",")])
-        except Exception as exc:
-            serving = {"error": repr(exc)}
 
     launches_per_step = 5 + 2 + 1 + 1     # bin: count, 2 scan, scatter, stable; spread: tile boxes, combine;
     #                                        interp: tiles (+ invalid points); advect

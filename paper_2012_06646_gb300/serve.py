@@ -109,6 +109,24 @@ class WaveCaps:
     tiles: int
 
 
+def place_jobs(costs, world: int) -> list:
+    """Owner rank of each job when a batch of independent jobs is sharded over `world` GPUs
+    (no collective: each rank serves its own jobs).  Longest job first onto the rank with the
+    least work so far (ties: the lower rank), so the ranks' loads differ by at most one job's
+    cost; deterministic, so every rank computes the same placement.  costs: work per job (for
+    a spread + interpolate job, its points plus its grid cells)."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0] * world
+    owner = [0] * len(costs)
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        owner[i] = r
+        load[r] += costs[i]
+    return owner
+
+
 def never_fits(npts: int, cells: int, tiles: int, caps: WaveCaps) -> str:
     """Why a job can never join a wave of a slot with capacities `caps` ('' if it can)."""
     if npts > caps.points:

@@ -407,6 +407,7 @@ ib_status ib_plan_destroy(ib_plan p) {
 }
 
 ib_status ib_bin(ib_plan p, long long npts, const void* X, void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_bin");
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   return run_bin(p, npts, X, (cudaStream_t)stream);
@@ -414,6 +415,7 @@ ib_status ib_bin(ib_plan p, long long npts, const void* X, void* stream) {
 
 ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, void* f, unsigned flags,
                     void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_spread");
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
@@ -454,6 +456,7 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
 
 ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u, void* U, unsigned flags,
                          void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_interpolate");
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (npts > 0 && (!u || !U)) return IB_ERR_INVALID_ARG;
@@ -486,6 +489,7 @@ ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u
 
 ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* field, const void* v, double scale,
                       void* D, unsigned flags, void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_pos_grad");
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (npts > 0 && (!field || !v || !D)) return IB_ERR_INVALID_ARG;
@@ -514,6 +518,7 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
 
 ib_status ib_advect(ib_plan p, long long npts, const void* X, const void* U, double dt, void* Xout,
                     void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_advect");
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (p->desc.ncomp != p->desc.dim) return IB_ERR_INVALID_ARG;
@@ -532,6 +537,7 @@ ib_status ib_advect(ib_plan p, long long npts, const void* X, const void* U, dou
 
 ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* G, void* f, int algorithm, int beta,
                           void* buffer, void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_spread_paper");
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
@@ -715,6 +721,7 @@ ib_status ib_batch_destroy(ib_batch b) {
 }
 
 ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags, void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_batch_run");
   if (!b || njobs < 0 || (njobs > 0 && !jobs)) return IB_ERR_INVALID_ARG;
   if (njobs > b->desc.max_jobs) return IB_ERR_CAPACITY;
   if (flags != 0) return IB_ERR_INVALID_ARG;
@@ -771,6 +778,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
 }
 
 ib_status ib_batch_run_host(ib_batch b, int njobs, const ib_host_job* jobs, void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_batch_run_host");
   if (!b || njobs < 0 || (njobs > 0 && !jobs)) return IB_ERR_INVALID_ARG;
   if (!(b->desc.flags & IB_BATCH_HOST_IO) || !b->io) return IB_ERR_INVALID_ARG;
   if (njobs > b->desc.max_jobs) return IB_ERR_CAPACITY;

@@ -266,6 +266,7 @@ ib_status ib_stokes_create(const ib_plan_desc* desc, ib_stokes* out) {
 
 ib_status ib_stokes_solve(ib_stokes s, const void* f, const void* u_old, void* u, double rho_over_k, double mu,
                           void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_stokes_solve");
   if (!s || !f || !u) return IB_ERR_INVALID_ARG;
   if (!(rho_over_k >= 0.0) || !(mu >= 0.0) || !isfinite(rho_over_k) || !isfinite(mu) ||
       (rho_over_k == 0.0 && mu == 0.0))

@@ -3,10 +3,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "ib_common.cuh"
 
 namespace ibgb {
+
+// NVTX range over one C-ABI call: profilers attribute the kernels the call
+// enqueues to a range named after the entry point (ncu --nvtx-include
+// "ib_spread/").  Without a profiler attached the push and pop do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Tile side of the spreading boxes: 16 in 3-D when the box (side + 4)^3 of
 // every component and the staging records fit in shared memory, else 8; 32 in 2-D.

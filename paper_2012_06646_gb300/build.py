@@ -75,7 +75,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
     # cuFFT (the Stokes solve) is linked dynamically, found through the
     # toolkit's library directory when the loader path lacks it.
     cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
-    res = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcufft", "-Xlinker", f"-rpath={cudalib}"],
+    # Only the C ABI (ib_*) is exported (linker version script).
+    exports = os.path.join(CSRC, "libibgb.map")
+    res = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcufft", "-Xlinker", f"-rpath={cudalib}",
+                          "-Xlinker", f"--version-script={exports}"],
                          capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{res.stdout}\n{res.stderr}")

@@ -32,6 +32,19 @@ def test_every_declared_symbol_is_exported(abi):
     assert sorted(abi.SIGNATURES) == names
 
 
+def test_only_the_c_abi_is_exported(abi):
+    # The linker version script keeps the internal C++ functions (and the static CUDA
+    # runtime) local: the dynamic symbol table defines exactly the header's functions.
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--defined-only", abi.LIB_PATH], capture_output=True, text=True, check=True)
+    funcs = sorted(ln.split()[-1] for ln in out.stdout.splitlines() if len(ln.split()) == 3 and ln.split()[1] == "T")
+    assert funcs == header_functions()
+
+
 def _desc(abi, **kw):
     d = abi.ib_plan_desc()
     d.dim = kw.get("dim", 3)

@@ -215,3 +215,13 @@ def test_inputs_are_deterministic_and_stream_separated():
     assert abs(g.mean()) < 0.03 and abs(g.std() - 1.0) < 0.03
     assert len(ib_inputs.icosphere(4)) == 2562
     assert abs(ib_inputs.rbc_volume(3.91) - 94.4) < 0.2
+    # the cheap large-case generators: deterministic, in range, and not degenerate
+    u1 = ib_inputs.uniform_array(5, (30000, 3))
+    assert np.array_equal(u1, ib_inputs.uniform_array(5, (30000, 3)))
+    assert u1.dtype == np.float32 and u1.min() >= -1.0 and u1.max() < 1.0 and abs(float(u1.mean())) < 0.02
+    w = ib_inputs.wave_field(16)
+    assert w.shape == (3, 16, 16, 16) and w.dtype == np.float32 and np.abs(w).max() <= 1.0
+    assert np.array_equal(w, ib_inputs.wave_field(16))
+    assert np.abs(np.diff(w, axis=3)).mean() > 0.5           # neighbouring nodes differ strongly
+    k, l, m, ph = 3, 251, 17, 0.3                             # component 0 at node (x, y, z) = (1, 2, 3)
+    assert abs(float(w[0, 3, 2, 1]) - np.sin(2 * np.pi * (k * 1 + l * 2 + m * 3) / 16 + ph)) < 1e-6

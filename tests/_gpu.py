@@ -1,6 +1,6 @@
 """Helpers for the GPU parity tests: device transfer and the tolerance checks.
 
-Tolerances (stated by the spec accuracy target, FP32 path):
+Tolerances (the accuracy target of the FP32 path):
   spreading      per node   |f - f_ref| <= 1e-5 * fabs_k + floor, and f = 0 exactly where fabs_k = 0
   interpolation  per point  |U - U_ref| <= 1e-5 * Uabs_j + floor, and max |U - U_ref| <= 1e-5 max |U_ref|
 where fabs_k / Uabs_j are the oracle's sums of |contribution|.  `floor` is

@@ -280,7 +280,7 @@ def test_interpolates_linears_exactly(orc, mac, kernel):
 
 @pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_adjointness(orc, kernel):
-    """<S G, u>_h = h^d sum_k f_k u_k equals <G, S* u>_L = sum_j G_j U_j (spec: 1e-12)."""
+    """<S G, u>_h = h^d sum_k f_k u_k equals <G, S* u>_L = sum_j G_j U_j (target: 1e-12 relative)."""
     g = orc.Grid(dim=3, n=(12, 10, 8), L=(1.2, 1.0, 0.8), mac=True, kernel=kernel)
     X = ib_inputs.uniform_points(31, 500, g.L, 3, dtype=np.float64)
     G = ib_inputs.normal_array(32, (500, 3), dtype=np.float64)

@@ -48,6 +48,11 @@
  *     at a time.
  *   - Results are run-to-run bit-reproducible: every node sum is formed in
  *     a fixed order that does not depend on scheduling.
+ *   - The shared library exports exactly the functions declared here.  Each
+ *     compute call (ib_bin, ib_spread, ib_interpolate, ib_pos_grad,
+ *     ib_advect, ib_spread_paper, ib_batch_run, ib_batch_run_host,
+ *     ib_stokes_solve) pushes an NVTX range named after itself while it
+ *     enqueues its work, for profilers; it costs nothing without one.
  */
 #ifndef IB_H
 #define IB_H

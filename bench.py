@@ -138,6 +138,15 @@ def step_distribution(ms: list):
             "max": float(a.max()), "mean": float(a.mean()), "n": int(a.size)}
 
 
+def output_hash(*tensors) -> str:
+    """First 16 hex digits of a SHA-256 over the bytes of the given tensors (the step's outputs):
+    equal across runs of the same configuration, since every sum has a fixed order."""
+    h = hashlib.sha256()
+    for t in tensors:
+        h.update(t.detach().cpu().numpy().tobytes())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
     captured on the current kernel sources (else None)."""
@@ -777,6 +786,10 @@ def run_ours(args):
                 b.synchronize()
                 step_ms.append(a.elapsed_time(b))
         torch.cuda.synchronize()
+        try:                                         # outputs of the last timed step, outside the timing
+            out_hash = {"f_and_U": output_hash(f, U), "after_steps": nsteps}
+        except Exception as exc:
+            out_hash = {"error": repr(exc)}
         # nvidia-smi samples every 50 ms: a timed region shorter than that is
         # sampled over a window extended by untimed repeats of the same step.
         while time.time() - t_begin < args.clock_window:
@@ -979,6 +992,8 @@ def run_ours(args):
             "step_ms_as_separate_calls": statistics.mean(plain_ms) if plain_ms else None,
             "step_as_cuda_graph": bool(graphs),
             "step_ms_distribution": step_distribution(step_ms),
+            "calls_ms_distribution": {k: step_distribution(v) for k, v in per_call.items()},
+            "output_sha256_16": out_hash,
             "serving": serving,
             "membranes": membranes,
             "paper_algorithms": paper,

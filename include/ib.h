@@ -125,6 +125,8 @@ enum { IB_F32 = 0, IB_F64 = 1 };
                                   ib_spread computes sum_j W_kj G_j (no h^-d), the adjoint of interpolation;
                                   ib_interpolate computes h^-d sum_k W_kj u_k, the adjoint of spreading
                                   (W_kj = prod_b phi(t_b - r_b); Eqs. matrix-interp, matrix-spread: S* = S^T) */
+#define IB_SPREAD_GRAD  0x10u  /* ib_pos_grad: differentiate the weights of spreading, which carry h^-d
+                                  (Eq. disc-spread): the library multiplies `scale` by h^-d = prod_b N_b/L_b */
 
 typedef struct ib_plan_s* ib_plan;
 
@@ -198,11 +200,13 @@ ib_status ib_interpolate(ib_plan plan, long long npts, const void* X, const void
 
 /* Position derivative of the interpolation weights, contracted with a field
  * and a per-point vector (derived from Eqs. disc-interp and disc-spread):
- *   D_{j,b} = scale * sum_a v_{j,a} sum_t field_a[i+t] d/dX_b[prod_c phi(t_c - r_c)].
- * With field = u, v = dLoss/dU and scale = 1 this is dLoss/dX of
- * interpolation; with field = dLoss/df, v = G and scale = h^-d it is dLoss/dX
- * of spreading.  X (npts, dim), field [ncomp][grid], v (npts, ncomp) read;
- * D (npts, dim) written.  Bins X first unless IB_REUSE_BINS. */
+ *   D_{j,b} = s * sum_a v_{j,a} sum_t field_a[i+t] d/dX_b[prod_c phi(t_c - r_c)],
+ * s = scale, or scale * h^-d with IB_SPREAD_GRAD.  With field = u, v = dLoss/dU,
+ * scale = 1 and no flag this is dLoss/dX of interpolation; with field =
+ * dLoss/df, v = G, scale = 1 and IB_SPREAD_GRAD it is dLoss/dX of spreading
+ * (the library applies h^-d).  X (npts, dim), field [ncomp][grid], v (npts,
+ * ncomp) read; D (npts, dim) written.  Flags: IB_REUSE_BINS, IB_SPREAD_GRAD;
+ * any other bit is IB_ERR_INVALID_ARG.  Bins X first unless IB_REUSE_BINS. */
 ib_status ib_pos_grad(ib_plan plan, long long npts, const void* X, const void* field, const void* v,
                       double scale, void* D, unsigned flags, void* stream);
 
@@ -337,19 +341,23 @@ ib_status ib_batch_check(ib_batch batch, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Interpolation for callers that cannot allocate device memory.  The paper
- * has no counterpart: it exists for callers that may not call cudaMalloc,
- * such as code running inside a CUDA graph being captured, a host callback,
- * or a process whose allocator is owned by someone else.  Same result as
- * ib_plan_create + ib_interpolate + ib_plan_destroy for the grid `desc`, but
- * the binning scratch is a fixed device array compiled into the library
- * (about 28 MB, held on every GPU that loads the library until the process
- * exits), so nothing is allocated or freed: no cudaMalloc, cudaFree or
- * allocating library routine runs.
- *   - desc: grid description as for ib_plan_create (max_points and flags are
- *     not used; flags must be 0).  X (npts, dim), u [ncomp][grid] read,
- *     U (npts, ncomp) written; device pointers owned by the caller.
- *   - Limits: n0 n1 n2 <= IB_NOALLOC_MAX_CELLS and npts <= IB_NOALLOC_MAX_POINTS,
- *     else IB_ERR_CAPACITY with nothing enqueued.
+ * has no counterpart.  Some callers must not call cudaMalloc: code whose
+ * device memory belongs to another allocator under a fixed budget (a
+ * framework's pool, a process sharing the GPU under a memory cap), where a
+ * new allocation can fail or fragment that budget, and latency-critical
+ * loops, where cudaMalloc and cudaFree can synchronise the whole device.
+ * This entry point gives the same result as ib_plan_create + ib_interpolate
+ * + ib_plan_destroy for the grid `desc`, but its binning scratch is a fixed
+ * device array compiled into the library (about 28 MB, held on every GPU that
+ * loads the library until the process exits), so nothing is allocated or
+ * freed: no cudaMalloc, cudaFree or allocating library routine runs.
+ *   - desc: grid description as for ib_plan_create; max_points is ignored,
+ *     and flags must be 0 (else IB_ERR_INVALID_ARG).  X (npts, dim),
+ *     u [ncomp][grid] read, U (npts, ncomp) written; device pointers owned by
+ *     the caller.
+ *   - Limits: n0 n1 n2 (n0 n1 in 2-D) <= IB_NOALLOC_MAX_CELLS and
+ *     npts <= IB_NOALLOC_MAX_POINTS, else IB_ERR_CAPACITY with nothing
+ *     enqueued.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and caches it; make that first call on each
  *     device before any stream capture.
@@ -357,8 +365,9 @@ ib_status ib_batch_check(ib_batch batch, void* stream);
  *     behind; each call clears what must start at zero.  Calls whose work
  *     overlaps on the GPU (different streams, or host threads) race on the
  *     array: order them on one stream.
- *   - Non-finite or out-of-range positions interpolate to NaN (no error word
- *     is read back).
+ *   - No error word is read back: non-finite or out-of-range positions
+ *     interpolate to NaN, and in a library built with IB_DEBUG_BOUNDS a
+ *     failed index check skips its access without being reported.
  * ------------------------------------------------------------------------- */
 #define IB_NOALLOC_MAX_CELLS (1ll << 21)
 #define IB_NOALLOC_MAX_POINTS (1ll << 20)

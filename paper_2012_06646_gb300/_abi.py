@@ -50,6 +50,7 @@ IB_ACCUMULATE = 0x1
 IB_COMPENSATED = 0x2
 IB_REUSE_BINS = 0x4
 IB_ADJOINT = 0x8
+IB_SPREAD_GRAD = 0x10
 
 IB_BATCH_HOST_IO = 0x1
 

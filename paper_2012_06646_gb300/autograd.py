@@ -5,7 +5,7 @@ spreading is f = h^-d W^T G and interpolation is U = W u (Eqs. disc-spread,
 disc-interp; S* = S^T, Eqs. matrix-interp and matrix-spread).  Hence
 
   spread:       dL/dG = h^-d W (dL/df)      -> ib_interpolate with IB_ADJOINT
-                dL/dX = h^-d D(dL/df, G)    -> ib_pos_grad, scale = h^-d
+                dL/dX = h^-d D(dL/df, G)    -> ib_pos_grad with IB_SPREAD_GRAD (h^-d applied in C)
   interpolate:  dL/du = W^T (dL/dU)         -> ib_spread with IB_ADJOINT
                 dL/dX = D(u, dL/dU)         -> ib_pos_grad, scale = 1
 
@@ -55,7 +55,7 @@ class SpreadFunction(torch.autograd.Function):
         if ctx.needs_input_grad[1]:
             gG = plan.interpolate(Xc, gf, reuse_bins=True, adjoint=True)
         if ctx.needs_input_grad[0]:
-            gX = plan.pos_grad(Xc, gf, G.detach().contiguous(), scale=plan.hmd, reuse_bins=True)
+            gX = plan.pos_grad(Xc, gf, G.detach().contiguous(), reuse_bins=True, spread=True)
         return gX, gG, None, None
 
 

@@ -493,8 +493,9 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (npts > 0 && (!field || !v || !D)) return IB_ERR_INVALID_ARG;
-  if (flags & ~IB_REUSE_BINS) return IB_ERR_INVALID_ARG;
+  if (flags & ~(IB_REUSE_BINS | IB_SPREAD_GRAD)) return IB_ERR_INVALID_ARG;
   if (!isfinite(scale)) return IB_ERR_INVALID_ARG;
+  if (flags & IB_SPREAD_GRAD) scale *= p->job.hmd;   // spreading's weights carry h^-d (Eq. disc-spread)
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare(p, npts, X, flags, s);
   if (st != IB_OK) return st;

@@ -200,14 +200,16 @@ class Plan:
               "ib_interpolate")
         return U
 
-    def pos_grad(self, X, field, v, scale: float = 1.0, D=None, reuse_bins=False, stream=None):
+    def pos_grad(self, X, field, v, scale: float = 1.0, D=None, reuse_bins=False, spread=False, stream=None):
+        """ib_pos_grad; spread=True differentiates spreading's weights (IB_SPREAD_GRAD:
+        the library multiplies scale by h^-d)."""
         n = self._points(X)
         self._check(field, self.grid_shape(), "field")
         self._check(v, (n, self.ncomp), "v")
         if D is None:
             D = self._new((n, self.dim))
         self._check(D, (n, self.dim), "D")
-        flags = _abi.IB_REUSE_BINS if reuse_bins else 0
+        flags = (_abi.IB_REUSE_BINS if reuse_bins else 0) | (_abi.IB_SPREAD_GRAD if spread else 0)
         if not reuse_bins:
             self.bin_epoch += 1
         check(self.lib.ib_pos_grad(self.handle, n, _ptr(X), _ptr(field), _ptr(v), float(scale), _ptr(D), flags,
@@ -244,14 +246,6 @@ class Plan:
         p = torch.as_tensor(_DeviceArray(perm.value, npts.value, "<i4"), device=self.device)
         s = torch.as_tensor(_DeviceArray(start.value, ncell.value + 2, "<i4"), device=self.device)
         return p.to(torch.int64), s.to(torch.int64)
-
-    @property
-    def hmd(self) -> float:
-        """h^-d of the plan's grid (product of N_b / L_b)."""
-        v = 1.0
-        for b in range(self.dim):
-            v *= self.n[b] / self.L[b]
-        return v
 
     def close(self):
         if getattr(self, "handle", None):

@@ -250,6 +250,10 @@ def test_pos_grad_matches_oracle(P, orc):
     D = host(plan.pos_grad(dev(X), dev(field), dev(v), scale=2.5))
     D_ref, Dabs = orc.pos_grad(g, X, field, v)
     assert_interp_close(D, 2.5 * D_ref, 2.5 * Dabs, rel=2e-5, what="pos_grad")
+    # IB_SPREAD_GRAD: the library applies spreading's h^-d to the same sum
+    hmd = orc.inv_cell_volume(g)
+    Ds = host(plan.pos_grad(dev(X), dev(field), dev(v), scale=2.5, reuse_bins=True, spread=True))
+    assert_interp_close(Ds, 2.5 * hmd * D_ref, 2.5 * hmd * Dabs, rel=2e-5, what="pos_grad (spread)")
 
 
 def test_advect_wraps(P):

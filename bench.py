@@ -60,8 +60,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=100_000)
     ap.add_argument("--clock-window", type=float, default=1.0,
                     help="seconds of clock sampling from the start of the timed steps")
-    ap.add_argument("--serve-jobs", type=int, default=384, help="jobs of the served-batch measurement (0: skip)")
-    ap.add_argument("--serve-loads", default="0.9,2.0",
+    ap.add_argument("--serve-jobs", type=int, default=4096, help="jobs of the served-batch measurement (0: skip)")
+    ap.add_argument("--serve-loads", default="0.5,0.9,1.5",
                     help="offered loads as multiples of the one-job loop's capacity, comma separated")
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step as separate calls instead of one CUDA graph replay")
@@ -450,56 +450,126 @@ def touched_nodes_mac(X: np.ndarray, N: int) -> int:
     return total
 
 
-def membrane_bench(device, stream, reps: int, peak: float, seed: int = 0, N: int = 128):
-    """The clustered-membrane workload: randomly oriented, non-overlapping red cells
-    (2562 points each) packed into the 128^3 MAC box, smooth membrane forces.
+FLOOR32 = 64 * 1.1754943508222875e-38      # 64 FLT_MIN: contributions below the FP32 normal range
+
+
+def error_vs_oracle(got, ref, absref, floor: float = FLOOR32) -> dict:
+    """Worst relative error of a GPU result against the FP64 oracle, in the tests'
+    measure: |got - ref| / (sum |terms| + floor) per node or point (the sum of
+    |terms| is the oracle's sum of |contribution|), with the tolerance it must meet."""
+    got = np.asarray(got, dtype=np.float64)
+    err = np.abs(got - ref)
+    rel = err / (absref + floor)
+    return {"max_rel_err": float(rel.max()) if rel.size else 0.0,
+            "mean_rel_err": float(rel.mean()) if rel.size else 0.0,
+            "sum_abs_err": float(err.sum()), "count": int(rel.size), "tolerance": 1e-5,
+            "within_tolerance": bool(np.all(err <= 1e-5 * absref + floor))}
+
+
+def membrane_bench(device, stream, reps: int, peak: float, seed: int = 0, N: int = 128, oracle_check: bool = True):
+    """The clustered-membrane workload: 17 randomly oriented, non-overlapping red
+    cells compressed to about 40 % volume fraction in the 128^3 MAC box, with
+    2562 points per cell and with the paper's 8832, smooth membrane forces.
     Times binning + spreading (TwoSum node sums, and plain) and interpolation,
-    CUDA events on the stream, L2 flushed before each timed call."""
+    CUDA events on the stream, L2 flushed before each timed call; then (outside
+    the timing) states the error of each result against the FP64 oracle."""
     import torch
     import ib_inputs
     from paper_2012_06646_gb300.plan import Plan
-    mem = ib_inputs.pack_membranes(seed)
-    X = torch.from_numpy(mem.X).to(device)
-    G = torch.from_numpy(ib_inputs.membrane_forces(seed, mem)).to(device)
-    u = torch.from_numpy(ib_inputs.normal_array(seed + 1, (3, N, N, N))).to(device)
-    n = X.shape[0]
-    plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", max_points=n, compensated=True, device=device)
-    f = torch.empty(plan.grid_shape(), dtype=torch.float32, device=device)
-    U = torch.empty((n, 3), dtype=torch.float32, device=device)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    calls = {
-        "bin_and_spread_compensated": lambda: plan.spread(X, G, f=f, compensated=True, stream=stream),
-        "bin_and_spread": lambda: plan.spread(X, G, f=f, stream=stream),
-        "interp": lambda: plan.interpolate(X, u, U=U, reuse_bins=True, stream=stream),
-    }
-    ms = {}
-    with torch.cuda.stream(stream):
-        for name, call in calls.items():
-            call()
-            t = []
-            for r in range(reps):
-                flush.fill_(r & 0xFF)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
+    out = {}
+    for label, per_cell in (("rbc2562", None), ("rbc8832", 8832)):
+        mem = ib_inputs.pack_membranes(seed, points_per_cell=per_cell)
+        Gh = ib_inputs.membrane_forces(seed, mem)
+        uh = ib_inputs.normal_array(seed + 1, (3, N, N, N))
+        X = torch.from_numpy(mem.X).to(device)
+        G = torch.from_numpy(Gh).to(device)
+        u = torch.from_numpy(uh).to(device)
+        n = X.shape[0]
+        plan = Plan(3, (N, N, N), (1.0, 1.0, 1.0), grid="mac", max_points=n, compensated=True, device=device)
+        f = torch.empty(plan.grid_shape(), dtype=torch.float32, device=device)
+        U = torch.empty((n, 3), dtype=torch.float32, device=device)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+        calls = {
+            "bin_and_spread_compensated": lambda: plan.spread(X, G, f=f, compensated=True, stream=stream),
+            "bin_and_spread": lambda: plan.spread(X, G, f=f, stream=stream),
+            "interp": lambda: plan.interpolate(X, u, U=U, reuse_bins=True, stream=stream),
+        }
+        ms = {}
+        with torch.cuda.stream(stream):
+            for name, call in calls.items():
                 call()
-                b.record(stream)
-                b.synchronize()
-                t.append(a.elapsed_time(b))
-            ms[name] = statistics.mean(t)
-    plan.check(stream)
-    pair = ms["bin_and_spread_compensated"] + ms["interp"]
-    grid_bytes = 2 * (n * 24 + 3 * N ** 3 * 4)
-    touched = touched_nodes_mac(mem.X, N)
-    touched_bytes = 2 * (n * 24 + touched * 4)
-    return {"workload": f"{len(mem.centres)} red cells x 2562 points ({n} points, volume fraction "
-                        f"{mem.volume_fraction:.3f}), {N}^3 MAC grid, FP32, TwoSum node sums in spreading",
-            "calls_ms": ms, "pts_per_s": n / (pair / 1e3),
-            "roofline_full_grid": {"achieved_gbs": grid_bytes / (pair / 1e3) / 1e9, "peak": peak,
-                                   "frac": grid_bytes / (pair / 1e3) / 1e9 / peak, "bytes": grid_bytes},
-            "roofline_touched_nodes": {"achieved_gbs": touched_bytes / (pair / 1e3) / 1e9, "peak": peak,
-                                       "frac": touched_bytes / (pair / 1e3) / 1e9 / peak, "bytes": touched_bytes,
-                                       "touched_nodes": touched},
-            "note": "spread + interpolate pair (compensated spread, binning included)"}
+                t = []
+                for r in range(reps):
+                    flush.fill_(r & 0xFF)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    call()
+                    b.record(stream)
+                    b.synchronize()
+                    t.append(a.elapsed_time(b))
+                ms[name] = statistics.mean(t)
+        plan.check(stream)
+        pair = ms["bin_and_spread_compensated"] + ms["interp"]
+        grid_bytes = 2 * (n * 24 + 3 * N ** 3 * 4)
+        touched = touched_nodes_mac(mem.X, N)
+        touched_bytes = 2 * (n * 24 + touched * 4)
+        res = {"workload": f"{len(mem.centres)} red cells x {n // max(1, len(mem.centres))} points ({n} points, "
+                           f"volume fraction {mem.volume_fraction:.3f}), {N}^3 MAC grid, FP32, TwoSum node sums "
+                           "in spreading",
+               "calls_ms": ms, "pts_per_s": n / (pair / 1e3),
+               "roofline_full_grid": {"achieved_gbs": grid_bytes / (pair / 1e3) / 1e9, "peak": peak,
+                                      "frac": grid_bytes / (pair / 1e3) / 1e9 / peak, "bytes": grid_bytes},
+               "roofline_touched_nodes": {"achieved_gbs": touched_bytes / (pair / 1e3) / 1e9, "peak": peak,
+                                          "frac": touched_bytes / (pair / 1e3) / 1e9 / peak, "bytes": touched_bytes,
+                                          "touched_nodes": touched},
+               "note": "spread + interpolate pair (compensated spread, binning included)"}
+        if oracle_check:
+            import oracle
+            oracle.build()
+            with torch.cuda.stream(stream):
+                fc = plan.spread(X, G, compensated=True, stream=stream).cpu().numpy()
+                fp = plan.spread(X, G, reuse_bins=True, stream=stream).cpu().numpy()
+                Ug = plan.interpolate(X, u, reuse_bins=True, stream=stream).cpu().numpy()
+            g = oracle.Grid(dim=3, n=(N, N, N), L=(1.0, 1.0, 1.0), mac=True)
+            f_ref, fabs = oracle.spread(g, mem.X, Gh)
+            U_ref, Uabs = oracle.interp(g, mem.X, uh)
+            ec, ep = error_vs_oracle(fc, f_ref, fabs), error_vs_oracle(fp, f_ref, fabs)
+            res["error_vs_fp64_oracle"] = {
+                "spread_compensated": ec, "spread_plain": ep, "interp": error_vs_oracle(Ug, U_ref, Uabs),
+                "compensated_over_plain_sum_abs_err": ec["sum_abs_err"] / ep["sum_abs_err"] if ep["sum_abs_err"] else None,
+                "measure": "per node |f - f_ref| / (sum |terms| + 64 FLT_MIN), per point likewise; every node and point"}
+        out[label] = res
+    return out
+
+
+def accuracy_uniform(plan, X, G, u, N: int, stream, seed: int = 0, sample: int = 20_000, box: int = 24) -> dict:
+    """Error of the headline workload's spreading and interpolation against the FP64
+    oracle, outside the timing.  Interpolation: a sample of points, each against
+    the oracle's own sum.  Spreading: the nodes of an interior sub-box of box^3
+    cells, against the oracle's spread of every point whose support reaches
+    them (points with floor(X N) within 3 cells of the sub-box), which gives
+    those nodes their complete sums."""
+    import torch
+    import oracle
+    oracle.build()
+    with torch.cuda.stream(stream):
+        f = plan.spread(X, G, stream=stream).cpu().numpy()
+        U = plan.interpolate(X, u, reuse_bins=True, stream=stream).cpu().numpy()
+    Xh = X.cpu().numpy()
+    Gh = G.cpu().numpy()
+    uh = u.cpu().numpy()
+    g = oracle.Grid(dim=3, n=(N, N, N), L=(1.0, 1.0, 1.0), mac=True)
+    pick = np.linspace(0, len(Xh) - 1, min(sample, len(Xh))).astype(np.int64)
+    U_ref, Uabs = oracle.interp(g, Xh[pick], uh)
+    c0 = N // 3
+    cells = np.floor(Xh.astype(np.float64) * N).astype(np.int64)
+    sel = np.all((cells >= c0 - 3) & (cells <= c0 + box + 2), axis=1)
+    f_ref, fabs = oracle.spread(g, Xh[sel], Gh[sel])
+    w = np.s_[:, c0:c0 + box, c0:c0 + box, c0:c0 + box]
+    return {"spread": dict(error_vs_oracle(f[w], f_ref[w], fabs[w]),
+                           nodes=f"{box}^3 interior nodes x 3 components from {int(sel.sum())} points"),
+            "interp": dict(error_vs_oracle(U[pick], U_ref, Uabs), points=f"{len(pick)} evenly spaced points"),
+            "measure": "per node |f - f_ref| / (sum |terms| + 64 FLT_MIN), per point likewise"}
 
 
 def kernels_bench(device, stream, X, G, u, reps: int, N: int, peak: float, oracle_sample: int = 0):
@@ -895,7 +965,8 @@ def run_ours(args):
     membranes = None
     if args.membrane_reps > 0 and rank == 0:
         try:
-            membranes = membrane_bench(device, stream, args.membrane_reps, load_peaks()[0])
+            membranes = membrane_bench(device, stream, args.membrane_reps, load_peaks()[0],
+                                       oracle_check=not args.no_cpu_baseline)
         except Exception as exc:
             membranes = {"error": repr(exc)}
 
@@ -938,6 +1009,13 @@ def run_ours(args):
         except Exception as exc:
             serving = {"error": repr(exc)}
 
+    accuracy = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            accuracy = accuracy_uniform(plan, X, Gs[0], ud, N, stream, args.seed)
+        except Exception as exc:
+            accuracy = {"error": repr(exc)}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -976,7 +1054,7 @@ def run_ours(args):
             cpu_all = {"value": None, "unit": "pts/s", "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
 
 
-    launches_per_step = 5 + 2 + 1 + 1     # bin: count, 2 scan, scatter, stable; spread: tile boxes, combine;
+    launches_per_step = 4 + 2 + 1 + 1     # bin: count, scan, scatter, stable; spread: tile boxes, combine;
     #                                        interp: tiles (+ invalid points); advect
     line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -994,6 +1072,7 @@ def run_ours(args):
             "step_ms_distribution": step_distribution(step_ms),
             "calls_ms_distribution": {k: step_distribution(v) for k, v in per_call.items()},
             "output_sha256_16": out_hash,
+            "error_vs_fp64_oracle": accuracy,
             "serving": serving,
             "membranes": membranes,
             "paper_algorithms": paper,

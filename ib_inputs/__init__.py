@@ -234,49 +234,127 @@ class Membranes:
     attempts: int
 
 
-def pack_membranes(seed: int, L: float = 1.0, target_cells: int = 17, subdivisions: int = 4,
-                   max_attempts: int = 20000, gap: float = 0.02, dtype=np.float32) -> Membranes:
-    """Random sequential addition of non-overlapping, randomly oriented RBCs in a periodic box.
+@functools.lru_cache(maxsize=8)
+def fibonacci_sphere(n: int) -> np.ndarray:
+    """n nearly uniform points on the unit sphere (golden-angle spiral), for point counts
+    that are not icosphere counts (the paper's 8832 data sites per cell)."""
+    k = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * k / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = np.pi * (3.0 - math.sqrt(5.0)) * k
+    out = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    out.setflags(write=False)
+    return out
 
-    The box side L stands for the paper's 16 um, so R0 = 3.91/16 L.  A
-    candidate is rejected when any of its surface points (inflated by
-    `gap` R0) lies inside an accepted cell or vice versa, over periodic
-    images.  Placement stops at `target_cells` or after `max_attempts`;
-    the achieved volume fraction is returned with the points.
+
+def rbc_points(R0: float, sphere: np.ndarray) -> np.ndarray:
+    """Omori RBC surface points (body frame) from unit-sphere points by (theta, phi) = (atan2(y,x), asin z)."""
+    theta = np.arctan2(sphere[:, 1], sphere[:, 0])
+    phi = np.arcsin(np.clip(sphere[:, 2], -1.0, 1.0))
+    cphi = np.cos(phi)
+    return np.stack([R0 * np.cos(theta) * cphi, R0 * np.sin(theta) * cphi,
+                     R0 * _omori_p(cphi) * np.sin(phi)], axis=1)
+
+
+def _small_rotation(u: np.ndarray, angle: float) -> np.ndarray:
+    """Rotation by `angle` * u[3] about the axis of (u[0], u[1], u[2]) - 1/2 (Rodrigues)."""
+    axis = u[:3] - 0.5
+    nrm = np.linalg.norm(axis)
+    axis = axis / nrm if nrm > 1e-12 else np.array([0.0, 0.0, 1.0])
+    t = angle * (2.0 * u[3] - 1.0)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(t) * K + (1.0 - math.cos(t)) * (K @ K)
+
+
+def pack_membranes(seed: int, L: float = 1.0, target_cells: int = 17, subdivisions: int = 4,
+                   max_attempts: int = 20000, gap: float = 0.02, dtype=np.float32,
+                   points_per_cell: int | None = None, max_sweeps: int = 600) -> Membranes:
+    """Non-overlapping, randomly oriented RBCs in a periodic box, packed by compression.
+
+    The box side L stands for the paper's 16 um, so R0 = 3.91/16 L.  Two cells
+    overlap when a probe point of one (its surface inflated by `gap` R0) lies
+    inside the other, over the nearest periodic image.  The cells are first
+    placed by random sequential addition at a reduced size s R0 (s = 0.6),
+    where `target_cells` of them fit easily, with uniform random orientations
+    (Shoemake quaternions); then they are compressed: sweeps of Monte Carlo
+    moves (a small random translation and rotation of each cell in turn,
+    kept when it overlaps nothing) alternate with growing s to the largest
+    overlap-free value, until s = 1 or `max_sweeps` sweeps.  A packing that
+    cannot reach full size keeps the cells placed so far at s = 1 that do not
+    overlap (dropping the others).  Every random number comes from the
+    counter-based streams of this module, so the packing depends on `seed`
+    only.  The surface points are the subdivision-`subdivisions` icosphere
+    (2562 points for 4), or `points_per_cell` golden-spiral points, mapped
+    onto the Omori shape; the achieved volume fraction is returned.
     """
     R0 = RBC_R0_UM / BOX_UM * L
-    surf = rbc_surface(R0, subdivisions)
-    probe = rbc_surface(R0 * (1.0 + gap), 3)
+    sphere = fibonacci_sphere(points_per_cell) if points_per_cell else icosphere(subdivisions)
+    surf = rbc_points(R0, sphere)
+    unit_probe = rbc_points(1.0, icosphere(3)) * (1.0 + gap)       # R0 = 1, inflated
     kc = stream_key(seed, "rbc-centre")
     kr = stream_key(seed, "rbc-rotation")
+    km = stream_key(seed, "rbc-move")
+
+    def near(d, sc):
+        return np.linalg.norm(d) <= 2.0 * sc * R0 * (1.0 + gap)
+
+    def overlap(c1, R1, c2, R2, sc):
+        d = c1 - c2
+        d -= L * np.round(d / L)
+        if not near(d, sc):
+            return False
+        p1 = unit_probe * (sc * R0)
+        if rbc_inside((p1 @ R1.T + d) @ R2, sc * R0).any():
+            return True
+        return bool(rbc_inside((p1 @ R2.T - d) @ R1, sc * R0).any())
+
+    def free(i, c, R, cen, rot, sc):
+        return not any(overlap(c, R, cen[j], rot[j], sc) for j in range(len(cen)) if j != i)
+
+    # 1. random sequential addition at the reduced size
+    s = 0.6
     centres, rots = [], []
     attempts = 0
-    images = np.array([[i, j, k] for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)],
-                      dtype=np.float64) * L
     while len(centres) < target_cells and attempts < max_attempts:
         c = uniform(kc, 3, offset=3 * attempts) * L
         R = random_rotation(kr, attempts)
         attempts += 1
-        ok = True
-        for c2, R2 in zip(centres, rots):
-            d = c - c2
-            d -= L * np.round(d / L)
-            if np.linalg.norm(d) > 2.0 * R0 * (1.0 + gap):
-                continue
-            for img in images:
-                cc = c2 + d + img  # candidate centre seen from cell 2 (nearest images only)
-                if np.linalg.norm(cc - c2) > 2.0 * R0 * (1.0 + gap):
-                    continue
-                p_in_2 = (probe @ R.T + cc - c2) @ R2          # candidate probe -> body frame of cell 2
-                p2_in_c = (probe @ R2.T + c2 - cc) @ R         # cell-2 probe -> candidate body frame
-                if rbc_inside(p_in_2, R0).any() or rbc_inside(p2_in_c, R0).any():
-                    ok = False
-                    break
-            if not ok:
-                break
-        if ok:
+        if free(-1, c, R, centres, rots, s):
             centres.append(c)
             rots.append(R)
+    # 2. compression: Monte Carlo sweeps, then the largest overlap-free size
+    move = 0
+    sweeps = 0
+    step = 0.08
+    while s < 1.0 and sweeps < max_sweeps and centres:
+        for i in range(len(centres)):
+            u = uniform(km, 7, offset=7 * move)
+            move += 1
+            c = centres[i] + (u[:3] - 0.5) * (2.0 * step * s * R0)
+            c -= L * np.floor(c / L)
+            R = _small_rotation(u[3:], 2.0 * step) @ rots[i]
+            if free(i, c, R, centres, rots, s):
+                centres[i], rots[i] = c, R
+        sweeps += 1
+        lo, hi = s, min(1.0, s * 1.03)
+        for _ in range(5):
+            mid = hi if _ == 0 else 0.5 * (lo + hi)
+            ok = all(not overlap(centres[i], rots[i], centres[j], rots[j], mid)
+                     for i in range(len(centres)) for j in range(i + 1, len(centres)))
+            if ok:
+                lo = mid
+                if _ == 0:
+                    break
+            else:
+                hi = mid
+        s = lo
+    if s < 1.0:   # not compressed to full size: keep the cells that fit at s = 1
+        kept_c, kept_r = [], []
+        for c, R in zip(centres, rots):
+            if free(-1, c, R, kept_c, kept_r, 1.0):
+                kept_c.append(c)
+                kept_r.append(R)
+        centres, rots = kept_c, kept_r
     pts, owner, offs = [], [], []
     for ci, (c, R) in enumerate(zip(centres, rots)):
         off = surf @ R.T
@@ -290,7 +368,7 @@ def pack_membranes(seed: int, L: float = 1.0, target_cells: int = 17, subdivisio
     return Membranes(X=X, cell_of_point=np.concatenate(owner) if owner else np.zeros(0, np.int64),
                      centres=np.array(centres).reshape(-1, 3), rotations=np.array(rots).reshape(-1, 3, 3),
                      offsets=np.concatenate(offs) if offs else np.zeros((0, 3)), R0=R0,
-                     volume_fraction=vf, attempts=attempts)
+                     volume_fraction=vf, attempts=attempts + sweeps)
 
 
 def membrane_forces(seed: int, mem: Membranes, dtype=np.float32) -> np.ndarray:

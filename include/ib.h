@@ -68,7 +68,9 @@ typedef enum {
   IB_ERR_INVALID_ARG = 1,     /* bad descriptor, null pointer, unsupported combination */
   IB_ERR_OOM = 2,             /* device or pinned host allocation failed */
   IB_ERR_CUDA = 3,            /* a CUDA runtime call failed (launch or copy) */
-  IB_ERR_TIMEOUT = 4,         /* reserved for a bounded device-side wait; no entry point waits on the device */
+  IB_ERR_TIMEOUT = 4,         /* a bounded device-side wait ran out (the binning scan's look-back, see
+                                 ib_selftest_bounded_wait): that call's bins are wrong; reported by
+                                 ib_plan_check / ib_batch_check */
   IB_ERR_CAPACITY = 5,        /* npts (or a batch wave) exceeds the capacity given at creation */
   IB_ERR_NOT_IMPLEMENTED = 6,
   IB_ERR_NONFINITE = 7,       /* a position was NaN or infinite (reported by ib_plan_check) */
@@ -413,6 +415,20 @@ ib_status ib_stokes_solve(ib_stokes solver, const void* f, const void* u_old, vo
 
 /* Synchronises the device, releases the plans and scratch; NULL is a no-op. */
 ib_status ib_stokes_destroy(ib_stokes solver);
+
+/* Self-test of the bounded device-side waits.  The binning scan (an exclusive
+ * prefix of the per-cell counts in one pass with decoupled look-back: each
+ * block waits for the chunk totals before its own) polls every wait a
+ * bounded number of times; a wait that runs out records IB_ERR_TIMEOUT in
+ * the error word and the kernel goes on to its end, so the device stays
+ * usable.  This call runs that wait once against a chunk state that nothing
+ * publishes, with a short limit (about 100 microseconds of polling), on
+ * `stream`, and returns what the error word reports: IB_ERR_TIMEOUT when the
+ * wait ran out and the kernel ended, as designed; IB_OK if it did not run
+ * out; IB_ERR_OOM or IB_ERR_CUDA if the test could not run.  Uses its own
+ * small stream-ordered scratch (cudaMallocAsync / cudaFreeAsync) and
+ * synchronises `stream`.  Paper counterpart: none. */
+ib_status ib_selftest_bounded_wait(void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* ib_status_string(ib_status status);

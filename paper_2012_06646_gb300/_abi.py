@@ -120,6 +120,7 @@ SIGNATURES = {
     "ib_stokes_solve": (_st, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "ib_stokes_destroy": (_st, [_vp]),
     "ib_set_allocator": (_st, [ib_alloc_fn, ib_free_fn, _vp]),
+    "ib_selftest_bounded_wait": (_st, [_vp]),
     "ib_status_string": (ctypes.c_char_p, [_st]),
     "ib_version": (ctypes.c_char_p, []),
 }

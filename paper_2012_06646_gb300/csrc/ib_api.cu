@@ -155,7 +155,7 @@ bool valid_shape(int dim, int grid, int kernel, int dtype, int ncomp) {
 
 // Arena layout shared by plans and batches.
 struct Layout {
-  size_t count, key, rank, perm_tmp, perm, block_sums, err, tflags, boxes, table, io, total;
+  size_t count, scan, key, rank, perm_tmp, perm, err, tflags, boxes, table, io, total;
 };
 
 Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t table_bytes, size_t io_bytes = 0,
@@ -163,11 +163,11 @@ Layout make_layout(long long ncell, long long npts, size_t boxes_bytes, size_t t
   Layout L;
   size_t off = 0;
   L.count = off;      off += align_up(sizeof(uint32_t) * (size_t)(ncell + 2));
+  L.scan = off;       off += align_up(sizeof(unsigned long long) * (size_t)(scan_blocks(ncell + 1) + 1));
   L.key = off;        off += align_up(sizeof(uint32_t) * (size_t)npts);
   L.rank = off;       off += align_up(sizeof(uint32_t) * (size_t)npts);
   L.perm_tmp = off;   off += align_up(sizeof(uint2) * (size_t)npts);
   L.perm = off;       off += align_up(sizeof(uint32_t) * (size_t)npts);
-  L.block_sums = off; off += align_up(sizeof(uint32_t) * (size_t)(scan_blocks(ncell + 1) + 1));
   L.err = off;        off += align_up(sizeof(uint32_t));
   L.tflags = off;     off += align_up(sizeof(uint32_t) * (size_t)ntiles);
   L.boxes = off;      off += align_up(boxes_bytes);
@@ -184,7 +184,8 @@ Bins carve(char* base, const Layout& L) {
   B.rank = (uint32_t*)(base + L.rank);
   B.perm_tmp = (uint2*)(base + L.perm_tmp);
   B.perm = (uint32_t*)(base + L.perm);
-  B.block_sums = (uint32_t*)(base + L.block_sums);
+  B.scan = (unsigned long long*)(base + L.scan);
+  B.order = nullptr;
   B.err = (uint32_t*)(base + L.err);
   B.tflags = L.boxes > L.tflags ? (uint32_t*)(base + L.tflags) : nullptr;
   B.ncell_total = 0;
@@ -203,6 +204,7 @@ ib_status check_error_word(uint32_t* err_dev, cudaStream_t s) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
   }
   if (e & ERR_BOUNDS) return IB_ERR_BOUNDS;
+  if (e & ERR_TIMEOUT) return IB_ERR_TIMEOUT;
   if (e & ERR_NONFINITE) return IB_ERR_NONFINITE;
   if (e & ERR_RANGE) return IB_ERR_RANGE;
   if (e & ERR_STALE) return IB_ERR_BINS_STALE;
@@ -228,6 +230,7 @@ struct ib_plan_s {
   bool binned;
   const void* binned_X;
   long long binned_n;
+  long long perm_n;    // points of the last completed binning (perm is a permutation of them), or -1
 };
 
 struct ib_batch_s {
@@ -291,9 +294,12 @@ ib_status run_bin(ib_plan p, long long npts, const void* X, cudaStream_t s) {
   Bins B = p->bins;
   B.npts_total = npts;
   B.ncell_total = p->job.ncell;
-  if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(B.ncell_total + 2), s) != cudaSuccess)
-    return IB_ERR_CUDA;
+  // the previous bins of as many points give the processing order (nearly sorted)
+  B.order = (npts > 0 && p->perm_n == npts) ? B.perm : nullptr;
+  if (clear_bins(B, s) != cudaSuccess) return IB_ERR_CUDA;
+  p->perm_n = -1;
   if (launch_bin(J, p->sh, B, p->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
+  p->perm_n = npts;
   p->binned = true;
   p->binned_X = X;
   p->binned_n = npts;
@@ -326,6 +332,31 @@ Bins call_bins(ib_plan p, long long npts) {
 }  // namespace
 
 extern "C" {
+
+ib_status ib_selftest_bounded_wait(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t na = sizeof(uint32_t) * (size_t)(2 * ibgb::kScanChunkCells + 1);
+  const size_t bytes = 256 + 256 + na;
+  void* buf = nullptr;
+  if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return IB_ERR_OOM;
+  }
+  char* b = (char*)buf;
+  unsigned long long* state = (unsigned long long*)b;   // ticket + two chunk states, all zero
+  uint32_t* err = (uint32_t*)(b + 256);
+  uint32_t* a = (uint32_t*)(b + 512);
+  ib_status out = IB_OK;
+  if (cudaMemsetAsync(buf, 0, bytes, s) != cudaSuccess ||
+      ibgb::launch_scan_wait_selftest(a, state, err, 1000, s) != cudaSuccess) {
+    out = IB_ERR_CUDA;
+  } else {
+    out = check_error_word(err, s);
+  }
+  cudaFreeAsync(buf, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
+  return out;
+}
 
 const char* ib_status_string(ib_status st) {
   switch (st) {
@@ -386,6 +417,7 @@ ib_status ib_plan_create(const ib_plan_desc* desc, ib_plan* out) {
     return ast;
   }
   p->bins = carve((char*)p->arena, p->layout);
+  p->perm_n = -1;
   p->boxes = (char*)p->arena + p->layout.boxes;
   p->bounded = p->job.bnd[0] || p->job.bnd[1] || p->job.bnd[2];
   p->gridx = p->bounded ? (char*)p->arena + p->layout.io : nullptr;
@@ -572,6 +604,7 @@ ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* 
   J.njobs = 1;
   const Bins B = call_bins(p, npts);
   p->binned = false;    // the bins are keyed by a component's cells from here on
+  p->perm_n = -1;       // and perm no longer lists the plan's last binning
   // The list of inhabited cells and its length reuse binning scratch that is
   // dead once the bins are built: perm_tmp (2 npts entries >= the number of
   // inhabited cells) and key.
@@ -582,8 +615,7 @@ ib_status ib_spread_paper(ib_plan p, long long npts, const void* X, const void* 
     // Keys: cells in component a's staggering (one staggering for every
     // component on the cell-centred grid: one sort).
     if (a == 0 || p->sh.mac) {
-      if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(ncell + 2), s) != cudaSuccess ||
-          launch_bin(J, p->sh, B, dtype, s, a) != cudaSuccess || launch_paper_cells(B, cells, q, s) != cudaSuccess) {
+      if (clear_bins(B, s) != cudaSuccess || launch_bin(J, p->sh, B, dtype, s, a) != cudaSuccess || launch_paper_cells(B, cells, q, s) != cudaSuccess) {
         out = IB_ERR_CUDA;
         break;
       }
@@ -770,7 +802,7 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
   Bins B = b->bins;
   B.ncell_total = cells;
   B.npts_total = pts;
-  if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(cells + 2), s) != cudaSuccess) return IB_ERR_CUDA;
+  if (clear_bins(B, s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_bin(J, b->sh, B, b->desc.dtype, s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_spread(J, b->sh, B, b->boxes, tiles, b->tile, b->desc.dtype, false, false, even_n0, s) != cudaSuccess)
     return IB_ERR_CUDA;
@@ -861,7 +893,7 @@ constexpr size_t kNaBytes =
     na_align(sizeof(uint32_t) * (size_t)(kNaCells + 2)) +                          // counts / cell starts
     3 * na_align(sizeof(uint32_t) * (size_t)kNaPoints) +                            // key, rank, perm
     na_align(sizeof(uint2) * (size_t)kNaPoints) +                                   // perm_tmp
-    na_align(sizeof(uint32_t) * (size_t)((kNaCells + 1 + kScanChunkCells - 1) / kScanChunkCells + 1)) +
+    na_align(sizeof(unsigned long long) * (size_t)((kNaCells + 1 + kScanChunkCells - 1) / kScanChunkCells + 1)) +
     na_align(sizeof(uint32_t));                                                     // error word
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -916,8 +948,8 @@ extern "C" ib_status ib_interpolate_noalloc(const ib_plan_desc* desc, long long 
   J.one.U = U;
   J.njobs = 1;
   cudaStream_t s = (cudaStream_t)stream;
-  // The array keeps the previous call's contents: the counts and the error word start from zero.
-  if (cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * (size_t)(jb.ncell + 2), s) != cudaSuccess) return IB_ERR_CUDA;
+  // The array keeps the previous call's contents: the counts, the scan state and the error word start from zero.
+  if (clear_bins(B, s) != cudaSuccess) return IB_ERR_CUDA;
   if (cudaMemsetAsync(B.err, 0, sizeof(uint32_t), s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_bin(J, sh, B, desc->dtype, s) != cudaSuccess) return IB_ERR_CUDA;
   if (launch_interp(J, sh, B, J.one.nitiles, desc->dtype, 1.0, s) != cudaSuccess) return IB_ERR_CUDA;

@@ -5,8 +5,10 @@
 //   1. k_bin_count   per point: exact cell of xi = 0, key = c_x + n0 (c_y + n1 c_z)
 //                    (plus the job's cell base), atomic per-cell count; the
 //                    value returned by the atomic is the point's arrival rank.
-//   2. scan          exclusive prefix of the counts -> cell_start (chunk
-//                    totals, then each chunk adds the totals before it).
+//                    Points are taken in the order of the previous binning of
+//                    the plan when it had as many points (k_bin_count_ord).
+//   2. scan          exclusive prefix of the counts -> cell_start, one pass
+//                    with decoupled look-back (bounded waits).
 //   3. k_bin_scatter perm_tmp[cell_start[key] + rank] = (point, key) (any order
 //                    in a cell).
 //   4. k_bin_stable  per sorted position: perm[cell_start[key] + #(same-cell
@@ -53,9 +55,9 @@ __device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, cons
   return (uint32_t)(jb.cell_base + key);
 }
 
-// Four consecutive points per thread (single job, 16-byte aligned X, FP32):
-// three vector loads of positions, four independent counting atomics in
-// flight, vector stores of keys and ranks.
+// Four consecutive points per thread (single job, 16-byte aligned X, FP32,
+// identity order): three vector loads of positions, four independent
+// counting atomics in flight, vector stores of keys and ranks.
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__ Jobs J, const Bins B, const Shape sh,
                                                          int key_comp) {
@@ -90,6 +92,58 @@ __global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__
       if (g0 + i < n) {
         B.key[g0 + i] = key[i];
         B.rank[g0 + i] = rank[i];
+      }
+  }
+}
+
+// Four points per thread taken in the order of the previous binning of the
+// same number of points (single job): positions t .. t + 3 of that order.
+// Between the timesteps of the method a point moves by a fraction of a cell,
+// so consecutive threads count into neighbouring cells (the atomics of a warp
+// fall on a few cache lines) and the scatter that follows writes nearly in
+// sequence.  Keys and ranks are stored by position t.  The result does not
+// depend on the order: the stable fix-up orders each cell by point index.
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_bin_count_ord(const __grid_constant__ Jobs J, const Bins B,
+                                                            const Shape sh, int key_comp) {
+  const long long t0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * 4;
+  const long long n = B.npts_total;
+  if (t0 >= n) return;
+  const Job& jb = J.one;
+  const T* X = (const T*)jb.X;
+  const bool full = t0 + 4 <= n;
+  uint32_t g[4] = {0u, 0u, 0u, 0u};
+  if (full) {
+    const uint4 o = *reinterpret_cast<const uint4*>(B.order + t0);
+    g[0] = o.x; g[1] = o.y; g[2] = o.z; g[3] = o.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (t0 + i < n) g[i] = B.order[t0 + i];
+  }
+  T x[4 * D];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long gi = IB_IN(B.err, g[i], n) ? (long long)g[i] : 0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) x[i * D + b] = (full || t0 + i < n) ? X[gi * D + b] : (T)0;
+  }
+  uint32_t key[4], rank[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (full || t0 + i < n) key[i] = point_key<T, D>(jb, B, x + i * D, sh, key_comp);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (full || t0 + i < n) rank[i] = IB_IN(B.err, key[i], B.ncell_total + 1) ? atomicAdd(&B.count[key[i]], 1u) : 0u;
+  if (full) {
+    *reinterpret_cast<uint4*>(B.key + t0) = make_uint4(key[0], key[1], key[2], key[3]);
+    *reinterpret_cast<uint4*>(B.rank + t0) = make_uint4(rank[0], rank[1], rank[2], rank[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (t0 + i < n) {
+        B.key[t0 + i] = key[i];
+        B.rank[t0 + i] = rank[i];
       }
   }
 }
@@ -148,84 +202,94 @@ __device__ __forceinline__ void load8(const uint32_t* __restrict__ a, long long 
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ a, long long m,
-                                                               uint32_t* __restrict__ sums) {
-  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
+// ---------------------------------------------------------------------------
+// Exclusive prefix of the counts in one pass (decoupled look-back): a block
+// takes the next chunk of kScanChunk counts from a ticket counter, so chunks
+// are started in increasing order and a block only ever waits on chunks
+// whose blocks are already running.  It publishes its chunk total
+// (aggregate), then reads the states of the chunks before it, 32 at a time,
+// adding aggregates until it meets a published inclusive prefix; it publishes
+// its own inclusive prefix and writes the chunk's exclusive offsets.  A state
+// is one 64-bit word (flag << 32 | value), written and read whole.  The ticket
+// and the states are cleared with the counts before each binning.  Every
+// wait polls a bounded number of times (kScanSpinLimit, about a second with
+// the pauses between polls); a wait that runs out sets ERR_TIMEOUT in the
+// error word (reported as IB_ERR_TIMEOUT) and the block goes on with the sum
+// it has, so the launch always ends.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kStAgg = 1ull << 32;
+constexpr unsigned long long kStInc = 2ull << 32;
+constexpr int kScanSpinLimit = 1 << 23;
+
+__device__ __forceinline__ unsigned long long load_state(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void store_state(unsigned long long* p, unsigned long long v) {
+  *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// Warp 0: the exclusive prefix of chunk `id` from the states of chunks
+// id - 1, id - 2, ... (state[1 + c] for chunk c).  Returns the sum; on a
+// wait that runs out, the sum of what was read.
+__device__ __forceinline__ uint32_t look_back(const unsigned long long* state, long long id, uint32_t* err,
+                                              int spin_limit) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0;
+  long long pos = id;   // chunks [0, pos) not yet summed
+  while (pos > 0) {
+    const long long c = pos - 1 - lane;
+    unsigned long long v = c >= 0 ? load_state(state + 1 + c) : kStInc;
+    int spins = 0;
+    while (__any_sync(0xffffffffu, (v >> 32) == 0ull)) {
+      if (++spins > spin_limit) {
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        return prefix;
+      }
+      __nanosleep(100);
+      if ((v >> 32) == 0ull) v = load_state(state + 1 + c);
+    }
+    const unsigned inc = __ballot_sync(0xffffffffu, (v >> 32) == 2ull);
+    // lanes up to the first inclusive prefix (nearest chunk first) contribute
+    const int stop = inc ? __ffs(inc) - 1 : 31;
+    uint32_t x = lane <= stop ? (uint32_t)v : 0u;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    prefix += x;
+    if (inc) break;
+    pos -= 32;
+  }
+  return prefix;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_lookback(uint32_t* __restrict__ a, long long m,
+                                                                 unsigned long long* __restrict__ state, long long nb,
+                                                                 uint32_t* err, int spin_limit, long long fixed_id) {
+  __shared__ long long s_id;
+  __shared__ uint32_t s_prefix;
+  if (threadIdx.x == 0) s_id = fixed_id >= 0 ? fixed_id : (long long)atomicAdd(state, 1ull);
+  __syncthreads();
+  const long long id = s_id;
+  if (id >= nb) return;
+  const long long base = id * kScanChunk + (long long)threadIdx.x * kScanItems;
   uint32_t v[kScanItems], s = 0;
   load8(a, base, m, v);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) s += v[i];
   uint32_t tot;
-  block_exclusive(s, &tot);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
-// One block: exclusive scan of the block sums in place; sums[nb] = grand total.
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t* __restrict__ sums, long long nb) {
-  uint32_t carry = 0;
-  for (long long base = 0; base < nb; base += kScanChunk) {
-    const long long i0 = base + (long long)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems], s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-      v[i] = (i0 + i < nb) ? sums[i0 + i] : 0u;
-      s += v[i];
+  uint32_t off = block_exclusive(s, &tot);
+  if (threadIdx.x < 32) {
+    uint32_t prefix = 0;
+    if (id == 0) {
+      if (threadIdx.x == 0) store_state(state + 1, kStInc | tot);
+    } else {
+      if (threadIdx.x == 0) store_state(state + 1 + id, kStAgg | tot);
+      prefix = look_back(state, id, err, spin_limit);
+      if (threadIdx.x == 0) store_state(state + 1 + id, kStInc | (uint32_t)(prefix + tot));
     }
-    uint32_t tot;
-    uint32_t off = carry + block_exclusive(s, &tot);
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-      if (i0 + i < nb) sums[i0 + i] = off;
-      off += v[i];
-    }
-    carry += tot;
+    if (threadIdx.x == 0) s_prefix = prefix;
   }
-  if (threadIdx.x == 0) sums[nb] = carry;
-}
-
-// Exclusive offsets of the chunks.  With `direct` the block sums are still raw
-// chunk totals (k_scan_sums skipped, nb <= kDirectBlocks): each block adds up
-// the totals of the chunks before it itself.
-constexpr long long kDirectBlocks = 4 * kScanThreads;
-
-__device__ __forceinline__ uint32_t block_sum(uint32_t v) {
-  __shared__ uint32_t part[kScanThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) part[warp] = v;
   __syncthreads();
-  uint32_t t = (lane < kScanThreads / 32) ? part[lane] : 0u;
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  __syncthreads();
-  return t;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restrict__ a, long long m,
-                                                              const uint32_t* __restrict__ sums, long long nb,
-                                                              int direct) {
-  const long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
-  uint32_t v[kScanItems], s = 0;
-  load8(a, base, m, v);
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) s += v[i];
-  uint32_t before;
-  if (direct) {
-    uint32_t p = 0;
-    for (long long j = threadIdx.x; j < blockIdx.x; j += kScanThreads) p += sums[j];
-    before = block_sum(p);
-    if (blockIdx.x == gridDim.x - 1) {
-      uint32_t q = 0;
-      for (long long j = threadIdx.x; j < nb; j += kScanThreads) q += sums[j];
-      q = block_sum(q);
-      if (threadIdx.x == 0) a[m] = q;
-    }
-  } else {
-    before = sums[blockIdx.x];
-  }
-  uint32_t tot;
-  uint32_t off = before + block_exclusive(s, &tot);
+  off += s_prefix;
   uint32_t o[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
@@ -240,16 +304,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restric
     for (int i = 0; i < kScanItems; ++i)
       if (base + i < m) a[base + i] = o[i];
   }
-  if (!direct && blockIdx.x == 0 && threadIdx.x == 0) a[m] = sums[nb];
+  if (id == nb - 1 && threadIdx.x == 0) a[m] = s_prefix + tot;   // the grand total
 }
 
+// perm_tmp[cell_start[key] + rank] = (point, key), position t of the
+// processing order (the point is order[t], or t without an order).
 __global__ void __launch_bounds__(kThreads) k_bin_scatter(const Bins B) {
-  const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (g >= B.npts_total) return;
-  const uint32_t k = B.key[g];
+  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (t >= B.npts_total) return;
+  const uint32_t k = B.key[t];
+  const uint32_t g = B.order ? B.order[t] : (uint32_t)t;
   if (!IB_IN(B.err, k, B.ncell_total + 1)) return;
-  const long long dst = (long long)B.count[k] + B.rank[g];
-  if (IB_IN(B.err, dst, B.npts_total)) B.perm_tmp[dst] = make_uint2((uint32_t)g, k);
+  const long long dst = (long long)B.count[k] + B.rank[t];
+  if (IB_IN(B.err, dst, B.npts_total)) B.perm_tmp[dst] = make_uint2(g, k);
 }
 
 // Stable order inside a cell, one thread per sorted position q: the point at
@@ -280,14 +347,29 @@ inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + thre
 
 long long scan_blocks(long long m) { return (m + kScanChunk - 1) / kScanChunk; }
 
+size_t bin_clear_bytes(const Bins& B) {
+  return (size_t)((const char*)(B.scan + 1 + scan_blocks(B.ncell_total + 1)) - (const char*)B.count);
+}
+
+cudaError_t clear_bins(const Bins& B, cudaStream_t s) { return cudaMemsetAsync(B.count, 0, bin_clear_bytes(B), s); }
+
 cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype, cudaStream_t s, int key_comp) {
   const long long n = B.npts_total;
   if (n > 0) {
     // key and rank are 256-byte aligned sections of the arena
     const bool vec = !J.table && ((uintptr_t)J.one.X % 16) == 0;
-    if (dtype == 0 && vec) {
-      if (sh.dim == 3) k_bin_count4<3><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
-      else k_bin_count4<2><<<grid_for((n + 3) / 4, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
+    const unsigned g4 = grid_for((n + 3) / 4, kThreads);
+    if (B.order && !J.table) {
+      if (dtype == 0) {
+        if (sh.dim == 3) k_bin_count_ord<float, 3><<<g4, kThreads, 0, s>>>(J, B, sh, key_comp);
+        else k_bin_count_ord<float, 2><<<g4, kThreads, 0, s>>>(J, B, sh, key_comp);
+      } else {
+        if (sh.dim == 3) k_bin_count_ord<double, 3><<<g4, kThreads, 0, s>>>(J, B, sh, key_comp);
+        else k_bin_count_ord<double, 2><<<g4, kThreads, 0, s>>>(J, B, sh, key_comp);
+      }
+    } else if (dtype == 0 && vec) {
+      if (sh.dim == 3) k_bin_count4<3><<<g4, kThreads, 0, s>>>(J, B, sh, key_comp);
+      else k_bin_count4<2><<<g4, kThreads, 0, s>>>(J, B, sh, key_comp);
     } else if (dtype == 0) {
       if (sh.dim == 3) k_bin_count<float, 3><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
       else k_bin_count<float, 2><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, B, sh, key_comp);
@@ -298,14 +380,19 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
   }
   const long long m = B.ncell_total + 1;  // cells plus the sentinel; count[m] receives the total
   const long long nb = scan_blocks(m);
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.block_sums);
-  const int direct = nb <= kDirectBlocks ? 1 : 0;
-  if (!direct) k_scan_sums<<<1, kScanThreads, 0, s>>>(B.block_sums, nb);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.block_sums, nb, direct);
+  k_scan_lookback<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.scan, nb, B.err, kScanSpinLimit, -1);
   if (n > 0) {
     k_bin_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);
     k_bin_stable<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_wait_selftest(uint32_t* a, unsigned long long* state, uint32_t* err, int spin_limit,
+                                      cudaStream_t s) {
+  // Chunk 1 of two, with chunk 0 never published: its look-back waits on a
+  // state that nothing sets and must give up after spin_limit polls.
+  k_scan_lookback<<<1, kScanThreads, 0, s>>>(a, 2 * kScanChunk, state, 2, err, spin_limit, 1);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ constexpr uint32_t ERR_NONFINITE = 1u;
 constexpr uint32_t ERR_RANGE = 2u;
 constexpr uint32_t ERR_STALE = 4u;   // a point's cell no longer matches its bin (X changed after binning)
 constexpr uint32_t ERR_BOUNDS = 8u;  // an index check of the IB_DEBUG_BOUNDS build failed (access skipped)
+constexpr uint32_t ERR_TIMEOUT = 16u; // a bounded device-side wait ran out (the kernel ended without it)
 
 // Index checks of the debug build.  Compiled with IB_DEBUG_BOUNDS, IB_IN(err,
 // i, n) is true when 0 <= i < n; otherwise it sets ERR_BOUNDS in the error
@@ -88,7 +89,8 @@ struct Bins {
   uint32_t* rank;        // [npts_total]: arrival rank of the point inside its cell
   uint2* perm_tmp;       // [npts_total]: (point, cell) in cell order, arbitrary order inside a cell
   uint32_t* perm;        // [npts_total]: points in cell order, index order inside a cell (stable)
-  uint32_t* block_sums;  // scan scratch
+  unsigned long long* scan;  // scan state right after count: ticket, then one state word per chunk
+  const uint32_t* order; // processing order of the points (a permutation, e.g. the previous perm), or null
   uint32_t* err;         // device error word
   uint32_t* tflags;      // [tiles]: 1 if the spreading tile holds points (its boxes were written), or null
   long long ncell_total;

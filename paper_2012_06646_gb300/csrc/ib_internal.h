@@ -52,6 +52,17 @@ cudaError_t launch_bounds_pad(const Job& jb, int ncomp, int dtype, const void* u
 constexpr long long kScanChunkCells = 8192;
 long long scan_blocks(long long m);
 
+// Zero the per-cell counts and the scan state that follows them (one memset;
+// B.scan must sit right after B.count), before every binning.
+size_t bin_clear_bytes(const Bins& B);
+cudaError_t clear_bins(const Bins& B, cudaStream_t s);
+
+// The binning scan's look-back wait run against a chunk state that nothing
+// publishes (a self-test of the bounded wait): `state` holds 3 zeroed words,
+// `a` 2 kScanChunkCells + 1 entries; must set ERR_TIMEOUT after spin_limit polls.
+cudaError_t launch_scan_wait_selftest(uint32_t* a, unsigned long long* state, uint32_t* err, int spin_limit,
+                                      cudaStream_t s);
+
 // Binning (Algorithm 4 keys, sort and unique-key offsets): count, scan,
 // scatter and stable fix-up.  B.count must be zeroed by the caller.  Keys are
 // cells of xi = 0, or with key_comp >= 0 cells in the staggering of that

@@ -17,7 +17,6 @@
 // (each point's sum has one writer), grouped by tile: the tile's grid values
 // plus a 2-node apron are staged in shared memory once, and every point of
 // the tile gathers its support from there.
-#include <cuda_pipeline.h>
 #include <math.h>
 
 #include "ib_internal.h"
@@ -382,16 +381,21 @@ constexpr int kRec3 = 76;
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4; };
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
 __device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ double4 load4(const double* p) {
   const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
   return make_double4(a.x, a.y, b.x, b.y);
 }
 
-// Stage 1 for one point: the record at rec.
+// Stage 1 for one point: the record at rec, with multipliers g[a] (h^-d G_a
+// for spreading, 1 for interpolation).  Returns false when X changed after
+// binning (the record then carries zero weights at a corner inside the box).
 template <typename T, bool MAC>
-__device__ __forceinline__ void tile3_record(const Job& jb, const Shape& sh, const Bins& B, const T xs[3],
-                                             const T gs[3], const int T0[3], const int TE[3], T* rec) {
+__device__ __forceinline__ bool tile3_record(const Job& jb, const Shape& sh, const Bins& B, const T xs[3],
+                                             const T g[3], const int T0[3], const int TE[3], T* rec) {
   using Gm = Geo<3, 8>;
   int o0[3], dl[3];
   T w0[3][4], w1[3][4];
@@ -408,10 +412,6 @@ __device__ __forceinline__ void tile3_record(const Job& jb, const Shape& sh, con
     if (MAC) weights(sh.kernel, c.r0, c.c0, w0[b]);
     weights(sh.kernel, c.r1, c.c1, w1[b]);
   }
-  const T hmd = (T)jb.hmd;
-  T g[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) g[a] = hmd * gs[a];
 #pragma unroll
   for (int b = 0; b < 3; ++b)   // both staggerings' corners inside the box (debug build)
     inside = inside && IB_IN(B.err, o0[b], Gm::BX - 3) && IB_IN(B.err, o0[b] + dl[b], Gm::BX - 3);
@@ -446,6 +446,7 @@ __device__ __forceinline__ void tile3_record(const Job& jb, const Shape& sh, con
   const T* wz2 = MAC ? w0[2] : w1[2];   // component 2's z weights
   store4(rec + 64, w1[2][0], w1[2][2], wz2[0], wz2[2]);
   store4(rec + 68, w1[2][1], w1[2][3], wz2[1], wz2[3]);
+  return inside;
 }
 
 // Stage 2 for one batch of cnt records starting at rb (one record past the
@@ -594,7 +595,11 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
   if (lane < M) fetch(point_of(lane), xs, gs);
   if (kSpreadBatch + lane < M) pn = point_of(kSpreadBatch + lane);
   for (uint32_t base = 0; base < M; base += kSpreadBatch) {
-    if (base + lane < M) tile3_record<T, MAC>(jb, sh, B, xs, gs, T0, TE, rec_s + lane * kRec3);
+    if (base + lane < M) {
+      const T hmd = (T)jb.hmd;
+      const T g[3] = {hmd * gs[0], hmd * gs[1], hmd * gs[2]};
+      tile3_record<T, MAC>(jb, sh, B, xs, g, T0, TE, rec_s + lane * kRec3);
+    }
     if (base + kSpreadBatch + lane < M) fetch(pn, xs, gs);
     if (base + 2 * kSpreadBatch + lane < M) pn = point_of(base + 2 * kSpreadBatch + lane);
     __syncwarp();
@@ -948,6 +953,90 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
 }
 
 // ---------------------------------------------------------------------------
+// Grid values of a tile's box -- nodes T0 - 2 .. T0 + TS + 1 (unwrapped) of
+// every component -- copied into shared memory through registers: each thread
+// loads up to kStageK entries (pairs when n0 is even and the field 2-entry
+// aligned: an x pair starting at an even node then never straddles the
+// periodic seam, T0 - 2 being even) before storing them, so the loads of a
+// thread are in flight together, and the 32 lanes of a store write
+// consecutive shared addresses (a row of the box after another).  An
+// asynchronous 8-byte copy (cp.async) costs about 22 shared wavefronts per
+// warp instruction here against 2 for the plain stores.  Wrapped column, row
+// and plane offsets come from small tables built with a true modulo, so any
+// grid size n >= 1 (several periodic images inside one box) is read in range.
+// Ends with the stores issued; the caller synchronises the block.
+// ---------------------------------------------------------------------------
+constexpr int kStageK = 8;
+
+template <typename T, int D, int TS, int NTH>
+__device__ __forceinline__ void stage_box(const Job& jb, int nc, const int T0[3], T* box, uint32_t* err) {
+  using Gm = Geo<D, TS>;
+  static_assert(NTH >= Gm::BX && NTH >= Gm::BY, "one thread per table entry");
+  __shared__ int xoff_s[Gm::BX];
+  __shared__ int yoff_s[Gm::BY];
+  __shared__ int zoff_s[Gm::BZ];
+  const int tid = threadIdx.x;
+  const int n0 = jb.n[0], n1 = jb.n[1];
+  if (tid < Gm::BX) xoff_s[tid] = modn(T0[0] - 2 + tid, n0);
+  if (tid < Gm::BY) yoff_s[tid] = modn(T0[1] - 2 + tid, n1) * n0;
+  if (tid < Gm::BZ) zoff_s[tid] = (D == 3) ? modn(T0[2] - 2 + tid, jb.n[2]) * n0 * n1 : 0;
+  __syncthreads();
+  const T* u = (const T*)jb.u;
+  const int nrows_box = nc * Gm::BZ * Gm::BY;
+  if ((n0 % 2) == 0 && ((uintptr_t)u % (2 * sizeof(T))) == 0) {
+    using P2 = typename Vec2<T>::type;
+    constexpr int NP = Gm::BX / 2;
+    const int total = nrows_box * NP;
+    for (int i0 = tid; i0 < total; i0 += NTH * kStageK) {
+      P2 v[kStageK];
+#pragma unroll
+      for (int k = 0; k < kStageK; ++k) {
+        const int i = i0 + k * NTH;
+        if (i < total) {
+          const int row = i / NP;
+          const int c = i - row * NP;
+          const int a = row / (Gm::BZ * Gm::BY);
+          const int rem = row - a * (Gm::BZ * Gm::BY);
+          const int bz = rem / Gm::BY;
+          const int by = rem - bz * Gm::BY;
+          const long long si = (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xoff_s[2 * c]);
+          v[k] = IB_IN(err, si, nc * jb.ncell - 1) ? *reinterpret_cast<const P2*>(u + si) : P2{};
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kStageK; ++k) {
+        const int i = i0 + k * NTH;
+        if (i < total) *reinterpret_cast<P2*>(box + 2 * i) = v[k];   // row * BX + 2 c = 2 i
+      }
+    }
+  } else {
+    const int total = nrows_box * Gm::BX;
+    for (int i0 = tid; i0 < total; i0 += NTH * kStageK) {
+      T v[kStageK];
+#pragma unroll
+      for (int k = 0; k < kStageK; ++k) {
+        const int i = i0 + k * NTH;
+        if (i < total) {
+          const int row = i / Gm::BX;
+          const int bx = i - row * Gm::BX;
+          const int a = row / (Gm::BZ * Gm::BY);
+          const int rem = row - a * (Gm::BZ * Gm::BY);
+          const int bz = rem / Gm::BY;
+          const int by = rem - bz * Gm::BY;
+          const long long si = (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xoff_s[bx]);
+          v[k] = IB_IN(err, si, nc * jb.ncell) ? u[si] : (T)0;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kStageK; ++k) {
+        const int i = i0 + k * NTH;
+        if (i < total) box[i] = v[k];                                 // row * BX + bx = i
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Interpolation by tiles: the CTA of a tile copies the grid values of the
 // tile plus a 2-node apron (every component) into shared memory with
 // asynchronous copies, then each thread takes one of the tile's points (cell
@@ -990,54 +1079,8 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   const int nc = sh.ncomp;
   const int tid = threadIdx.x;
 
-  // Grid values of the box: nodes T0 - 2 .. T0 + TS + 1 (unwrapped), all components,
-  // fetched with cp.async, two entries per copy when n0 is even.  Wrapped row
-  // offsets come from two small tables.
-  {
-    constexpr int BXP = (Gm::BX <= 16) ? 16 : 64;
-    constexpr int RSTEP = kInterpThreads / BXP;         // rows per block iteration
-    __shared__ int yoff_s[Gm::BY];
-    __shared__ int zoff_s[Gm::BZ];
-    const int n0 = jb.n[0], n1 = jb.n[1];
-    if (tid < Gm::BY) yoff_s[tid] = wrapn(T0[1] - 2 + tid, n1) * n0;
-    if (tid < Gm::BZ) zoff_s[tid] = (D == 3) ? wrapn(T0[2] - 2 + tid, jb.n[2]) * n0 * n1 : 0;
-    __syncthreads();
-    const T* u = (const T*)jb.u;
-    const int nrows_box = nc * Gm::BZ * Gm::BY;
-    if ((n0 % 2) == 0 && ((uintptr_t)u % (2 * sizeof(T))) == 0) {
-      // Even n0 and an aligned grid: x pairs starting at an even node never
-      // straddle the periodic seam, so every row is fetched as BX/2 copies of
-      // two entries (T0 - 2 is even).
-      constexpr int NP = Gm::BX / 2;
-      for (int i = tid; i < nrows_box * NP; i += kInterpThreads) {
-        const int row = i / NP;
-        const int c = i - row * NP;
-        const int a = row / (Gm::BZ * Gm::BY);
-        const int rem = row - a * (Gm::BZ * Gm::BY);
-        const int bz = rem / Gm::BY;
-        const int by = rem - bz * Gm::BY;
-        const int xw = wrapn(T0[0] - 2 + 2 * c, n0);
-        const long long si = (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
-        if (IB_IN(B.err, si, nc * jb.ncell - 1))
-          __pipeline_memcpy_async(box + row * Gm::BX + 2 * c, u + si, 2 * sizeof(T));
-      }
-    } else {
-      for (int bx0 = tid % BXP; bx0 < Gm::BX; bx0 += BXP) {
-        const int xw = wrapn(T0[0] - 2 + bx0, n0);
-        for (int row = tid / BXP; row < nrows_box; row += RSTEP) {
-          const int a = row / (Gm::BZ * Gm::BY);
-          const int rem = row - a * (Gm::BZ * Gm::BY);
-          const int bz = rem / Gm::BY;
-          const int by = rem - bz * Gm::BY;
-          const long long si = (long long)a * jb.ncell + (zoff_s[bz] + yoff_s[by] + xw);
-          if (IB_IN(B.err, si, nc * jb.ncell)) __pipeline_memcpy_async(box + row * Gm::BX + bx0, u + si, sizeof(T));
-        }
-      }
-    }
-    __pipeline_commit();
-  }
-
-  // Rows of the tile's own cells (x fastest inside a row): start and count in the bins.
+  // Rows of the tile's own cells (x fastest inside a row): start and count in the
+  // bins, requested before the box is staged.
   const int nrows = (D == 3) ? TE[1] * TE[2] : TE[1];
   uint32_t cnt = 0, st = 0;
   if (tid < nrows) {
@@ -1047,6 +1090,7 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     st = B.count[cell];
     cnt = B.count[cell + TE[0]] - st;
   }
+  stage_box<T, D, TS, kInterpThreads>(jb, nc, T0, box, B.err);
   {
     const int lane = tid & 31, warp = tid >> 5;
     uint32_t inc = cnt;
@@ -1072,7 +1116,6 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     rpre[tid] = before + inc - cnt;
     if (tid == 0) rpre[kInterpThreads] = wsum[kInterpWarps - 1];
   }
-  __pipeline_wait_prior(0);
   __syncthreads();
 
   const uint32_t P = rpre[kInterpThreads];

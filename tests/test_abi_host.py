@@ -225,3 +225,32 @@ def test_inputs_are_deterministic_and_stream_separated():
     assert np.abs(np.diff(w, axis=3)).mean() > 0.5           # neighbouring nodes differ strongly
     k, l, m, ph = 3, 251, 17, 0.3                             # component 0 at node (x, y, z) = (1, 2, 3)
     assert abs(float(w[0, 3, 2, 1]) - np.sin(2 * np.pi * (k * 1 + l * 2 + m * 3) / 16 + ph)) < 1e-6
+
+
+def test_membrane_packing_reaches_the_stated_density_without_overlap():
+    """The clustered-membrane workload: 17 randomly oriented red cells (R0 = 3.91/16
+    of the box) compressed to about 40 % volume fraction; no point of a fine
+    (subdivision-5) surface of one cell lies inside another, over periodic
+    images; the paper's 8832 points per cell gives the denser variant."""
+    import numpy as np
+    import ib_inputs
+    m = ib_inputs.pack_membranes(0)
+    assert len(m.centres) == 17 and len(m.X) == 17 * 2562
+    assert 0.385 < m.volume_fraction < 0.40
+    assert m.X.dtype == np.float32 and m.X.min() >= 0.0 and m.X.max() < 1.0
+    P = ib_inputs.rbc_points(m.R0, ib_inputs.icosphere(5))
+    for i in range(17):
+        for j in range(17):
+            if i != j:
+                d = m.centres[i] - m.centres[j]
+                d -= np.round(d)
+                assert not ib_inputs.rbc_inside((P @ m.rotations[i].T + d) @ m.rotations[j], m.R0).any()
+    # orientations are rotations (orthonormal, det 1)
+    for R in m.rotations:
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-9) and abs(np.linalg.det(R) - 1.0) < 1e-9
+    m2 = ib_inputs.pack_membranes(0)
+    assert np.array_equal(m.X, m2.X)                                  # depends on the seed only
+    d8 = ib_inputs.pack_membranes(1, points_per_cell=8832)
+    assert len(d8.centres) == 17 and len(d8.X) == 17 * 8832
+    sph = ib_inputs.fibonacci_sphere(8832)
+    assert np.allclose(np.linalg.norm(sph, axis=1), 1.0) and abs(sph.mean(axis=0)).max() < 1e-3

@@ -222,19 +222,28 @@ def test_positions_changed_after_binning_are_reported(P):
     plan.check()
 
 
-def test_compensated_spread_on_membranes(P, orc):
-    """Clustered RBC membranes (red-cell packing), FP32 with TwoSum node sums."""
-    mem = ib_inputs.pack_membranes(0, target_cells=6, max_attempts=2000)
+@pytest.mark.parametrize("per_cell", [None, 8832], ids=["rbc2562", "rbc8832"])
+def test_compensated_spread_on_membranes(P, orc, per_cell):
+    """Clustered RBC membranes: 17 red cells compressed to about 40 % volume
+    fraction in the 128^3 MAC box (2562 points per cell, and the paper's 8832),
+    FP32 with TwoSum node sums and plain; interpolation on the same points."""
+    mem = ib_inputs.pack_membranes(0, points_per_cell=per_cell)
+    assert len(mem.centres) == 17 and mem.volume_fraction > 0.385
     X = mem.X
     G = ib_inputs.membrane_forces(0, mem)
     n = (128, 128, 128)
+    u = ib_inputs.normal_array(7, (3, 128, 128, 128))
     plan = P(3, n, (1.0, 1.0, 1.0), max_points=len(X), compensated=True)
     g = orc.Grid(dim=3, n=n, L=(1.0, 1.0, 1.0))
     f_ref, fabs = orc.spread(g, X, G)
     fc = host(plan.spread(dev(X), dev(G), compensated=True))
-    fp = host(plan.spread(dev(X), dev(G)))
+    fp = host(plan.spread(dev(X), dev(G), reuse_bins=True))
+    U = host(plan.interpolate(dev(X), dev(u), reuse_bins=True))
+    plan.check()
     assert_spread_close(fc, f_ref, fabs, what="compensated")
     assert_spread_close(fp, f_ref, fabs, what="plain")
+    U_ref, Uabs = orc.interp(g, X, u)
+    assert_interp_close(U, U_ref, Uabs)
     ec = np.abs(fc - f_ref).sum()
     ep = np.abs(fp - f_ref).sum()
     assert ec <= ep

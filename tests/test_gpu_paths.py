@@ -160,3 +160,73 @@ def test_offsets_near_half_cells_origin_and_negative(P, orc, mac):
         g = orc.Grid(dim=3, n=n, L=(1.0, 1.0, 1.0), mac=mac)
         f_ref, fabs = orc.spread(g, X, G)
         assert_spread_close(f, f_ref, fabs, what=f"spread of X = {X[0].tolist()}")
+
+
+def _bins_ref(orc, g, X):
+    return orc.bin_stable(orc.cell_keys(g, X.astype(np.float64)), g.ncell)[:2]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+def test_binning_in_the_previous_order_stays_exact(P, orc, dtype):
+    """A plan re-binning as many points takes them in the order of its last
+    bins (consecutive threads then count nearby cells); the bins must still be
+    the stable sort, whatever that order: after a small displacement, after a
+    new random point set, after invalid positions, and after a binning of a
+    different number of points (identity order again)."""
+    n, L, npts = (48, 40, 36), (1.0, 0.8, 0.75), 60_000
+    g = orc.Grid(dim=3, n=n, L=L, mac=True)
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    plan = P(3, n, L, max_points=npts, dtype=tdt)
+    X0 = ib_inputs.uniform_points(31, npts, L, 3, dtype=dtype)
+    step = (ib_inputs.normal_array(32, (npts, 3), dtype=np.float64) * (0.3 / 48)).astype(dtype)
+    X1 = (X0 + step).astype(dtype)                                   # a timestep's displacement
+    X2 = ib_inputs.uniform_points(33, npts, L, 3, dtype=dtype)       # unrelated positions
+    X3 = X2.copy()
+    X3[::997] = np.nan                                               # invalid positions sort last
+    X4 = X1[: npts - 7].copy()                                       # another point count
+    for X in (X0, X1, X2, X1, X4, X1):
+        plan.bin(dev(X))
+        perm, start = plan.bins()
+        perm_ref, start_ref = _bins_ref(orc, g, X)
+        assert np.array_equal(host(perm), perm_ref)
+        assert np.array_equal(host(start)[: g.ncell + 1], start_ref)
+        plan.check()
+    plan.bin(dev(X3))
+    perm, start = plan.bins()
+    valid = ~np.isnan(X3).any(axis=1)
+    iv, ii = np.flatnonzero(valid), np.flatnonzero(~valid)
+    pv, start_ref = _bins_ref(orc, g, X3[valid])
+    assert np.array_equal(host(perm), np.concatenate([iv[pv], ii]))  # invalid points last, in index order
+    assert np.array_equal(host(start)[: g.ncell + 1], start_ref)
+    with pytest.raises(Exception):
+        plan.check()                                                 # the NaN positions are reported
+    # spreading and interpolation on ordered bins equal those on fresh bins, bit for bit
+    G = dev(ib_inputs.normal_array(34, (npts, 3), dtype=dtype))
+    u = dev(ib_inputs.normal_array(35, (3, 36, 40, 48), dtype=dtype))
+    plan.bin(dev(X0))
+    f1 = host(plan.spread(dev(X1), G))                                # bins X1 in X0's order
+    U1 = host(plan.interpolate(dev(X1), u, reuse_bins=True))
+    fresh = P(3, n, L, max_points=npts, dtype=tdt)
+    assert np.array_equal(host(fresh.spread(dev(X1), G)), f1)
+    assert np.array_equal(host(fresh.interpolate(dev(X1), u, reuse_bins=True)), U1)
+
+
+def test_bounded_wait_runs_out_and_the_device_stays_usable(P, orc):
+    """The binning scan waits (decoupled look-back) with a bounded number of
+    polls; the self-test runs one wait on a chunk state that nothing publishes
+    and must report IB_ERR_TIMEOUT, after which binning works as before."""
+    from paper_2012_06646_gb300 import _abi
+    lib = _abi.load()
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.ib_selftest_bounded_wait(s) == _abi.IB_ERR_TIMEOUT
+    assert lib.ib_selftest_bounded_wait(s) == _abi.IB_ERR_TIMEOUT
+    n, L = (32, 32, 32), (1.0, 1.0, 1.0)
+    X = ib_inputs.uniform_points(41, 5000, L, 3)
+    plan = P(3, n, L, max_points=5000)
+    plan.bin(dev(X))
+    plan.check()
+    g = orc.Grid(dim=3, n=n, L=L, mac=True)
+    perm, start = plan.bins()
+    perm_ref, start_ref = _bins_ref(orc, g, X)
+    assert np.array_equal(host(perm), perm_ref)
+    assert np.array_equal(host(start)[: g.ncell + 1], start_ref)

@@ -341,6 +341,17 @@ ib_status ib_batch_run_host(ib_batch batch, int njobs, const ib_host_job* jobs, 
 /* As ib_plan_check, for the batch object's device error word. */
 ib_status ib_batch_check(ib_batch batch, void* stream);
 
+/* Status of the device error word as the last ib_batch_run_host wave on this
+ * batch left it: that call ends by copying the word (not clearing it) into
+ * pinned host memory on its stream, so once the caller knows the stream has
+ * passed the wave (an event recorded after the call has completed) this
+ * decodes the copy without any CUDA call or synchronisation.  The word keeps
+ * accumulating until ib_batch_check reads and clears it: a server calls
+ * ib_batch_check only when this reports an error, to learn and clear that
+ * wave's outcome.  IB_ERR_INVALID_ARG for a batch without IB_BATCH_HOST_IO.
+ * Host-only.  Paper counterpart: none (serving form). */
+ib_status ib_batch_wave_status(ib_batch batch);
+
 /* ---------------------------------------------------------------------------
  * Interpolation for callers that cannot allocate device memory.  The paper
  * has no counterpart.  Some callers must not call cudaMalloc: code whose

@@ -114,6 +114,7 @@ SIGNATURES = {
     "ib_batch_destroy": (_st, [_vp]),
     "ib_batch_run": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_job), ctypes.c_uint, _vp]),
     "ib_batch_check": (_st, [_vp, _vp]),
+    "ib_batch_wave_status": (_st, [_vp]),
     "ib_batch_run_host": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_host_job), _vp]),
     "ib_interpolate_noalloc": (_st, [ctypes.POINTER(ib_plan_desc), _ll, _vp, _vp, _vp, _vp]),
     "ib_stokes_create": (_st, [ctypes.POINTER(ib_plan_desc), ctypes.POINTER(_vp)]),

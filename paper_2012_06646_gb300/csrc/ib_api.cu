@@ -193,6 +193,16 @@ Bins carve(char* base, const Layout& L) {
   return B;
 }
 
+// Status of an error word's bits, the most serious first.
+ib_status decode_error_word(uint32_t e) {
+  if (e & ERR_BOUNDS) return IB_ERR_BOUNDS;
+  if (e & ERR_TIMEOUT) return IB_ERR_TIMEOUT;
+  if (e & ERR_NONFINITE) return IB_ERR_NONFINITE;
+  if (e & ERR_RANGE) return IB_ERR_RANGE;
+  if (e & ERR_STALE) return IB_ERR_BINS_STALE;
+  return IB_OK;
+}
+
 ib_status check_error_word(uint32_t* err_dev, cudaStream_t s) {
   // Read (and clear) on the caller's stream, so the check waits for that
   // stream's work only, not for other streams as the legacy stream would.
@@ -203,12 +213,7 @@ ib_status check_error_word(uint32_t* err_dev, cudaStream_t s) {
     if (cudaMemsetAsync(err_dev, 0, sizeof(uint32_t), s) != cudaSuccess) return IB_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return IB_ERR_CUDA;
   }
-  if (e & ERR_BOUNDS) return IB_ERR_BOUNDS;
-  if (e & ERR_TIMEOUT) return IB_ERR_TIMEOUT;
-  if (e & ERR_NONFINITE) return IB_ERR_NONFINITE;
-  if (e & ERR_RANGE) return IB_ERR_RANGE;
-  if (e & ERR_STALE) return IB_ERR_BINS_STALE;
-  return IB_OK;
+  return decode_error_word(e);
 }
 
 }  // namespace
@@ -243,7 +248,8 @@ struct ib_batch_s {
   Bins bins;
   void* boxes;
   Job* d_table;
-  Job* h_stage;        // pinned staging buffer of the job table
+  Job* h_stage;        // pinned staging buffer of the job table, then one word:
+  uint32_t* h_err;     // pinned copy of the error word, written by each host-I/O wave's stream
   cudaEvent_t uploaded;
   bool pending;
   char* io;            // IB_BATCH_HOST_IO: device X, G, U (max_points) and grids (max_cells)
@@ -711,7 +717,7 @@ ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out) {
     delete b;
     return ast;
   }
-  if (cudaMallocHost((void**)&b->h_stage, sizeof(Job) * (size_t)desc->max_jobs) != cudaSuccess) {
+  if (cudaMallocHost((void**)&b->h_stage, sizeof(Job) * (size_t)desc->max_jobs + 16) != cudaSuccess) {
     cudaGetLastError();
     arena_free(b->alloc, b->arena);
     delete b;
@@ -734,6 +740,8 @@ ib_status ib_batch_create(const ib_batch_desc* desc, ib_batch* out) {
     }
     b->io = (char*)b->arena + b->layout.io;
   }
+  b->h_err = (uint32_t*)((char*)b->h_stage + sizeof(Job) * (size_t)desc->max_jobs);
+  *b->h_err = 0u;
   b->bins = carve((char*)b->arena, b->layout);
   b->boxes = (char*)b->arena + b->layout.boxes;
   b->d_table = (Job*)((char*)b->arena + b->layout.table);
@@ -865,7 +873,15 @@ ib_status ib_batch_run_host(ib_batch b, int njobs, const ib_host_job* jobs, void
         cudaSuccess)
       return IB_ERR_CUDA;
   }
+  // the error word as this wave leaves it, for ib_batch_wave_status (no synchronisation needed)
+  if (cudaMemcpyAsync(b->h_err, b->bins.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return IB_ERR_CUDA;
   return IB_OK;
+}
+
+ib_status ib_batch_wave_status(ib_batch b) {
+  if (!b || !(b->desc.flags & IB_BATCH_HOST_IO)) return IB_ERR_INVALID_ARG;
+  return decode_error_word(*(volatile uint32_t*)b->h_err);
 }
 
 ib_status ib_batch_check(ib_batch b, void* stream) {

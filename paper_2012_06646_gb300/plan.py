@@ -398,6 +398,11 @@ class Batch:
         """ib_batch_check without raising: the status code of the error word (read and cleared)."""
         return int(self.lib.ib_batch_check(self.handle, _stream_ptr(stream)))
 
+    def wave_status(self) -> int:
+        """ib_batch_wave_status: the error word as the last run_host wave left it (no synchronisation;
+        valid once that wave's stream has passed it)."""
+        return int(self.lib.ib_batch_wave_status(self.handle))
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.ib_batch_destroy(self.handle)

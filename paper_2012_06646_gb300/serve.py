@@ -14,9 +14,10 @@ never leaves the device).  The loop
     from pinned host memory into the slot's device buffers, the wave runs
     in a fixed number of launches for any number of jobs, and U is copied
     back, all on the slot's stream;
-  * retires a wave when its completion event fires, reads the wave's device
-    error word on the slot's stream and records each request's outcome and
-    latency (completion minus arrival).
+  * retires a wave when its completion event fires, reads the copy of the
+    device error word that the wave's own stream left in pinned memory (the
+    blocking read-and-clear on the slot's stream only when it shows an error)
+    and records each request's outcome and latency (completion minus arrival).
 
 Failures are handled on the host, per request: a job that can never fit a
 wave slot (points, cells or tiles above the slot's capacity, or an invalid
@@ -233,7 +234,10 @@ class Server:
             for i, w in enumerate(slots):
                 if w is not None and w.event.query():
                     tdone = time.perf_counter() - t0
-                    err = self.batches[i].status(self.streams[i])
+                    # the wave's copy of the error word; the blocking read-and-clear only on an error
+                    err = self.batches[i].wave_status()
+                    if err != _abi.IB_OK:
+                        err = self.batches[i].status(self.streams[i])
                     if err not in (_abi.IB_OK, _abi.IB_ERR_NONFINITE, _abi.IB_ERR_RANGE):
                         raise IBError(err, "served wave")
                     for r in w.reqs:

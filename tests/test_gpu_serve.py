@@ -85,6 +85,39 @@ def test_batch_run_host_equals_device_batch(mods):
     hbatch.close()
 
 
+def test_wave_status_reports_each_host_wave_without_a_sync(mods):
+    """ib_batch_wave_status: the error word as the last host-I/O wave left it, read from
+    pinned memory that the wave's stream wrote; ib_batch_check still reads and clears it."""
+    from paper_2012_06646_gb300 import _abi
+    Plan, Batch, serve = mods
+    b = Batch(dim=3, max_jobs=4, max_points=1 << 14, max_cells=1 << 16, host_io=True)
+    specs = _jobs(11, 3)
+    waves = []
+    for bad in (False, True, False):
+        jobs = []
+        for sp in specs:
+            X = ib_inputs.job_points(sp)
+            if bad:
+                X[sp.npts // 2] = np.nan
+            G = ib_inputs.normal_array(sp.seed, (sp.npts, 3), purpose="job-G")
+            jobs.append(((sp.N,) * 3, (1.0,) * 3, torch.from_numpy(X).pin_memory(), torch.from_numpy(G).pin_memory(),
+                         torch.empty((sp.npts, 3)).pin_memory()))
+        waves.append(jobs)
+    s = torch.cuda.current_stream()
+    b.run_host(waves[0], stream=s)
+    s.synchronize()
+    assert b.wave_status() == _abi.IB_OK
+    b.run_host(waves[1], stream=s)
+    s.synchronize()
+    assert b.wave_status() == _abi.IB_ERR_NONFINITE
+    assert b.status(s) == _abi.IB_ERR_NONFINITE              # read and cleared
+    b.run_host(waves[2], stream=s)
+    s.synchronize()
+    assert b.wave_status() == _abi.IB_OK
+    assert all(bool(torch.isnan(U[sp.npts // 2]).all()) for (_, _, _, _, U), sp in zip(waves[1], specs))
+    b.close()
+
+
 def test_server_continuous_batching_matches_single_loop(mods):
     Plan, Batch, serve = mods
     specs = _jobs(9, 60)

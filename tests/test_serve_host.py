@@ -63,6 +63,9 @@ def make_fake_batch(abi, fail_at=None):
             e, self.err = self.err, abi.IB_OK
             return e
 
+        def wave_status(self):
+            return self.err                    # the word as the last wave left it, not cleared
+
         def check(self, stream=None):
             abi.check(self.status(stream), "ib_batch_check")
 

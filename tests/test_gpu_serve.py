@@ -90,7 +90,7 @@ def test_wave_status_reports_each_host_wave_without_a_sync(mods):
     pinned memory that the wave's stream wrote; ib_batch_check still reads and clears it."""
     from paper_2012_06646_gb300 import _abi
     Plan, Batch, serve = mods
-    b = Batch(dim=3, max_jobs=4, max_points=1 << 14, max_cells=1 << 16, host_io=True)
+    b = Batch(dim=3, max_jobs=4, max_points=1 << 16, max_cells=1 << 20, host_io=True)
     specs = _jobs(11, 3)
     waves = []
     for bad in (False, True, False):

@@ -262,6 +262,67 @@ ib_status ib_plan_bins(ib_plan plan, const void** perm, const void** cell_start,
                        long long* npts);
 
 /* ---------------------------------------------------------------------------
+ * z-slab decomposition: a prototype of splitting one problem over GPUs (the
+ * paper's Section 5 names a different kappa or # on each node as the way to
+ * distribute the method).  The grid is cut along z into slabs of whole
+ * 8-node tile layers; slab k owns layers [b_k, b_{k+1}) and the points whose
+ * cell (xi = 0) lies in them.  Each slab's plan is a plan of the whole grid
+ * that only ever works on its own layers:
+ *   spreading: ib_slab_spread bins the slab's points and forms the tile
+ *     boxes of its layers, then packs the box planes that reach the
+ *     neighbouring slabs (the two node planes below the slab, from its bottom
+ *     layer, into send_lo; the two above it, from its top layer, into
+ *     send_hi).  The caller moves send_lo to the lower neighbour's recv_hi and
+ *     send_hi to the upper neighbour's recv_lo (periodically: slab 0's lower
+ *     neighbour is the last slab) by any device copy -- a peer copy or a
+ *     collective between GPUs, a plain copy on one GPU; then ib_slab_combine
+ *     places the received planes and forms f on the slab's own node planes
+ *     [8 b_k, 8 b_{k+1}) only.  Every node sum runs over the same boxes in the
+ *     same order as ib_spread's, so the slabs' planes together equal ib_spread's
+ *     f bit for bit.
+ *   interpolation: a slab needs the field on its own planes and two planes on
+ *     each side (the support of its points' cells); after that halo copy (plain
+ *     copies of node planes, by the caller), ib_interpolate on the slab's
+ *     points gives their values, equal to ib_interpolate's on the whole point
+ *     set bit for bit.
+ * Requirements (else IB_ERR_INVALID_ARG): dim 3, ncomp 3, a 4-point kernel, no
+ * bounded dimension, n2 a multiple of 8 and at least 16.  The plan's scratch
+ * is that of the whole grid (a production split would hold its layers and one
+ * neighbouring layer each side).  Paper counterpart: the distribution the
+ * paper's summary proposes; not in its algorithms.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of one side's packed planes (send_lo, send_hi, recv_lo, recv_hi each):
+ * n0/8 x n1/8 tiles x 3 components x (2 with IB_COMPENSATED in flags, else 1)
+ * box planes x 2 z planes x 12 x 12 entries of the dtype.  Host-only. */
+ib_status ib_slab_halo_bytes(ib_plan plan, unsigned flags, size_t* bytes);
+
+/* owner[j] = the slab k with layer_bounds[k] <= (cell of X_j along z) / 8 <
+ * layer_bounds[k + 1], or -1 for an invalid position (the exact cell map of
+ * ib_bin).  layer_bounds: host array of nslab + 1 increasing tile layers, from
+ * 0 to n2 / 8; 1 <= nslab <= 64.  X (npts, 3) device, owner (npts) int32
+ * device. */
+ib_status ib_slab_owner(ib_plan plan, long long npts, const void* X, int nslab, const int* layer_bounds, int* owner,
+                        void* stream);
+
+/* Bin the slab's npts points X (all of them with their cell in layers
+ * [zb, ze), as ib_slab_owner assigns them; a point outside contributes
+ * nothing), form the tile boxes of layers [zb, ze) with forces G, and pack
+ * the planes for the neighbours into send_lo and send_hi (device buffers of
+ * ib_slab_halo_bytes each, caller-owned).  Flags: IB_COMPENSATED (a plan
+ * created with IB_PLAN_COMPENSATED), IB_REUSE_BINS. */
+ib_status ib_slab_spread(ib_plan plan, long long npts, const void* X, const void* G, int zb, int ze, void* send_lo,
+                         void* send_hi, unsigned flags, void* stream);
+
+/* Place the planes received from the lower (recv_lo: that slab's send_hi) and
+ * upper (recv_hi: its send_lo) neighbours and form f on node planes
+ * [8 zb, 8 ze) of the whole-grid array f [3][n2][n1][n0] (other planes are not
+ * touched).  Follows ib_slab_spread on the same plan and layers.  Flags:
+ * IB_COMPENSATED (as given to ib_slab_spread), IB_ACCUMULATE. */
+ib_status ib_slab_combine(ib_plan plan, void* f, int zb, int ze, const void* recv_lo, const void* recv_hi,
+                          unsigned flags, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Batched, served form: one wave of independent spread + interpolate jobs of
  * uneven grid and point counts runs as a fixed number of launches, whatever
  * the number of jobs.  Jobs in a wave share dim, grid kind, kernel, dtype and
@@ -313,8 +374,9 @@ ib_status ib_batch_destroy(ib_batch batch);
  * G -> f for every job with G != NULL, then interpolate u -> U for every job
  * with u != NULL.  The job array is copied before the call returns.  Waits
  * (host side) for the previous wave's job-table upload on this batch object
- * before reusing its staging buffer.  IB_ERR_CAPACITY if the wave exceeds
- * the batch capacity. */
+ * before reusing its staging buffer.  A wave of one job runs the single-job
+ * launches of a plan (no table upload), with the same result.
+ * IB_ERR_CAPACITY if the wave exceeds the batch capacity. */
 ib_status ib_batch_run(ib_batch batch, int njobs, const ib_job* jobs, unsigned flags, void* stream);
 
 /* A served job with host-resident data (see ib_batch_run_host). */

@@ -113,6 +113,10 @@ SIGNATURES = {
     "ib_batch_create": (_st, [ctypes.POINTER(ib_batch_desc), ctypes.POINTER(_vp)]),
     "ib_batch_destroy": (_st, [_vp]),
     "ib_batch_run": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_job), ctypes.c_uint, _vp]),
+    "ib_slab_halo_bytes": (_st, [_vp, ctypes.c_uint, ctypes.POINTER(ctypes.c_size_t)]),
+    "ib_slab_owner": (_st, [_vp, _ll, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp, _vp]),
+    "ib_slab_spread": (_st, [_vp, _ll, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint, _vp]),
+    "ib_slab_combine": (_st, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint, _vp]),
     "ib_batch_check": (_st, [_vp, _vp]),
     "ib_batch_wave_status": (_st, [_vp]),
     "ib_batch_run_host": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ib_host_job), _vp]),

@@ -492,6 +492,155 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   return IB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// z-slab decomposition (prototype of the multi-GPU split): see include/ib.h.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kSlabTile = 8;
+// A tile's box holds node planes T0 - 2 .. T0 + 9: planes 0-1 lie below the
+// tile layer (nodes T0 - 2, T0 - 1), planes kSlabTop and kSlabTop + 1 above it
+// (nodes T0 + 8, T0 + 9).
+constexpr int kSlabTop = kSlabTile + 2;
+
+// Shape requirements of the slab calls: three-component 3-D 4-point plans on
+// periodic grids whose z size is a whole number of 8-node tile layers.
+bool slab_shape_ok(ib_plan p) {
+  return p && p->desc.dim == 3 && p->desc.ncomp == 3 && kernel_width(p->desc.kernel) == 4 && !p->bounded &&
+         p->tile_plain == kSlabTile && p->tile_comp == kSlabTile && p->job.n[2] % kSlabTile == 0 &&
+         p->job.n[2] >= 2 * kSlabTile;
+}
+
+// One side's halo slices: for every tile of a tile layer, component and
+// plane of the box (value, and error when compensated), two z planes of the box.
+struct SlabSlices {
+  size_t rows, width, pitch;   // bytes: row width and box pitch (a row = one component plane of a tile)
+  size_t layer_stride;         // bytes between consecutive tile layers in the box array
+};
+
+SlabSlices slab_slices(ib_plan p, bool comp) {
+  const size_t e = (size_t)entry_bytes(p->desc.dtype, false);
+  const size_t bxy = (size_t)(kSlabTile + 4) * (kSlabTile + 4);
+  const size_t bv = bxy * (kSlabTile + 4);
+  const size_t planes = comp ? 2 : 1;
+  const size_t tiles_per_layer = (size_t)p->job.ntile[0] * (size_t)p->job.ntile[1];
+  SlabSlices sl;
+  sl.rows = tiles_per_layer * 3 * planes;
+  sl.width = 2 * bxy * e;
+  sl.pitch = bv * e;
+  sl.layer_stride = tiles_per_layer * 3 * planes * bv * e;
+  return sl;
+}
+
+bool slab_range_ok(ib_plan p, int zb, int ze) { return zb >= 0 && zb < ze && ze <= p->job.ntile[2]; }
+
+}  // namespace
+
+ib_status ib_slab_halo_bytes(ib_plan p, unsigned flags, size_t* bytes) {
+  if (!slab_shape_ok(p) || !bytes || (flags & ~IB_COMPENSATED)) return IB_ERR_INVALID_ARG;
+  const SlabSlices sl = slab_slices(p, (flags & IB_COMPENSATED) != 0);
+  *bytes = sl.rows * sl.width;
+  return IB_OK;
+}
+
+ib_status ib_slab_owner(ib_plan p, long long npts, const void* X, int nslab, const int* layer_bounds, int* owner,
+                        void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_slab_owner");
+  if (!slab_shape_ok(p) || npts < 0 || (npts > 0 && (!X || !owner)) || !layer_bounds) return IB_ERR_INVALID_ARG;
+  if (nslab < 1 || nslab > ibgb::kMaxSlabs) return IB_ERR_INVALID_ARG;
+  ibgb::SlabBounds sb;
+  memset(&sb, 0, sizeof(sb));
+  sb.nslab = nslab;
+  sb.tile = kSlabTile;
+  if (layer_bounds[0] != 0 || layer_bounds[nslab] != p->job.ntile[2]) return IB_ERR_INVALID_ARG;
+  for (int k = 0; k <= nslab; ++k) {
+    if (k > 0 && layer_bounds[k] <= layer_bounds[k - 1]) return IB_ERR_INVALID_ARG;
+    sb.bound[k] = layer_bounds[k];
+  }
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.njobs = 1;
+  if (launch_slab_owner(J, sb, npts, p->desc.dtype, owner, (cudaStream_t)stream) != cudaSuccess) return IB_ERR_CUDA;
+  return IB_OK;
+}
+
+ib_status ib_slab_spread(ib_plan p, long long npts, const void* X, const void* G, int zb, int ze, void* send_lo,
+                         void* send_hi, unsigned flags, void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_slab_spread");
+  ib_status st = check_call(p, npts, X);
+  if (st != IB_OK) return st;
+  if (!slab_shape_ok(p) || !slab_range_ok(p, zb, ze) || !send_lo || !send_hi || (npts > 0 && !G))
+    return IB_ERR_INVALID_ARG;
+  if (flags & ~(IB_COMPENSATED | IB_REUSE_BINS)) return IB_ERR_INVALID_ARG;
+  const bool comp = (flags & IB_COMPENSATED) != 0;
+  if (comp && !(p->desc.flags & IB_PLAN_COMPENSATED)) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = prepare(p, npts, X, flags, s);
+  if (st != IB_OK) return st;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.npts = npts;
+  J.one.X = X;
+  J.one.G = G ? G : X;   // npts == 0: any non-null marker; no point is read
+  J.njobs = 1;
+  const long long per_layer = (long long)p->job.ntile[0] * p->job.ntile[1];
+  if (launch_slab_boxes(J, p->sh, call_bins(p, npts), p->boxes, zb * per_layer, (ze - zb) * per_layer,
+                        p->desc.dtype, comp, s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  // The boundary layers' box planes that reach the neighbouring slabs: planes
+  // 0-1 of the bottom layer (the two node planes below the slab) and planes
+  // TS+2 .. TS+3 of the top layer (the two above it).
+  const SlabSlices sl = slab_slices(p, comp);
+  const size_t e = (size_t)entry_bytes(p->desc.dtype, false);
+  const size_t bxy = (size_t)(kSlabTile + 4) * (kSlabTile + 4);
+  const char* boxes = (const char*)p->boxes;
+  if (cudaMemcpy2DAsync(send_lo, sl.width, boxes + (size_t)zb * sl.layer_stride, sl.pitch, sl.width, sl.rows,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpy2DAsync(send_hi, sl.width, boxes + (size_t)(ze - 1) * sl.layer_stride + kSlabTop * bxy * e, sl.pitch,
+                        sl.width, sl.rows, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  return IB_OK;
+}
+
+ib_status ib_slab_combine(ib_plan p, void* f, int zb, int ze, const void* recv_lo, const void* recv_hi,
+                          unsigned flags, void* stream) {
+  const ibgb::NvtxRange nvtx_range("ib_slab_combine");
+  if (!slab_shape_ok(p) || !slab_range_ok(p, zb, ze) || !f || !recv_lo || !recv_hi) return IB_ERR_INVALID_ARG;
+  if (flags & ~(IB_COMPENSATED | IB_ACCUMULATE)) return IB_ERR_INVALID_ARG;
+  const bool comp = (flags & IB_COMPENSATED) != 0;
+  if (comp && !(p->desc.flags & IB_PLAN_COMPENSATED)) return IB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ntz = p->job.ntile[2];
+  const SlabSlices sl = slab_slices(p, comp);
+  const size_t e = (size_t)entry_bytes(p->desc.dtype, false);
+  const size_t bxy = (size_t)(kSlabTile + 4) * (kSlabTile + 4);
+  char* boxes = (char*)p->boxes;
+  // the lower neighbour's top-layer planes go to layer zb - 1, the upper
+  // neighbour's bottom-layer planes to layer ze (periodically wrapped)
+  const int lo_layer = (zb - 1 + ntz) % ntz, hi_layer = ze % ntz;
+  if (cudaMemcpy2DAsync(boxes + (size_t)lo_layer * sl.layer_stride + kSlabTop * bxy * e, sl.pitch, recv_lo, sl.width,
+                        sl.width, sl.rows, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpy2DAsync(boxes + (size_t)hi_layer * sl.layer_stride, sl.pitch, recv_hi, sl.width, sl.width, sl.rows,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  Jobs J;
+  memset(&J, 0, sizeof(J));
+  J.one = p->job;
+  J.one.f = f;
+  J.one.G = f;           // a non-null marker: the combination skips jobs without forces
+  J.njobs = 1;
+  const long long plane = (long long)p->job.n[0] * p->job.n[1];
+  if (launch_slab_combine(J, p->sh, call_bins(p, 0), p->boxes, (long long)zb * kSlabTile * plane,
+                          (long long)ze * kSlabTile * plane, p->desc.dtype, comp, (flags & IB_ACCUMULATE) != 0,
+                          pair_aligned(p->job.n[0], f, p->desc.dtype), s) != cudaSuccess)
+    return IB_ERR_CUDA;
+  return IB_OK;
+}
+
 ib_status ib_interpolate(ib_plan p, long long npts, const void* X, const void* u, void* U, unsigned flags,
                          void* stream) {
   const ibgb::NvtxRange nvtx_range("ib_interpolate");
@@ -799,14 +948,23 @@ ib_status ib_batch_run(ib_batch b, int njobs, const ib_job* jobs, unsigned flags
     itiles += jb.nitiles;
     if (cells > b->desc.max_cells || pts > b->desc.max_points || tiles > b->desc.max_tiles) return IB_ERR_CAPACITY;
   }
-  if (cudaMemcpyAsync(b->d_table, b->h_stage, sizeof(Job) * (size_t)njobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return IB_ERR_CUDA;
-  if (cudaEventRecord(b->uploaded, s) != cudaSuccess) return IB_ERR_CUDA;
-  b->pending = true;
   Jobs J;
   memset(&J, 0, sizeof(J));
-  J.table = b->d_table;
-  J.njobs = njobs;
+  if (njobs == 1) {
+    // A lone job (a light load) runs the single-job launches: the job in the
+    // kernel parameters, no table upload or table lookups -- the kernels and
+    // arithmetic of a plan, so the result is the same bit for bit.
+    J.one = b->h_stage[0];
+    J.njobs = 1;
+  } else {
+    if (cudaMemcpyAsync(b->d_table, b->h_stage, sizeof(Job) * (size_t)njobs, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return IB_ERR_CUDA;
+    if (cudaEventRecord(b->uploaded, s) != cudaSuccess) return IB_ERR_CUDA;
+    b->pending = true;
+    J.table = b->d_table;
+    J.njobs = njobs;
+  }
   Bins B = b->bins;
   B.ncell_total = cells;
   B.npts_total = pts;

@@ -343,6 +343,28 @@ __global__ void __launch_bounds__(kThreads) k_bin_stable(const Bins B) {
 
 inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Owner slab of each point: its cell of xi = 0 along z (the exact cell map,
+// wrapped periodically) lies in tile layer L = cell / 8, and slab k owns the
+// layers [bounds[k], bounds[k + 1]).  Invalid positions get -1.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_slab_owner(const __grid_constant__ Jobs J, const SlabBounds sb,
+                                                         long long n, int* __restrict__ owner) {
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const Job& jb = J.one;
+  Cell1<T> c;
+  const uint32_t e = point_cell<T>(((const T*)jb.X)[i * 3 + 2], jb, 2, c);
+  int o = -1;
+  if (e == 0) {
+    const int nz = jb.n[2];
+    const int cz = ((unsigned)c.i0 < (unsigned)nz) ? c.i0 : modn(c.i0, nz);
+    const int layer = cz / sb.tile;
+    for (int k = 0; k < sb.nslab; ++k)
+      if (layer >= sb.bound[k] && layer < sb.bound[k + 1]) o = k;
+  }
+  owner[i] = o;
+}
+
 }  // namespace
 
 long long scan_blocks(long long m) { return (m + kScanChunk - 1) / kScanChunk; }
@@ -393,6 +415,13 @@ cudaError_t launch_scan_wait_selftest(uint32_t* a, unsigned long long* state, ui
   // Chunk 1 of two, with chunk 0 never published: its look-back waits on a
   // state that nothing sets and must give up after spin_limit polls.
   k_scan_lookback<<<1, kScanThreads, 0, s>>>(a, 2 * kScanChunk, state, 2, err, spin_limit, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slab_owner(const Jobs& J, const SlabBounds& sb, long long n, int dtype, int* owner, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (dtype == 0) k_slab_owner<float><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sb, n, owner);
+  else k_slab_owner<double><<<grid_for(n, kThreads), kThreads, 0, s>>>(J, sb, n, owner);
   return cudaGetLastError();
 }
 

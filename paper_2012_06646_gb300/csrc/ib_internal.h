@@ -94,6 +94,25 @@ cudaError_t launch_paper_sum(const Jobs& J, int dtype, int a, int beta, const vo
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles_total,
                           int tile, int dtype, bool compensated, bool accumulate, bool even_n0, cudaStream_t s);
 
+// z-slab pieces of three-component 3-D spreading (8^3 tiles): the tile boxes
+// of tiles [tile_begin, tile_begin + ntiles) only (dense: every box written),
+// and the combination of cells [cell_begin, cell_end) only.
+cudaError_t launch_slab_boxes(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long tile_begin,
+                              long long ntiles, int dtype, bool comp, cudaStream_t s);
+cudaError_t launch_slab_combine(const Jobs& J, const Shape& sh, const Bins& B, const void* boxes, long long cell_begin,
+                                long long cell_end, int dtype, bool comp, bool accumulate, bool even_n0,
+                                cudaStream_t s);
+
+// Slab of each point (its xi = 0 cell's tile layer along z within the bounds),
+// -1 for an invalid position.
+constexpr int kMaxSlabs = 64;
+struct SlabBounds {
+  int nslab;
+  int tile;                    // tile side along z
+  int bound[kMaxSlabs + 1];    // tile layers: slab k owns [bound[k], bound[k + 1])
+};
+cudaError_t launch_slab_owner(const Jobs& J, const SlabBounds& sb, long long n, int dtype, int* owner, cudaStream_t s);
+
 // Tile side of the interpolation tiles: 8 in 3-D, 32 in 2-D.
 inline int interp_tile_side(int dim) { return dim == 3 ? 8 : 32; }
 

@@ -502,7 +502,7 @@ __device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane
 
 template <typename T, bool COMP, bool MAC>
 __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
-                                                     T* __restrict__ boxes, int skip_empty) {
+                                                     T* __restrict__ boxes, int skip_empty, long long tile_begin) {
   constexpr int TS = 8;
   using Gm = Geo<3, TS>;
   constexpr int PLANES = COMP ? 2 : 1;
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
   __shared__ uint32_t rpre[NROWS + 1];
   __shared__ Job sjob;
   const int lane = threadIdx.x;
-  const long long gt = blockIdx.x;
+  const long long gt = tile_begin + blockIdx.x;   // tile_begin > 0: a z-slab's tiles only
   // boxes of component a: sums at a * PLANES * BV, errors (compensated) at + BV;
   // then kSpreadBatch + 1 records
   T* box = reinterpret_cast<T*>(smem_raw);
@@ -781,11 +781,12 @@ template <typename T, int D, int TS, bool CP, int V, bool CHECK>
 __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_constant__ Jobs J, const Shape sh,
                                                              const T* __restrict__ boxes,
                                                              const uint32_t* __restrict__ tflags, long long ncell_total,
-                                                             int accumulate, uint32_t* err) {
+                                                             int accumulate, uint32_t* err, long long cell_begin) {
   using Gm = Geo<D, TS>;
   // Blocks walk the grid from its end: the tile kernel writes the boxes in
   // tile order, so the last-written boxes (the ones still in L2) are read first.
-  const int c = ((gridDim.x - 1 - blockIdx.x) * kThreads + threadIdx.x) * V;   // global cell ids stay below 2^31
+  // Cells [cell_begin, ncell_total): every cell, or a z-slab's planes.
+  const int c = (int)cell_begin + ((gridDim.x - 1 - blockIdx.x) * kThreads + threadIdx.x) * V;   // ids below 2^31
   if (c >= ncell_total) return;
   const int jj = job_of_cell(J, c);
   const Job jb = job_at(J, jj);
@@ -1372,24 +1373,26 @@ void launch_spread_warp(const Jobs& J, const Shape& sh, const Bins& B, void* box
 
 template <typename T, bool COMP, bool MAC>
 void launch_spread_tile3(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, int skip_empty,
-                         cudaStream_t s) {
+                         cudaStream_t s, long long tile_begin = 0) {
   using Gm = Geo<3, 8>;
   const size_t bytes = ((size_t)3 * (COMP ? 2 : 1) * Gm::BV + (size_t)(kSpreadBatch + 1) * kRec3) * sizeof(T);
   cudaFuncSetAttribute(k_spread_tile3<T, COMP, MAC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   allow_smem(k_spread_tile3<T, COMP, MAC>, bytes);
-  k_spread_tile3<T, COMP, MAC><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes, skip_empty);
+  k_spread_tile3<T, COMP, MAC><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes, skip_empty, tile_begin);
 }
 
 template <typename T, int D, int TS, bool CP, int V>
 void launch_combine(const Jobs& J, const Shape& sh, const Bins& B, const void* boxes, int acc, bool sparse,
-                    cudaStream_t s) {
-  const unsigned g = grid_for((B.ncell_total + V - 1) / V, kThreads);
+                    cudaStream_t s, long long cell_begin = 0, long long cell_end = -1) {
+  if (cell_end < 0) cell_end = B.ncell_total;
+  const unsigned g = grid_for((cell_end - cell_begin + V - 1) / V, kThreads);
+  if (g == 0) return;
   if (sparse)
-    k_spread_combine<T, D, TS, CP, V, true><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total, acc,
-                                                                   B.err);
+    k_spread_combine<T, D, TS, CP, V, true><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, cell_end, acc,
+                                                                   B.err, cell_begin);
   else
-    k_spread_combine<T, D, TS, CP, V, false><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, B.ncell_total,
-                                                                    acc, B.err);
+    k_spread_combine<T, D, TS, CP, V, false><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, cell_end,
+                                                                    acc, B.err, cell_begin);
 }
 
 template <typename T, int D, int TS>
@@ -1461,6 +1464,34 @@ cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* b
   return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
 }
 
+template <typename T>
+cudaError_t slab_boxes_impl(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long tile_begin,
+                            long long ntiles, bool comp, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (sh.mac) {
+    if (comp) launch_spread_tile3<T, true, true>(J, sh, B, boxes, ntiles, 0, s, tile_begin);
+    else launch_spread_tile3<T, false, true>(J, sh, B, boxes, ntiles, 0, s, tile_begin);
+  } else {
+    if (comp) launch_spread_tile3<T, true, false>(J, sh, B, boxes, ntiles, 0, s, tile_begin);
+    else launch_spread_tile3<T, false, false>(J, sh, B, boxes, ntiles, 0, s, tile_begin);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t slab_combine_impl(const Jobs& J, const Shape& sh, const Bins& B, const void* boxes, long long cell_begin,
+                              long long cell_end, bool comp, bool accumulate, bool even_n0, cudaStream_t s) {
+  const int acc = accumulate ? 1 : 0;
+  if (even_n0) {
+    if (comp) launch_combine<T, 3, 8, true, 2>(J, sh, B, boxes, acc, false, s, cell_begin, cell_end);
+    else launch_combine<T, 3, 8, false, 2>(J, sh, B, boxes, acc, false, s, cell_begin, cell_end);
+  } else {
+    if (comp) launch_combine<T, 3, 8, true, 1>(J, sh, B, boxes, acc, false, s, cell_begin, cell_end);
+    else launch_combine<T, 3, 8, false, 1>(J, sh, B, boxes, acc, false, s, cell_begin, cell_end);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T, int D, int TS>
 cudaError_t interp_impl(const Jobs& J, const Shape& sh, const Bins& B, long long ntiles, double scale,
                         cudaStream_t s) {
@@ -1518,6 +1549,19 @@ cudaError_t launch_advect(const Jobs& J, const Shape& sh, int dtype, const void*
     else k_advect<double, 2><<<grid, kThreads, 0, s>>>(J, (const double*)U, dt, (double*)Xout, vec);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_slab_boxes(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long tile_begin,
+                              long long ntiles, int dtype, bool comp, cudaStream_t s) {
+  if (dtype == 0) return slab_boxes_impl<float>(J, sh, B, boxes, tile_begin, ntiles, comp, s);
+  return slab_boxes_impl<double>(J, sh, B, boxes, tile_begin, ntiles, comp, s);
+}
+
+cudaError_t launch_slab_combine(const Jobs& J, const Shape& sh, const Bins& B, const void* boxes, long long cell_begin,
+                                long long cell_end, int dtype, bool comp, bool accumulate, bool even_n0,
+                                cudaStream_t s) {
+  if (dtype == 0) return slab_combine_impl<float>(J, sh, B, boxes, cell_begin, cell_end, comp, accumulate, even_n0, s);
+  return slab_combine_impl<double>(J, sh, B, boxes, cell_begin, cell_end, comp, accumulate, even_n0, s);
 }
 
 }  // namespace ibgb

@@ -38,6 +38,7 @@ kernels give each job its own bins, tiles and summation order.
 from __future__ import annotations
 
 import collections
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -207,7 +208,13 @@ class Server:
         return _Wave(reqs=reqs, bufs=[], event=ev, footprint=footprint)
 
     def serve(self, requests: list, realtime: bool = True) -> ServeStats:
-        """Serve `requests` (sorted by arrival).  realtime=False admits everything at t = 0."""
+        """Serve `requests` (sorted by arrival).  realtime=False admits everything at t = 0.
+        Python's cyclic garbage collector is paused while the loop runs: a collection over
+        thousands of live request objects can stall it for tens of milliseconds."""
+        with _gc_paused():
+            return self._serve(requests, realtime)
+
+    def _serve(self, requests: list, realtime: bool) -> ServeStats:
         stats = StatsAccumulator()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque = collections.deque()
@@ -314,9 +321,27 @@ class StatsAccumulator:
                           max_inflight_bytes=self.max_inflight, outcomes=dict(self.outcomes))
 
 
+class _gc_paused:
+    """Pause the cyclic garbage collector for the duration of a serving loop."""
+
+    def __enter__(self):
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        if self.was:
+            gc.enable()
+
+
 def single_job_loop(requests: list, realtime: bool = True, device=None) -> ServeStats:
     """One job per launch sequence: for each request in arrival order, copy X and G in, ib_spread +
-    ib_interpolate on a plan for its grid size, copy U out, wait."""
+    ib_interpolate on a plan for its grid size, copy U out, wait (the garbage collector paused, as
+    for the server)."""
+    with _gc_paused():
+        return _single_job_loop(requests, realtime, device)
+
+
+def _single_job_loop(requests: list, realtime: bool, device) -> ServeStats:
     device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     plans, bufs = {}, {}
     maxn = collections.defaultdict(int)

@@ -50,6 +50,13 @@ def test_batched_wave_equals_single_jobs_and_oracle(mods, orc):
         U_ref, Uabs = orc.interp(g, X, host(f).astype(np.float64))
         assert_interp_close(host(U), U_ref, Uabs)
         plan.close()
+    # a wave of one job runs the single-job launches: the same result as in the mix
+    for sp, (X, G, Xd, Gd, f, U) in list(zip(specs, bufs))[:3]:
+        f2 = torch.empty_like(f)
+        U2 = torch.empty_like(U)
+        batch.run([batch.job_struct((sp.N,) * 3, (1.0,) * 3, Xd, G=Gd, f=f2, u=f2, U=U2)])
+        batch.check()
+        assert torch.equal(f2, f) and torch.equal(U2, U)
 
 
 def test_batch_run_host_equals_device_batch(mods):

@@ -956,7 +956,7 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
 // ---------------------------------------------------------------------------
 // Grid values of a tile's box -- nodes T0 - 2 .. T0 + TS + 1 (unwrapped) of
 // every component -- copied into shared memory through registers: each thread
-// loads up to kStageK entries (pairs when n0 is even and the field 2-entry
+// loads stage_k entries (pairs when n0 is even and the field 2-entry
 // aligned: an x pair starting at an even node then never straddles the
 // periodic seam, T0 - 2 being even) before storing them, so the loads of a
 // thread are in flight together, and the 32 lanes of a store write
@@ -967,7 +967,10 @@ __device__ __forceinline__ void node_offsets(const Job& jb, int b, int i, long l
 // grid size n >= 1 (several periodic images inside one box) is read in range.
 // Ends with the stores issued; the caller synchronises the block.
 // ---------------------------------------------------------------------------
-constexpr int kStageK = 8;
+// Entries a thread has in flight while staging: 12 FP32 pairs (a thread's
+// share of a 3-D box, 20-21 pairs, in two rounds at 72 registers; 24 in one
+// round cost 80 registers and spills), half as many FP64 pairs.
+template <typename T> __host__ __device__ constexpr int stage_k() { return sizeof(T) == 4 ? 12 : 6; }
 
 template <typename T, int D, int TS, int NTH>
 __device__ __forceinline__ void stage_box(const Job& jb, int nc, const int T0[3], T* box, uint32_t* err) {
@@ -984,14 +987,15 @@ __device__ __forceinline__ void stage_box(const Job& jb, int nc, const int T0[3]
   __syncthreads();
   const T* u = (const T*)jb.u;
   const int nrows_box = nc * Gm::BZ * Gm::BY;
+  constexpr int K = stage_k<T>();
   if ((n0 % 2) == 0 && ((uintptr_t)u % (2 * sizeof(T))) == 0) {
     using P2 = typename Vec2<T>::type;
     constexpr int NP = Gm::BX / 2;
     const int total = nrows_box * NP;
-    for (int i0 = tid; i0 < total; i0 += NTH * kStageK) {
-      P2 v[kStageK];
+    for (int i0 = tid; i0 < total; i0 += NTH * K) {
+      P2 v[K];
 #pragma unroll
-      for (int k = 0; k < kStageK; ++k) {
+      for (int k = 0; k < K; ++k) {
         const int i = i0 + k * NTH;
         if (i < total) {
           const int row = i / NP;
@@ -1005,17 +1009,17 @@ __device__ __forceinline__ void stage_box(const Job& jb, int nc, const int T0[3]
         }
       }
 #pragma unroll
-      for (int k = 0; k < kStageK; ++k) {
+      for (int k = 0; k < K; ++k) {
         const int i = i0 + k * NTH;
         if (i < total) *reinterpret_cast<P2*>(box + 2 * i) = v[k];   // row * BX + 2 c = 2 i
       }
     }
   } else {
     const int total = nrows_box * Gm::BX;
-    for (int i0 = tid; i0 < total; i0 += NTH * kStageK) {
-      T v[kStageK];
+    for (int i0 = tid; i0 < total; i0 += NTH * K) {
+      T v[K];
 #pragma unroll
-      for (int k = 0; k < kStageK; ++k) {
+      for (int k = 0; k < K; ++k) {
         const int i = i0 + k * NTH;
         if (i < total) {
           const int row = i / Gm::BX;
@@ -1029,7 +1033,7 @@ __device__ __forceinline__ void stage_box(const Job& jb, int nc, const int T0[3]
         }
       }
 #pragma unroll
-      for (int k = 0; k < kStageK; ++k) {
+      for (int k = 0; k < K; ++k) {
         const int i = i0 + k * NTH;
         if (i < total) box[i] = v[k];                                 // row * BX + bx = i
       }
@@ -1071,8 +1075,15 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     }
     return;
   }
-  if (threadIdx.x == 0) sjob = job_at(J, job_of_itile(J, gt));
-  __syncthreads();
+  {
+    // the tile's job into shared memory, one word per thread (the hot loops read it
+    // faster from there than from the kernel parameters)
+    const int j = job_of_itile(J, gt);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&job_at(J, j));
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sjob);
+    for (int w = threadIdx.x; w < (int)(sizeof(Job) / 4); w += kInterpThreads) dst[w] = src[w];
+    __syncthreads();
+  }
   const Job& jb = sjob;
   if (jb.u == nullptr) return;
   int T0[3], TE[3];

@@ -779,7 +779,7 @@ def run_ours(args):
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    names = ("bin", "spread", "interp", "advect")
+    names = ("bin", "interp", "spread", "advect")
     per_call = {k: [] for k in names}
     step_ms = []
     try:
@@ -795,10 +795,11 @@ def run_ours(args):
         plan.bin(X, stream=stream)
         if e is not None:
             e[1].record(stream)
-        plan.spread(X, G, f=f, reuse_bins=True, stream=stream)
+        plan.interpolate(X, ud, U=U, reuse_bins=True, stream=stream)
         if e is not None:
             e[2].record(stream)
-        plan.interpolate(X, ud, U=U, reuse_bins=True, stream=stream)
+        # interpolation wrote only U: spreading may start during its last wave
+        plan.spread(X, G, f=f, reuse_bins=True, overlap_previous=True, stream=stream)
         if e is not None:
             e[3].record(stream)
         plan.advect(X, U, dt, out=X, stream=stream)

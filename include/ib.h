@@ -129,6 +129,14 @@ enum { IB_F32 = 0, IB_F64 = 1 };
                                   (W_kj = prod_b phi(t_b - r_b); Eqs. matrix-interp, matrix-spread: S* = S^T) */
 #define IB_SPREAD_GRAD  0x10u  /* ib_pos_grad: differentiate the weights of spreading, which carry h^-d
                                   (Eq. disc-spread): the library multiplies `scale` by h^-d = prod_b N_b/L_b */
+#define IB_OVERLAP_PREVIOUS 0x20u
+                               /* ib_spread with IB_REUSE_BINS: the caller guarantees that the library call
+                                  issued just before this one on the same stream wrote nothing this call
+                                  reads (X, G, the plan's bins) -- e.g. an ib_interpolate of the same points
+                                  into a separate U.  The spreading kernel may then start while that call's
+                                  last kernel finishes (programmatic dependent launch), filling its tail.
+                                  Ignored without IB_REUSE_BINS.  Wrong if the previous call was ib_bin, or
+                                  wrote X or G: the result is then undefined. */
 
 typedef struct ib_plan_s* ib_plan;
 
@@ -187,7 +195,9 @@ ib_status ib_bin(ib_plan plan, long long npts, const void* X, void* stream);
 
 /* Spreading (Eq. disc-spread): f = S G, or f += S G with IB_ACCUMULATE.
  * X (npts, dim), G (npts, ncomp) read; f [ncomp][grid] written.  Bins X
- * first unless IB_REUSE_BINS.  IB_COMPENSATED carries every node sum as a
+ * first unless IB_REUSE_BINS.  Flags: IB_ACCUMULATE, IB_COMPENSATED,
+ * IB_REUSE_BINS, IB_ADJOINT, IB_OVERLAP_PREVIOUS (others: IB_ERR_INVALID_ARG).
+ * IB_COMPENSATED carries every node sum as a
  * TwoSum (value, error) pair and rounds once at the end; it needs a plan
  * created with IB_PLAN_COMPENSATED (else IB_ERR_INVALID_ARG).  npts = 0
  * writes zeros (or leaves f unchanged with IB_ACCUMULATE). */

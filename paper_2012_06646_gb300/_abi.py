@@ -51,6 +51,7 @@ IB_COMPENSATED = 0x2
 IB_REUSE_BINS = 0x4
 IB_ADJOINT = 0x8
 IB_SPREAD_GRAD = 0x10
+IB_OVERLAP_PREVIOUS = 0x20
 
 IB_BATCH_HOST_IO = 0x1
 

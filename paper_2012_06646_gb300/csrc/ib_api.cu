@@ -457,8 +457,11 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
   if (!f || (npts > 0 && !G)) return IB_ERR_INVALID_ARG;
-  if (flags & ~(IB_ACCUMULATE | IB_COMPENSATED | IB_REUSE_BINS | IB_ADJOINT)) return IB_ERR_INVALID_ARG;
+  if (flags & ~(IB_ACCUMULATE | IB_COMPENSATED | IB_REUSE_BINS | IB_ADJOINT | IB_OVERLAP_PREVIOUS))
+    return IB_ERR_INVALID_ARG;
   const bool comp = (flags & IB_COMPENSATED) != 0;
+  // Without IB_REUSE_BINS this call bins first, and its own binning kernels precede the spreading.
+  const bool overlap = (flags & IB_OVERLAP_PREVIOUS) && (flags & IB_REUSE_BINS);
   if (comp && !(p->desc.flags & IB_PLAN_COMPENSATED)) return IB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   st = prepare(p, npts, X, flags, s);
@@ -483,7 +486,7 @@ ib_status ib_spread(ib_plan p, long long npts, const void* X, const void* G, voi
         cudaSuccess)
       return IB_ERR_CUDA;
   } else if (launch_spread(J, p->sh, call_bins(p, npts), p->boxes, J.one.ntiles, tile, p->desc.dtype, comp, acc,
-                           pair_aligned(p->job.n[0], fo, p->desc.dtype), s) != cudaSuccess) {
+                           pair_aligned(p->job.n[0], fo, p->desc.dtype), s, overlap) != cudaSuccess) {
     return IB_ERR_CUDA;
   }
   if (p->bounded && launch_bounds_crop(p->job, p->desc.ncomp, p->desc.dtype, p->gridx, f,

@@ -61,6 +61,7 @@ __device__ __forceinline__ uint32_t point_key(const Job& jb, const Bins& B, cons
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__ Jobs J, const Bins B, const Shape sh,
                                                          int key_comp) {
+  pdl_launch_dependents();   // writes keys, ranks and counts (scratch) only
   const long long g0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * 4;
   const long long n = B.npts_total;
   if (g0 >= n) return;
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_count4(const __grid_constant__
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_bin_count_ord(const __grid_constant__ Jobs J, const Bins B,
                                                             const Shape sh, int key_comp) {
+  pdl_launch_dependents();
   const long long t0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * 4;
   const long long n = B.npts_total;
   if (t0 >= n) return;
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_count_ord(const __grid_constan
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_bin_count(const __grid_constant__ Jobs J, const Bins B, const Shape sh,
                                                         int key_comp) {
+  pdl_launch_dependents();
   const long long g = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (g >= B.npts_total) return;
   const Job& jb = job_at(J, job_of_point(J, g));
@@ -266,6 +269,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(uint32_t* __rest
                                                                  uint32_t* err, int spin_limit, long long fixed_id) {
   __shared__ long long s_id;
   __shared__ uint32_t s_prefix;
+  pdl_wait();                 // the counts of the kernel before
+  pdl_launch_dependents();
   if (threadIdx.x == 0) s_id = fixed_id >= 0 ? fixed_id : (long long)atomicAdd(state, 1ull);
   __syncthreads();
   const long long id = s_id;
@@ -310,6 +315,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(uint32_t* __rest
 // perm_tmp[cell_start[key] + rank] = (point, key), position t of the
 // processing order (the point is order[t], or t without an order).
 __global__ void __launch_bounds__(kThreads) k_bin_scatter(const Bins B) {
+  pdl_wait();
+  pdl_launch_dependents();
   const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (t >= B.npts_total) return;
   const uint32_t k = B.key[t];
@@ -325,6 +332,8 @@ __global__ void __launch_bounds__(kThreads) k_bin_scatter(const Bins B) {
 // workload of interest, and the cost stays bounded (quadratic in the largest
 // cell) for adversarial input.
 __global__ void __launch_bounds__(kThreads) k_bin_stable(const Bins B) {
+  pdl_wait();
+  pdl_launch_dependents();   // the bins are scratch; readers wait for this kernel
   const long long q = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (q >= B.npts_total) return;
   const uint2 e = B.perm_tmp[q];
@@ -402,12 +411,15 @@ cudaError_t launch_bin(const Jobs& J, const Shape& sh, const Bins& B, int dtype,
   }
   const long long m = B.ncell_total + 1;  // cells plus the sentinel; count[m] receives the total
   const long long nb = scan_blocks(m);
-  k_scan_lookback<<<(unsigned)nb, kScanThreads, 0, s>>>(B.count, m, B.scan, nb, B.err, kScanSpinLimit, -1);
-  if (n > 0) {
-    k_bin_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);
-    k_bin_stable<<<grid_for(n, kThreads), kThreads, 0, s>>>(B);
+  // The scan, scatter and fix-up start while the kernel before finishes (each
+  // waits for it before reading its results).
+  cudaError_t e = launch_pdl(k_scan_lookback, dim3((unsigned)nb), dim3(kScanThreads), 0, s, B.count, m, B.scan, nb,
+                             B.err, kScanSpinLimit, -1ll);
+  if (e == cudaSuccess && n > 0) {
+    e = launch_pdl(k_bin_scatter, dim3(grid_for(n, kThreads)), dim3(kThreads), 0, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_bin_stable, dim3(grid_for(n, kThreads)), dim3(kThreads), 0, s, B);
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_scan_wait_selftest(uint32_t* a, unsigned long long* state, uint32_t* err, int spin_limit,

@@ -20,6 +20,43 @@ constexpr uint32_t ERR_STALE = 4u;   // a point's cell no longer matches its bin
 constexpr uint32_t ERR_BOUNDS = 8u;  // an index check of the IB_DEBUG_BOUNDS build failed (access skipped)
 constexpr uint32_t ERR_TIMEOUT = 16u; // a bounded device-side wait ran out (the kernel ended without it)
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched by launch_pdl may begin
+// while the kernel before it on the stream is still running, as soon as every
+// block of that kernel has called pdl_launch_dependents() (or exited); its
+// pdl_wait() returns once the kernel before has completed and its writes are
+// visible.  Kernels launched the ordinary way start after the kernel before
+// has completed, and for them both calls do nothing.
+// The rules the kernels here keep: every block of a programmatically launched
+// kernel calls pdl_wait() before it reads anything another kernel wrote (the
+// one exception, the spreading tile kernel under IB_OVERLAP_PREVIOUS, still
+// waits in one block, so that its completion implies its predecessor's); a
+// kernel signals its dependents only after its own pdl_wait(), and early only
+// when what it writes is scratch of the library (the binning kernels) or when
+// the one dependent that reads its output early is the tile kernel under
+// IB_OVERLAP_PREVIOUS, whose caller vouches that it reads none of it
+// (interpolation).  Launched here: the scan, scatter and fix-up of binning,
+// interpolation, the spreading tile kernel and the box combination.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Index checks of the debug build.  Compiled with IB_DEBUG_BOUNDS, IB_IN(err,
 // i, n) is true when 0 <= i < n; otherwise it sets ERR_BOUNDS in the error
 // word and the access it guards is skipped, so a wrong index is reported

@@ -91,8 +91,12 @@ cudaError_t launch_paper_sum(const Jobs& J, int dtype, int a, int beta, const vo
 // `boxes`, then the fixed-order combination of overlapping boxes into f.
 // even_n0: every job of the launch has an even n0 (the combination then
 // handles two x-adjacent nodes per thread).
+// overlap: the tile kernel may start before the kernel before it on the stream
+// completes (IB_OVERLAP_PREVIOUS; the caller guarantees that kernel wrote
+// nothing the spreading reads).
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles_total,
-                          int tile, int dtype, bool compensated, bool accumulate, bool even_n0, cudaStream_t s);
+                          int tile, int dtype, bool compensated, bool accumulate, bool even_n0, cudaStream_t s,
+                          bool overlap = false);
 
 // z-slab pieces of three-component 3-D spreading (8^3 tiles): the tile boxes
 // of tiles [tile_begin, tile_begin + ntiles) only (dense: every box written),

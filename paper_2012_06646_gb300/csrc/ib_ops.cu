@@ -28,8 +28,7 @@ namespace {
 constexpr int kThreads = 256;
 
 template <int D, int TS>
-struct Geo {
-  static constexpr int TX = TS, TY = TS, TZ = (D == 3) ? TS : 1;
+struct Geo {   // box of a TS^D tile plus a 2-node apron on every side
   static constexpr int BX = TS + 4, BY = TS + 4, BZ = (D == 3) ? TS + 4 : 1;
   static constexpr int BV = BX * BY * BZ;
   static constexpr int NT = (D == 3) ? 4 : 1;  // support size along z
@@ -380,14 +379,15 @@ constexpr int kRec3 = 76;
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
+struct Dbl4 { double x, y, z, w; };   // four doubles read as two 16-byte halves
+template <> struct Vec4<double> { using type = Dbl4; };
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 __device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ double4 load4(const double* p) {
+__device__ __forceinline__ Dbl4 load4(const double* p) {
   const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-  return make_double4(a.x, a.y, b.x, b.y);
+  return Dbl4{a.x, a.y, b.x, b.y};
 }
 
 // Stage 1 for one point: the record at rec, with multipliers g[a] (h^-d G_a
@@ -502,8 +502,13 @@ __device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane
 
 template <typename T, bool COMP, bool MAC>
 __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
-                                                     T* __restrict__ boxes, int skip_empty, long long tile_begin) {
+                                                     T* __restrict__ boxes, int skip_empty, long long tile_begin,
+                                                     int overlap) {
   constexpr int TS = 8;
+  // Under IB_OVERLAP_PREVIOUS the caller guarantees that the kernel before
+  // wrote nothing this one reads: only block 0 waits for it (so that this
+  // kernel's completion still implies the previous one's).
+  if (!overlap || blockIdx.x == 0) pdl_wait();
   using Gm = Geo<3, TS>;
   constexpr int PLANES = COMP ? 2 : 1;
   constexpr int NROWS = TS * TS;
@@ -611,6 +616,11 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
   const uint4* src = reinterpret_cast<const uint4*>(box);
   uint4* dst = reinterpret_cast<uint4*>(boxes + gt * (long long)(3 * PLANES * Gm::BV));
   for (int i = lane; i < NV; i += 32) dst[i] = src[i];
+  // The combination may launch once every tile is done (it waits for this
+  // kernel before reading a box).  Signalled at the end: combination blocks
+  // launched at the start of the last wave only sat waiting on the SMs and
+  // slowed the spread call (177 us against 165 us).
+  pdl_launch_dependents();
 }
 
 // ---------------------------------------------------------------------------
@@ -783,6 +793,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
                                                              const uint32_t* __restrict__ tflags, long long ncell_total,
                                                              int accumulate, uint32_t* err, long long cell_begin) {
   using Gm = Geo<D, TS>;
+  pdl_wait();   // the tile boxes
   // Blocks walk the grid from its end: the tile kernel writes the boxes in
   // tile order, so the last-written boxes (the ones still in L2) are read first.
   // Cells [cell_begin, ncell_total): every cell, or a z-slab's planes.
@@ -1062,6 +1073,8 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
   __shared__ uint32_t rpre[kInterpThreads + 1];
   __shared__ uint32_t wsum[kInterpWarps];
   __shared__ Job sjob;                  // one copy of the job per CTA (broadcast reads)
+  pdl_wait();                           // the bins (and u) of the kernels before
+  pdl_launch_dependents();              // a spreading call under IB_OVERLAP_PREVIOUS may start
   const long long gt = blockIdx.x;
   if (gt == gridDim.x - 1) {
     // The last block: points with an invalid position, which sit after every
@@ -1384,12 +1397,13 @@ void launch_spread_warp(const Jobs& J, const Shape& sh, const Bins& B, void* box
 
 template <typename T, bool COMP, bool MAC>
 void launch_spread_tile3(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, int skip_empty,
-                         cudaStream_t s, long long tile_begin = 0) {
+                         cudaStream_t s, long long tile_begin = 0, int overlap = 0) {
   using Gm = Geo<3, 8>;
   const size_t bytes = ((size_t)3 * (COMP ? 2 : 1) * Gm::BV + (size_t)(kSpreadBatch + 1) * kRec3) * sizeof(T);
   cudaFuncSetAttribute(k_spread_tile3<T, COMP, MAC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   allow_smem(k_spread_tile3<T, COMP, MAC>, bytes);
-  k_spread_tile3<T, COMP, MAC><<<(unsigned)ntiles, 32, bytes, s>>>(J, sh, B, (T*)boxes, skip_empty, tile_begin);
+  launch_pdl(k_spread_tile3<T, COMP, MAC>, dim3((unsigned)ntiles), dim3(32), bytes, s, J, sh, B, (T*)boxes,
+             skip_empty, tile_begin, overlap);
 }
 
 template <typename T, int D, int TS, bool CP, int V>
@@ -1399,16 +1413,16 @@ void launch_combine(const Jobs& J, const Shape& sh, const Bins& B, const void* b
   const unsigned g = grid_for((cell_end - cell_begin + V - 1) / V, kThreads);
   if (g == 0) return;
   if (sparse)
-    k_spread_combine<T, D, TS, CP, V, true><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, cell_end, acc,
-                                                                   B.err, cell_begin);
+    launch_pdl(k_spread_combine<T, D, TS, CP, V, true>, dim3(g), dim3(kThreads), 0, s, J, sh, (const T*)boxes,
+               (const uint32_t*)B.tflags, cell_end, acc, B.err, cell_begin);
   else
-    k_spread_combine<T, D, TS, CP, V, false><<<g, kThreads, 0, s>>>(J, sh, (const T*)boxes, B.tflags, cell_end,
-                                                                    acc, B.err, cell_begin);
+    launch_pdl(k_spread_combine<T, D, TS, CP, V, false>, dim3(g), dim3(kThreads), 0, s, J, sh, (const T*)boxes,
+               (const uint32_t*)B.tflags, cell_end, acc, B.err, cell_begin);
 }
 
 template <typename T, int D, int TS>
 cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, bool comp,
-                        bool accumulate, bool pairs, cudaStream_t s) {
+                        bool accumulate, bool pairs, cudaStream_t s, int overlap) {
   // A sparse call (fewer than 8 points per tile on average, e.g. a few membranes
   // in a large box) skips the boxes of empty tiles; a dense one writes every box
   // and combines without looking at tile flags.
@@ -1419,11 +1433,11 @@ cudaError_t spread_impl(const Jobs& J, const Shape& sh, const Bins& B, void* box
     if constexpr (D == 3 && TS == 8) {
       if (sh.ncomp == 3) {   // three components: one warp per tile for all of them
         if (sh.mac) {
-          if (comp) launch_spread_tile3<T, true, true>(J, sh, B, boxes, ntiles, skip, s);
-          else launch_spread_tile3<T, false, true>(J, sh, B, boxes, ntiles, skip, s);
+          if (comp) launch_spread_tile3<T, true, true>(J, sh, B, boxes, ntiles, skip, s, 0, overlap);
+          else launch_spread_tile3<T, false, true>(J, sh, B, boxes, ntiles, skip, s, 0, overlap);
         } else {
-          if (comp) launch_spread_tile3<T, true, false>(J, sh, B, boxes, ntiles, skip, s);
-          else launch_spread_tile3<T, false, false>(J, sh, B, boxes, ntiles, skip, s);
+          if (comp) launch_spread_tile3<T, true, false>(J, sh, B, boxes, ntiles, skip, s, 0, overlap);
+          else launch_spread_tile3<T, false, false>(J, sh, B, boxes, ntiles, skip, s, 0, overlap);
         }
         done = true;
       }
@@ -1464,15 +1478,16 @@ size_t box_bytes(int dim, int tile, int entry_bytes, int ncomp, int width) {
 }
 
 cudaError_t launch_spread(const Jobs& J, const Shape& sh, const Bins& B, void* boxes, long long ntiles, int tile,
-                          int dtype, bool comp, bool accumulate, bool even_n0, cudaStream_t s) {
+                          int dtype, bool comp, bool accumulate, bool even_n0, cudaStream_t s, bool overlap) {
   const bool p = even_n0;
+  const int ov = overlap ? 1 : 0;
   if (dtype == 0) {
-    if (sh.dim == 2) return spread_impl<float, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
-    return spread_impl<float, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+    if (sh.dim == 2) return spread_impl<float, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s, ov);
+    return spread_impl<float, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s, ov);
   }
-  if (sh.dim == 2) return spread_impl<double, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+  if (sh.dim == 2) return spread_impl<double, 2, 32>(J, sh, B, boxes, ntiles, comp, accumulate, p, s, ov);
   (void)tile;
-  return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s);
+  return spread_impl<double, 3, 8>(J, sh, B, boxes, ntiles, comp, accumulate, p, s, ov);
 }
 
 template <typename T>
@@ -1511,7 +1526,8 @@ cudaError_t interp_impl(const Jobs& J, const Shape& sh, const Bins& B, long long
   if (ntiles > 0 || B.npts_total > 0) {
     const size_t bytes = (size_t)sh.ncomp * Gm::BV * sizeof(T);
     allow_smem(k_interp_tile<T, D, TS>, bytes);
-    k_interp_tile<T, D, TS><<<(unsigned)(ntiles + 1), kInterpThreads, bytes, s>>>(J, sh, B, (T)scale);
+    launch_pdl(k_interp_tile<T, D, TS>, dim3((unsigned)(ntiles + 1)), dim3(kInterpThreads), bytes, s, J, sh, B,
+               (T)scale);
   }
   return cudaGetLastError();
 }

@@ -158,14 +158,17 @@ class Plan:
         self.bin_epoch += 1
 
     def spread(self, X, G, f=None, accumulate=False, compensated=False, reuse_bins=False, adjoint=False,
-               stream=None):
+               overlap_previous=False, stream=None):
+        """ib_spread.  overlap_previous (IB_OVERLAP_PREVIOUS, with reuse_bins): the library call just before
+        on the stream wrote nothing this one reads (X, G, the bins), so spreading may start during its tail."""
         n = self._points(X)
         self._check(G, (n, self.ncomp), "G")
         if f is None:
             f = self._new(self.grid_shape())
         self._check(f, self.grid_shape(), "f")
         flags = ((_abi.IB_ACCUMULATE if accumulate else 0) | (_abi.IB_COMPENSATED if compensated else 0)
-                 | (_abi.IB_REUSE_BINS if reuse_bins else 0) | (_abi.IB_ADJOINT if adjoint else 0))
+                 | (_abi.IB_REUSE_BINS if reuse_bins else 0) | (_abi.IB_ADJOINT if adjoint else 0)
+                 | (_abi.IB_OVERLAP_PREVIOUS if overlap_previous else 0))
         check(self.lib.ib_spread(self.handle, n, _ptr(X), _ptr(G), _ptr(f), flags, _stream_ptr(stream)), "ib_spread")
         if not reuse_bins:
             self.bin_epoch += 1

@@ -230,3 +230,52 @@ def test_bounded_wait_runs_out_and_the_device_stays_usable(P, orc):
     perm_ref, start_ref = _bins_ref(orc, g, X)
     assert np.array_equal(host(perm), perm_ref)
     assert np.array_equal(host(start)[: g.ncell + 1], start_ref)
+
+
+@pytest.mark.parametrize("comp", [False, True], ids=["plain", "compensated"])
+def test_spreading_that_overlaps_an_interpolation(P, orc, comp):
+    """IB_OVERLAP_PREVIOUS: the spreading kernel may start while the interpolation
+    before it finishes (every kernel of the path is launched programmatically);
+    f is bit for bit the spread issued on its own, eagerly and replayed from a CUDA
+    graph, and U is untouched by the overlap."""
+    n, L, npts = (48, 40, 56), (1.0, 0.8, 1.1), 150_000
+    X = ib_inputs.uniform_points(61, npts, L, 3)
+    G = ib_inputs.normal_array(62, (npts, 3))
+    u = ib_inputs.normal_array(63, (3, 56, 40, 48))
+    Xd, Gd, ud = dev(X), dev(G), dev(u)
+    plan = P(3, n, L, max_points=npts, compensated=comp)
+    f_alone = plan.spread(Xd, Gd, compensated=comp)
+    U_alone = plan.interpolate(Xd, ud, reuse_bins=True)
+    f = torch.empty_like(f_alone)
+    U = torch.empty_like(U_alone)
+
+    def pair():
+        plan.interpolate(Xd, ud, U=U, reuse_bins=True)
+        plan.spread(Xd, Gd, f=f, compensated=comp, reuse_bins=True, overlap_previous=True)
+
+    for _ in range(3):
+        f.fill_(float("nan"))
+        pair()
+        assert torch.equal(f, f_alone) and torch.equal(U, U_alone)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        pair()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pair()
+    for _ in range(3):
+        f.fill_(float("nan"))
+        U.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(f, f_alone) and torch.equal(U, U_alone)
+    # without IB_REUSE_BINS the flag is ignored (the call bins first)
+    f2 = plan.spread(Xd, Gd, compensated=comp, overlap_previous=True)
+    assert torch.equal(f2, f_alone)
+    plan.check()
+    gd = orc.Grid(dim=3, n=n, L=L, mac=True)
+    sel = np.arange(0, npts, 97)
+    U_ref, Uabs = orc.interp(gd, X[sel], u)
+    assert_interp_close(host(U)[sel], U_ref, Uabs)

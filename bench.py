@@ -802,7 +802,7 @@ def run_ours(args):
         plan.spread(X, G, f=f, reuse_bins=True, overlap_previous=True, stream=stream)
         if e is not None:
             e[3].record(stream)
-        plan.advect(X, U, dt, out=X, stream=stream)
+        plan.advect(X, U, dt, out=X, overlap_previous=True, stream=stream)   # spreading wrote only f
         if e is not None:
             e[4].record(stream)
 

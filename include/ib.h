@@ -130,13 +130,15 @@ enum { IB_F32 = 0, IB_F64 = 1 };
 #define IB_SPREAD_GRAD  0x10u  /* ib_pos_grad: differentiate the weights of spreading, which carry h^-d
                                   (Eq. disc-spread): the library multiplies `scale` by h^-d = prod_b N_b/L_b */
 #define IB_OVERLAP_PREVIOUS 0x20u
-                               /* ib_spread with IB_REUSE_BINS: the caller guarantees that the library call
-                                  issued just before this one on the same stream wrote nothing this call
-                                  reads (X, G, the plan's bins) -- e.g. an ib_interpolate of the same points
-                                  into a separate U.  The spreading kernel may then start while that call's
-                                  last kernel finishes (programmatic dependent launch), filling its tail.
-                                  Ignored without IB_REUSE_BINS.  Wrong if the previous call was ib_bin, or
-                                  wrote X or G: the result is then undefined. */
+                               /* ib_spread (with IB_REUSE_BINS) and ib_advect: the caller guarantees that
+                                  the library call issued just before this one on the same stream wrote
+                                  nothing this call reads (X, G and the plan's bins for spreading, X and U
+                                  for the update) -- e.g. an ib_interpolate of the same points into a
+                                  separate U before a spread, an ib_spread before the update.  The call's
+                                  kernel may then start while that call's last kernel finishes
+                                  (programmatic dependent launch), filling its tail.  Ignored by ib_spread
+                                  without IB_REUSE_BINS.  Wrong if the previous call was ib_bin or wrote
+                                  what this one reads: the result is then undefined. */
 
 typedef struct ib_plan_s* ib_plan;
 
@@ -224,9 +226,12 @@ ib_status ib_pos_grad(ib_plan plan, long long npts, const void* X, const void* f
 
 /* Lagrangian position update of the timestep (steps b and g of Section 2):
  * Xout = X + dt U, wrapped into [0, L) per dimension.  X, U (npts, dim);
- * Xout may alias X.  Requires ncomp == dim. */
+ * Xout may alias X.  Requires ncomp == dim.  Flags: IB_OVERLAP_PREVIOUS (the
+ * library call just before on the stream wrote neither X nor U -- e.g. an
+ * ib_spread -- so the update may run during that call's last kernel); any
+ * other bit is IB_ERR_INVALID_ARG. */
 ib_status ib_advect(ib_plan plan, long long npts, const void* X, const void* U, double dt, void* Xout,
-                    void* stream);
+                    unsigned flags, void* stream);
 
 /* Read and clear the plan's device error word with copies ordered on
  * `stream`, waiting for that stream only (work on other streams keeps

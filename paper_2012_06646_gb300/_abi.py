@@ -104,7 +104,7 @@ SIGNATURES = {
     "ib_spread": (_st, [_vp, _ll, _vp, _vp, _vp, ctypes.c_uint, _vp]),
     "ib_interpolate": (_st, [_vp, _ll, _vp, _vp, _vp, ctypes.c_uint, _vp]),
     "ib_pos_grad": (_st, [_vp, _ll, _vp, _vp, _vp, ctypes.c_double, _vp, ctypes.c_uint, _vp]),
-    "ib_advect": (_st, [_vp, _ll, _vp, _vp, ctypes.c_double, _vp, _vp]),
+    "ib_advect": (_st, [_vp, _ll, _vp, _vp, ctypes.c_double, _vp, ctypes.c_uint, _vp]),
     "ib_plan_check": (_st, [_vp, _vp]),
     "ib_plan_bins": (_st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
     "ib_spread_paper": (_st, [_vp, _ll, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),

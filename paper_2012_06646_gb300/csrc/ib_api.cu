@@ -383,9 +383,9 @@ const char* ib_status_string(ib_status st) {
 }
 
 #ifdef IB_DEBUG_BOUNDS
-const char* ib_version(void) { return "ibgb 0.1 (sm_103a, IB_DEBUG_BOUNDS)"; }
+const char* ib_version(void) { return "ibgb 0.2 (sm_103a, IB_DEBUG_BOUNDS)"; }
 #else
-const char* ib_version(void) { return "ibgb 0.1 (sm_103a)"; }
+const char* ib_version(void) { return "ibgb 0.2 (sm_103a)"; }
 #endif
 
 ib_status ib_set_allocator(ib_alloc_fn alloc, ib_free_fn free_fn, void* ctx) {
@@ -708,10 +708,11 @@ ib_status ib_pos_grad(ib_plan p, long long npts, const void* X, const void* fiel
 }
 
 ib_status ib_advect(ib_plan p, long long npts, const void* X, const void* U, double dt, void* Xout,
-                    void* stream) {
+                    unsigned flags, void* stream) {
   const ibgb::NvtxRange nvtx_range("ib_advect");
   ib_status st = check_call(p, npts, X);
   if (st != IB_OK) return st;
+  if (flags & ~IB_OVERLAP_PREVIOUS) return IB_ERR_INVALID_ARG;
   if (p->desc.ncomp != p->desc.dim) return IB_ERR_INVALID_ARG;
   if (npts > 0 && (!U || !Xout)) return IB_ERR_INVALID_ARG;
   if (!isfinite(dt)) return IB_ERR_INVALID_ARG;
@@ -721,7 +722,9 @@ ib_status ib_advect(ib_plan p, long long npts, const void* X, const void* U, dou
   J.one.npts = npts;
   J.one.X = X;
   J.njobs = 1;
-  if (launch_advect(J, p->sh, p->desc.dtype, U, dt, Xout, (cudaStream_t)stream) != cudaSuccess) return IB_ERR_CUDA;
+  if (launch_advect(J, p->sh, p->desc.dtype, U, dt, Xout, (cudaStream_t)stream,
+                    (flags & IB_OVERLAP_PREVIOUS) != 0) != cudaSuccess)
+    return IB_ERR_CUDA;
   if (Xout == X) p->binned = false;  // positions changed in place: the bins no longer describe X
   return IB_OK;
 }

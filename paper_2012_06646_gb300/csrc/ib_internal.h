@@ -128,7 +128,8 @@ cudaError_t launch_interp(const Jobs& J, const Shape& sh, const Bins& B, long lo
 cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int dtype, const void* field,
                             const void* v, double scale, void* D, cudaStream_t s);
 
+// overlap: IB_OVERLAP_PREVIOUS (the kernel before wrote neither X nor U).
 cudaError_t launch_advect(const Jobs& J, const Shape& sh, int dtype, const void* U, double dt, void* Xout,
-                          cudaStream_t s);
+                          cudaStream_t s, bool overlap = false);
 
 }  // namespace ibgb

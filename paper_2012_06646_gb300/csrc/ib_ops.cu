@@ -794,6 +794,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_combine(const __grid_consta
                                                              int accumulate, uint32_t* err, long long cell_begin) {
   using Gm = Geo<D, TS>;
   pdl_wait();   // the tile boxes
+  pdl_launch_dependents();   // only a call under IB_OVERLAP_PREVIOUS reads before waiting, and not f
   // Blocks walk the grid from its end: the tile kernel writes the boxes in
   // tile order, so the last-written boxes (the ones still in L2) are read first.
   // Cells [cell_begin, ncell_total): every cell, or a z-slab's planes.
@@ -1319,10 +1320,13 @@ __global__ void __launch_bounds__(kThreads) k_pos_grad(const __grid_constant__ J
 // the scalar path.
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_advect(const __grid_constant__ Jobs J, const T* __restrict__ U, T dt,
-                                                     T* __restrict__ Xout, int vec) {
+                                                     T* __restrict__ Xout, int vec, int overlap) {
   constexpr int P = 16 / (int)sizeof(T);
   constexpr int NE = P * D;
   constexpr int NV = NE * (int)sizeof(T) / 16;
+  // IB_OVERLAP_PREVIOUS: the kernel before wrote neither X nor U; block 0 still
+  // waits for it, so that this kernel's completion implies the previous one's.
+  if (!overlap || blockIdx.x == 0) pdl_wait();
   const long long n = J.one.npts;
   const long long p0 = ((long long)blockIdx.x * kThreads + threadIdx.x) * P;
   if (p0 >= n) return;
@@ -1562,18 +1566,23 @@ cudaError_t launch_pos_grad(const Jobs& J, const Shape& sh, const Bins& B, int d
 }
 
 cudaError_t launch_advect(const Jobs& J, const Shape& sh, int dtype, const void* U, double dt, void* Xout,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool overlap) {
+  const int ov = overlap ? 1 : 0;
   const long long n = J.one.npts;
   if (n == 0) return cudaSuccess;
   const int vec = ((((uintptr_t)J.one.X) | ((uintptr_t)U) | ((uintptr_t)Xout)) % 16 == 0) ? 1 : 0;
   if (dtype == 0) {
     const unsigned grid = grid_for((n + 3) / 4, kThreads);
-    if (sh.dim == 3) k_advect<float, 3><<<grid, kThreads, 0, s>>>(J, (const float*)U, (float)dt, (float*)Xout, vec);
-    else k_advect<float, 2><<<grid, kThreads, 0, s>>>(J, (const float*)U, (float)dt, (float*)Xout, vec);
+    if (sh.dim == 3) launch_pdl(k_advect<float, 3>, dim3(grid), dim3(kThreads), 0, s, J, (const float*)U, (float)dt,
+                                (float*)Xout, vec, ov);
+    else launch_pdl(k_advect<float, 2>, dim3(grid), dim3(kThreads), 0, s, J, (const float*)U, (float)dt,
+                    (float*)Xout, vec, ov);
   } else {
     const unsigned grid = grid_for((n + 1) / 2, kThreads);
-    if (sh.dim == 3) k_advect<double, 3><<<grid, kThreads, 0, s>>>(J, (const double*)U, dt, (double*)Xout, vec);
-    else k_advect<double, 2><<<grid, kThreads, 0, s>>>(J, (const double*)U, dt, (double*)Xout, vec);
+    if (sh.dim == 3) launch_pdl(k_advect<double, 3>, dim3(grid), dim3(kThreads), 0, s, J, (const double*)U, dt,
+                                (double*)Xout, vec, ov);
+    else launch_pdl(k_advect<double, 2>, dim3(grid), dim3(kThreads), 0, s, J, (const double*)U, dt, (double*)Xout,
+                    vec, ov);
   }
   return cudaGetLastError();
 }

@@ -219,7 +219,9 @@ class Plan:
                                    _stream_ptr(stream)), "ib_pos_grad")
         return D
 
-    def advect(self, X, U, dt: float, out=None, stream=None):
+    def advect(self, X, U, dt: float, out=None, overlap_previous=False, stream=None):
+        """ib_advect: out = X + dt U, wrapped.  overlap_previous (IB_OVERLAP_PREVIOUS): the library call just
+        before on the stream wrote neither X nor U (e.g. a spread), so the update may start during its tail."""
         n = self._points(X)
         self._check(U, (n, self.dim), "U")
         if out is None:
@@ -227,8 +229,9 @@ class Plan:
         self._check(out, (n, self.dim), "out")
         if out.data_ptr() == X.data_ptr():
             self.bin_epoch += 1
-        check(self.lib.ib_advect(self.handle, n, _ptr(X), _ptr(U), float(dt), _ptr(out), _stream_ptr(stream)),
-              "ib_advect")
+        flags = _abi.IB_OVERLAP_PREVIOUS if overlap_previous else 0
+        check(self.lib.ib_advect(self.handle, n, _ptr(X), _ptr(U), float(dt), _ptr(out), flags,
+                                 _stream_ptr(stream)), "ib_advect")
         return out
 
     def check(self, stream=None) -> None:

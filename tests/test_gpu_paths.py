@@ -233,45 +233,53 @@ def test_bounded_wait_runs_out_and_the_device_stays_usable(P, orc):
 
 
 @pytest.mark.parametrize("comp", [False, True], ids=["plain", "compensated"])
-def test_spreading_that_overlaps_an_interpolation(P, orc, comp):
+def test_calls_that_overlap_the_previous_one(P, orc, comp):
     """IB_OVERLAP_PREVIOUS: the spreading kernel may start while the interpolation
-    before it finishes (every kernel of the path is launched programmatically);
-    f is bit for bit the spread issued on its own, eagerly and replayed from a CUDA
-    graph, and U is untouched by the overlap."""
+    before it finishes, and the position update while the spreading's combination
+    runs (every kernel of the path is launched programmatically); f and the new
+    positions are bit for bit those of the calls issued on their own, eagerly and
+    replayed from a CUDA graph, and U is untouched by the overlap."""
     n, L, npts = (48, 40, 56), (1.0, 0.8, 1.1), 150_000
     X = ib_inputs.uniform_points(61, npts, L, 3)
     G = ib_inputs.normal_array(62, (npts, 3))
     u = ib_inputs.normal_array(63, (3, 56, 40, 48))
     Xd, Gd, ud = dev(X), dev(G), dev(u)
+    dt = 0.37
     plan = P(3, n, L, max_points=npts, compensated=comp)
     f_alone = plan.spread(Xd, Gd, compensated=comp)
     U_alone = plan.interpolate(Xd, ud, reuse_bins=True)
+    Xn_alone = plan.advect(Xd, U_alone, dt)
     f = torch.empty_like(f_alone)
     U = torch.empty_like(U_alone)
+    Xn = torch.empty_like(Xn_alone)
 
-    def pair():
+    def calls():
         plan.interpolate(Xd, ud, U=U, reuse_bins=True)
         plan.spread(Xd, Gd, f=f, compensated=comp, reuse_bins=True, overlap_previous=True)
+        plan.advect(Xd, U, dt, out=Xn, overlap_previous=True)
+
+    def clear():
+        for t in (f, U, Xn):
+            t.fill_(float("nan"))
 
     for _ in range(3):
-        f.fill_(float("nan"))
-        pair()
-        assert torch.equal(f, f_alone) and torch.equal(U, U_alone)
+        clear()
+        calls()
+        assert torch.equal(f, f_alone) and torch.equal(U, U_alone) and torch.equal(Xn, Xn_alone)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        pair()
+        calls()
     torch.cuda.current_stream().wait_stream(s)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        pair()
+        calls()
     for _ in range(3):
-        f.fill_(float("nan"))
-        U.fill_(float("nan"))
+        clear()
         g.replay()
         torch.cuda.synchronize()
-        assert torch.equal(f, f_alone) and torch.equal(U, U_alone)
-    # without IB_REUSE_BINS the flag is ignored (the call bins first)
+        assert torch.equal(f, f_alone) and torch.equal(U, U_alone) and torch.equal(Xn, Xn_alone)
+    # without IB_REUSE_BINS the flag is ignored by spreading (the call bins first)
     f2 = plan.spread(Xd, Gd, compensated=comp, overlap_previous=True)
     assert torch.equal(f2, f_alone)
     plan.check()

@@ -500,7 +500,16 @@ __device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane
   }
 }
 
-template <typename T, bool COMP, bool MAC>
+// The job of a tile kernel's block: a single-job launch reads it straight from
+// the kernel parameters (constant-bank operands; a shared-memory copy costs each
+// tile about 0.7 us), a batched wave from the block's shared-memory copy.  Two
+// specialisations, so that neither reads through a generic pointer that may
+// point to either space (which was slower than both).
+template <bool ONE> __device__ __forceinline__ const Job& pick_job(const Jobs& J, const Job& s);
+template <> __device__ __forceinline__ const Job& pick_job<true>(const Jobs& J, const Job&) { return J.one; }
+template <> __device__ __forceinline__ const Job& pick_job<false>(const Jobs&, const Job& s) { return s; }
+
+template <typename T, bool COMP, bool MAC, bool ONE>
 __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Jobs J, const Shape sh, const Bins B,
                                                      T* __restrict__ boxes, int skip_empty, long long tile_begin,
                                                      int overlap) {
@@ -523,14 +532,14 @@ __global__ void __launch_bounds__(32) k_spread_tile3(const __grid_constant__ Job
   // then kSpreadBatch + 1 records
   T* box = reinterpret_cast<T*>(smem_raw);
   T* rec_s = box + 3 * PLANES * Gm::BV;
-  {
+  if constexpr (!ONE) {
     const int j = __shfl_sync(0xffffffffu, lane == 0 ? job_of_tile(J, gt) : 0, 0);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&job_at(J, j));
     uint32_t* dst = reinterpret_cast<uint32_t*>(&sjob);
     for (int w = lane; w < (int)(sizeof(Job) / 4); w += 32) dst[w] = src[w];
     __syncwarp();
   }
-  const Job& jb = sjob;
+  const Job& jb = pick_job<ONE>(J, sjob);
   if (jb.G == nullptr) return;
   int T0[3], TE[3];
   tile_coords<3, TS>(jb.ntile, jb.n, gt - jb.tile_base, T0, TE);
@@ -1404,10 +1413,17 @@ void launch_spread_tile3(const Jobs& J, const Shape& sh, const Bins& B, void* bo
                          cudaStream_t s, long long tile_begin = 0, int overlap = 0) {
   using Gm = Geo<3, 8>;
   const size_t bytes = ((size_t)3 * (COMP ? 2 : 1) * Gm::BV + (size_t)(kSpreadBatch + 1) * kRec3) * sizeof(T);
-  cudaFuncSetAttribute(k_spread_tile3<T, COMP, MAC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  allow_smem(k_spread_tile3<T, COMP, MAC>, bytes);
-  launch_pdl(k_spread_tile3<T, COMP, MAC>, dim3((unsigned)ntiles), dim3(32), bytes, s, J, sh, B, (T*)boxes,
-             skip_empty, tile_begin, overlap);
+  if (J.table) {
+    cudaFuncSetAttribute(k_spread_tile3<T, COMP, MAC, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    allow_smem(k_spread_tile3<T, COMP, MAC, false>, bytes);
+    launch_pdl(k_spread_tile3<T, COMP, MAC, false>, dim3((unsigned)ntiles), dim3(32), bytes, s, J, sh, B, (T*)boxes,
+               skip_empty, tile_begin, overlap);
+  } else {
+    cudaFuncSetAttribute(k_spread_tile3<T, COMP, MAC, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    allow_smem(k_spread_tile3<T, COMP, MAC, true>, bytes);
+    launch_pdl(k_spread_tile3<T, COMP, MAC, true>, dim3((unsigned)ntiles), dim3(32), bytes, s, J, sh, B, (T*)boxes,
+               skip_empty, tile_begin, overlap);
+  }
 }
 
 template <typename T, int D, int TS, bool CP, int V>

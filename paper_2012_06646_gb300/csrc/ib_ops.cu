@@ -500,11 +500,12 @@ __device__ __forceinline__ void tile3_add(T* box, const T* rb, int cnt, int lane
   }
 }
 
-// The job of a tile kernel's block: a single-job launch reads it straight from
-// the kernel parameters (constant-bank operands; a shared-memory copy costs each
-// tile about 0.7 us), a batched wave from the block's shared-memory copy.  Two
-// specialisations, so that neither reads through a generic pointer that may
-// point to either space (which was slower than both).
+// The job of a tile kernel's block (spreading, interpolation): a single-job
+// launch reads it straight from the kernel parameters (constant-bank operands;
+// filling a shared-memory copy costs each tile 0.2-0.7 us), a batched wave from
+// the block's shared-memory copy.  Two specialisations, so that neither reads
+// through a generic pointer that may point to either space (which was slower
+// than both).
 template <bool ONE> __device__ __forceinline__ const Job& pick_job(const Jobs& J, const Job& s);
 template <> __device__ __forceinline__ const Job& pick_job<true>(const Jobs& J, const Job&) { return J.one; }
 template <> __device__ __forceinline__ const Job& pick_job<false>(const Jobs&, const Job& s) { return s; }
@@ -1073,7 +1074,7 @@ constexpr int kInterpThreads = 128;   // 64 registers per thread: 8 tiles per SM
 constexpr int kInterpWarps = kInterpThreads / 32;
 static_assert(kInterpThreads >= 64, "a tile has up to 64 cell rows (3-D) or 32 (2-D), one per thread");
 
-template <typename T, int D, int TS>
+template <typename T, int D, int TS, bool ONE>
 __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_constant__ Jobs J, const Shape sh,
                                                                  const Bins B, const T scale) {
   using Gm = Geo<D, TS>;
@@ -1098,16 +1099,15 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_tile(const __grid_con
     }
     return;
   }
-  {
-    // the tile's job into shared memory, one word per thread (the hot loops read it
-    // faster from there than from the kernel parameters)
+  if constexpr (!ONE) {
+    // a batched wave: the tile's job into shared memory, one word per thread
     const int j = job_of_itile(J, gt);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(&job_at(J, j));
     uint32_t* dst = reinterpret_cast<uint32_t*>(&sjob);
     for (int w = threadIdx.x; w < (int)(sizeof(Job) / 4); w += kInterpThreads) dst[w] = src[w];
     __syncthreads();
   }
-  const Job& jb = sjob;
+  const Job& jb = pick_job<ONE>(J, sjob);
   if (jb.u == nullptr) return;
   int T0[3], TE[3];
   tile_coords<D, TS>(jb.itile, jb.n, gt - jb.itile_base, T0, TE);
@@ -1545,9 +1545,15 @@ cudaError_t interp_impl(const Jobs& J, const Shape& sh, const Bins& B, long long
   // One block per tile, plus one for the points with invalid positions.
   if (ntiles > 0 || B.npts_total > 0) {
     const size_t bytes = (size_t)sh.ncomp * Gm::BV * sizeof(T);
-    allow_smem(k_interp_tile<T, D, TS>, bytes);
-    launch_pdl(k_interp_tile<T, D, TS>, dim3((unsigned)(ntiles + 1)), dim3(kInterpThreads), bytes, s, J, sh, B,
-               (T)scale);
+    if (J.table) {
+      allow_smem(k_interp_tile<T, D, TS, false>, bytes);
+      launch_pdl(k_interp_tile<T, D, TS, false>, dim3((unsigned)(ntiles + 1)), dim3(kInterpThreads), bytes, s, J, sh,
+                 B, (T)scale);
+    } else {
+      allow_smem(k_interp_tile<T, D, TS, true>, bytes);
+      launch_pdl(k_interp_tile<T, D, TS, true>, dim3((unsigned)(ntiles + 1)), dim3(kInterpThreads), bytes, s, J, sh,
+                 B, (T)scale);
+    }
   }
   return cudaGetLastError();
 }

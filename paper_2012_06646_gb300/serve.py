@@ -283,14 +283,15 @@ class Server:
                     stats.waves += 1
                     stats.max_inflight = max(stats.max_inflight, inflight)
             if realtime and not waiting and pending and all(w is None for w in slots):
-                # Idle until the next arrival: sleep through a long gap, spin the last 2 ms.
-                # A sleep overshoots by tens of microseconds, and by milliseconds when the
-                # core drops into a deep idle state; a spinning loop reacts at once, as the
-                # single-job loop it is compared with does.
+                # Idle until the next arrival: sleep only through a gap longer than 50 ms
+                # (waking 10 ms early), spin otherwise.  A sleep overshoots by tens of
+                # microseconds, and by milliseconds when the core drops into a deep idle
+                # state; a spinning loop reacts at once, as the single-job loop it is
+                # compared with does.
                 target = pending[0].arrival
                 delay = target - (time.perf_counter() - t0)
-                if delay > 0.002:
-                    time.sleep(delay - 0.002)
+                if delay > 0.05:
+                    time.sleep(delay - 0.01)
                 while time.perf_counter() - t0 < target:
                     pass
         torch.cuda.synchronize(self.device)

@@ -287,3 +287,29 @@ def test_calls_that_overlap_the_previous_one(P, orc, comp):
     sel = np.arange(0, npts, 97)
     U_ref, Uabs = orc.interp(gd, X[sel], u)
     assert_interp_close(host(U)[sel], U_ref, Uabs)
+
+
+def test_flag_arguments_are_checked(P):
+    """Bits a call does not take are IB_ERR_INVALID_ARG, before anything is launched; the
+    overlap flag is taken by spreading and the position update, and nothing else new."""
+    from paper_2012_06646_gb300 import _abi
+    npts = 1000
+    plan = P(3, (16, 16, 16), (1.0, 1.0, 1.0), max_points=npts)
+    X = dev(ib_inputs.uniform_points(5, npts, (1.0, 1.0, 1.0), 3))
+    G = dev(ib_inputs.normal_array(6, (npts, 3)))
+    f = torch.empty(plan.grid_shape(), dtype=torch.float32, device="cuda")
+    U = torch.empty((npts, 3), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    lib = plan.lib
+    bad = 0x40
+    assert lib.ib_spread(plan.handle, npts, X.data_ptr(), G.data_ptr(), f.data_ptr(), bad, s) == _abi.IB_ERR_INVALID_ARG
+    assert lib.ib_advect(plan.handle, npts, X.data_ptr(), U.data_ptr(), 0.1, U.data_ptr(), _abi.IB_REUSE_BINS,
+                         s) == _abi.IB_ERR_INVALID_ARG
+    assert lib.ib_interpolate(plan.handle, npts, X.data_ptr(), f.data_ptr(), U.data_ptr(),
+                              _abi.IB_OVERLAP_PREVIOUS, s) == _abi.IB_ERR_INVALID_ARG
+    # the accepted forms run
+    plan.bin(X)
+    plan.spread(X, G, f=f, reuse_bins=True, overlap_previous=True)
+    Xn = plan.advect(X, U.zero_(), 0.1, overlap_previous=True)     # spreading wrote neither X nor U
+    plan.check()
+    assert torch.equal(Xn, X)

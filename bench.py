@@ -1162,7 +1162,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{N}^3 MAC grid, {npts} uniform points per GPU, FP32, standard 4-point "
-                                   "kernel; per step: bin, spread, interpolate, advect",
+                                   "kernel; per step: bin, interpolate, spread (overlapping the interpolation's tail), advect",
                        "grid": N, "n_points": npts, "steps": args.steps,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
